@@ -1,0 +1,152 @@
+"""CPU oracle for the exhaustive flux-balanced pathway traversal.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
+with the CUDA library (``paper_1804_02867_gb300``) and never imports it.
+
+* ``efm_oracle.c``  -- the plain C enumerator (built into ``liboracle.so``);
+* ``reference.py``  -- a pure-Python restatement for tiny inputs;
+* ``bruteforce.py`` -- brute-force EFM enumeration over every support.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_SRC = os.path.join(_HERE, "efm_oracle.c")
+
+TRUNCATED, CAPPED, OVERFLOW_DROPPED = 1, 2, 4
+COUNTER_FIELDS = ("levels", "seeds", "expansions", "overflow", "balanced", "candidates", "results",
+                  "pruned", "frontier", "frontier_max", "status")
+
+
+class _Limits(ctypes.Structure):
+    _fields_ = [("max_len", ctypes.c_int32), ("max_secondary", ctypes.c_int32),
+                ("max_results", ctypes.c_int64), ("max_frontier", ctypes.c_int64)]
+
+
+class _Counters(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in COUNTER_FIELDS]
+
+
+@dataclass
+class Limits:
+    max_len: int = 64
+    max_secondary: int = 4
+    max_results: int = 0
+    max_frontier: int = 0
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle (plain gcc, no architecture-specific flags)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-Wall", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.POINTER
+        lib.oracle_enumerate.argtypes = [
+            ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32),
+            P(ctypes.c_uint8), P(ctypes.c_uint8), ctypes.c_int32, P(_Limits),
+            P(P(ctypes.c_uint64)), P(ctypes.c_int64), P(ctypes.c_int32), P(_Counters)]
+        lib.oracle_enumerate.restype = ctypes.c_int
+        lib.oracle_rank.argtypes = [ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int64), ctypes.c_int32,
+                                    P(ctypes.c_int32)]
+        lib.oracle_rank.restype = ctypes.c_int
+        lib.oracle_column_map.argtypes = [ctypes.c_int32, P(ctypes.c_uint8), P(ctypes.c_int32),
+                                          P(ctypes.c_int32)]
+        lib.oracle_column_map.restype = ctypes.c_int
+        lib.oracle_free.argtypes = [ctypes.c_void_p]
+        lib.oracle_free.restype = None
+        _lib = lib
+    return _lib
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def enumerate_pathways(net, target: int, limits: Limits):
+    """Run the C oracle for one (network, target).  Returns
+    (supports uint64[n, W] sorted by (|U|, column list), counters dict)."""
+    lib = _load()
+    rp = np.ascontiguousarray(net.row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(net.col_idx, dtype=np.int32)
+    cf = np.ascontiguousarray(net.coef, dtype=np.int32)
+    rv = np.ascontiguousarray(net.reversible, dtype=np.uint8)
+    ex = np.ascontiguousarray(net.external, dtype=np.uint8)
+    lim = _Limits(limits.max_len, limits.max_secondary, limits.max_results, limits.max_frontier)
+    out = ctypes.POINTER(ctypes.c_uint64)()
+    n = ctypes.c_int64(0)
+    W = ctypes.c_int32(0)
+    ctr = _Counters()
+    rc = lib.oracle_enumerate(net.n_met, net.n_rxn, _ptr(rp, ctypes.c_int32), _ptr(ci, ctypes.c_int32),
+                              _ptr(cf, ctypes.c_int32), _ptr(rv, ctypes.c_uint8), _ptr(ex, ctypes.c_uint8),
+                              int(target), ctypes.byref(lim), ctypes.byref(out), ctypes.byref(n),
+                              ctypes.byref(W), ctypes.byref(ctr))
+    if rc != 0:
+        if out:
+            lib.oracle_free(out)
+        raise RuntimeError(f"oracle_enumerate failed with code {rc}")
+    w = W.value
+    if n.value > 0:
+        arr = np.ctypeslib.as_array(out, shape=(n.value * w,)).copy().reshape(n.value, w)
+    else:
+        arr = np.zeros((0, w), dtype=np.uint64)
+    lib.oracle_free(out)
+    return arr, {f: int(getattr(ctr, f)) for f in COUNTER_FIELDS}
+
+
+def rank(A, force_big: bool = False) -> int:
+    """Exact rank over Q of an integer matrix (Bareiss; bigint fallback)."""
+    lib = _load()
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.int64))
+    if A.ndim != 2 or A.size == 0:
+        return 0
+    r = ctypes.c_int32(0)
+    rc = lib.oracle_rank(A.shape[0], A.shape[1], _ptr(A, ctypes.c_int64), int(force_big), ctypes.byref(r))
+    if rc != 0:
+        raise RuntimeError(f"oracle_rank failed with code {rc}")
+    return r.value
+
+
+def column_map(net):
+    """Split columns: (original reaction, direction) per column."""
+    lib = _load()
+    rv = np.ascontiguousarray(net.reversible, dtype=np.uint8)
+    n = net.n_rxn + int(rv.sum())
+    cr = np.zeros(n, dtype=np.int32)
+    cd = np.zeros(n, dtype=np.int32)
+    lib.oracle_column_map(net.n_rxn, _ptr(rv, ctypes.c_uint8), _ptr(cr, ctypes.c_int32), _ptr(cd, ctypes.c_int32))
+    return cr, cd
+
+
+def supports_to_lists(supports) -> list:
+    """uint64[n, W] bitsets -> list of ascending column tuples."""
+    out = []
+    for row in np.asarray(supports, dtype=np.uint64):
+        cols = []
+        for w, word in enumerate(row):
+            word = int(word)
+            while word:
+                low = word & -word
+                cols.append(w * 64 + low.bit_length() - 1)
+                word ^= low
+        out.append(tuple(cols))
+    return out

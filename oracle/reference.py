@@ -1,0 +1,206 @@
+"""Pure-Python restatement of the traversal for tiny inputs.
+
+TEST INFRASTRUCTURE ONLY.  A second, independent spelling of the same
+definition as ``efm_oracle.c`` (Python integers, Fraction elimination,
+dictionaries instead of sorted arrays).  It additionally carries the explicit
+flux vector v of one path (with the integer scale s, S_int v = s * EF) to
+every state and checks, at every step, that the stored extra-flux vector EF is
+a positive multiple of S_int v (Eq. 2) and that v is positive exactly on U --
+the invariant the integer ray update (Eq. 3) relies on.
+"""
+from __future__ import annotations
+
+from fractions import Fraction
+from math import gcd
+
+INT32_MAX = 2**31 - 1
+TRUNCATED, CAPPED, OVERFLOW_DROPPED = 1, 2, 4
+
+
+def split_network(net):
+    """Columns: forward then reverse (if reversible) per reaction (Def. 6
+    direction).  Returns (S_int as list of rows over columns, twin, full S
+    rows, internal row indices)."""
+    S = net.dense()
+    cols = []  # (reaction, direction)
+    for j in range(net.n_rxn):
+        cols.append((j, 1))
+        if net.reversible[j]:
+            cols.append((j, -1))
+    N = len(cols)
+    twin = [-1] * N
+    for k in range(N - 1):
+        if cols[k][0] == cols[k + 1][0]:
+            twin[k], twin[k + 1] = k + 1, k
+    full = [[int(S[m, j]) * d for (j, d) in cols] for m in range(net.n_met)]
+    internal = [m for m in range(net.n_met) if not net.external[m]]
+    S_int = [full[m] for m in internal]
+    return S_int, twin, full, cols
+
+
+def rank_fraction(rows):
+    """Rank over Q by Gaussian elimination on Fractions."""
+    A = [[Fraction(x) for x in r] for r in rows]
+    if not A:
+        return 0
+    n_r, n_c = len(A), len(A[0])
+    r = 0
+    for c in range(n_c):
+        piv = next((i for i in range(r, n_r) if A[i][c] != 0), None)
+        if piv is None:
+            continue
+        A[r], A[piv] = A[piv], A[r]
+        for i in range(n_r):
+            if i != r and A[i][c] != 0:
+                f = A[i][c] / A[r][c]
+                A[i] = [x - f * y for x, y in zip(A[i], A[r])]
+        r += 1
+        if r == n_r:
+            break
+    return r
+
+
+def nullity_one(S_int, U, N):
+    """Def. 3 for a balanced support U: nullity over Q of S_int[:, U] is 1."""
+    cols = [k for k in range(N) if (U >> k) & 1]
+    sub = [[row[k] for k in cols] for row in S_int if any(row[k] for k in cols)]
+    return len(cols) - rank_fraction(sub) == 1
+
+
+def _normalise(ef):
+    g = 0
+    for x in ef:
+        g = gcd(g, abs(x))
+    if g == 0:
+        return tuple(ef), True
+    return tuple(x // g for x in ef), False
+
+
+def enumerate_reference(net, target, max_len=64, max_secondary=4, max_results=0, max_frontier=0):
+    S_int, twin, full, cols = split_network(net)
+    M = len(S_int)
+    N = len(cols)
+    deg_out = [sum(1 for k in range(N) if S_int[i][k] < 0) for i in range(M)]
+    deg_in = [sum(1 for k in range(N) if S_int[i][k] > 0) for i in range(M)]
+    ctr = dict(levels=0, seeds=0, expansions=0, overflow=0, balanced=0, candidates=0, results=0,
+               pruned=0, frontier=0, frontier_max=0, status=0)
+    seen = set()
+    results = []  # (U, level)
+
+    def col_of(k):
+        return [S_int[i][k] for i in range(M)]
+
+    def judge(U, level):
+        if U in seen:
+            return
+        seen.add(U)
+        ctr["candidates"] += 1
+        if nullity_one(S_int, U, N):
+            results.append((U, level))
+            ctr["results"] += 1
+
+    def check_invariant(U, ef, v):
+        b = [sum(S_int[i][k] * v.get(k, 0) for k in v) for i in range(M)]
+        assert all(x > 0 for x in v.values())
+        assert set(v) == {k for k in range(N) if (U >> k) & 1}
+        # b is a positive multiple of ef
+        nz = [i for i in range(M) if b[i] != 0]
+        if not nz:
+            assert not any(ef)
+            return
+        i0 = nz[0]
+        assert ef[i0] != 0 and (b[i0] > 0) == (ef[i0] > 0)
+        assert all(b[i] * ef[i0] == ef[i] * b[i0] for i in range(M))
+
+    # level 0: seeds
+    F = {}  # (U, ef) -> (sec, v)
+    for j in range(N):
+        if target >= 0 and full[target][j] <= 0:
+            continue
+        ctr["seeds"] += 1
+        raw = col_of(j)
+        ef, zero = _normalise(raw)
+        U = 1 << j
+        v = {j: 1}
+        scale = max((abs(x) for x in raw), default=0) and gcd(*[abs(x) for x in raw])
+        check_invariant(U, ef, v)
+        if zero:
+            ctr["balanced"] += 1
+            judge(U, 0)
+        else:
+            F[(U, ef)] = (0, v, scale)
+
+    def finish():
+        if ctr["overflow"]:
+            ctr["status"] |= OVERFLOW_DROPPED
+        res = sorted((U for U, _ in results), key=lambda U: (bin(U).count("1"),
+                                                             [k for k in range(N) if (U >> k) & 1]))
+        if max_results > 0:
+            res = res[:max_results]
+        return res, ctr
+
+    ctr["levels"] = 1
+    if max_frontier > 0 and len(F) > max_frontier:
+        ctr["status"] |= TRUNCATED
+        return finish()
+    ctr["frontier"] += len(F)
+    ctr["frontier_max"] = max(ctr["frontier_max"], len(F))
+    if max_results > 0 and ctr["results"] >= max_results:
+        ctr["status"] |= CAPPED
+        return finish()
+
+    level = 0
+    while F:
+        level += 1
+        C = {}
+        for (U, ef), (sec, v, scale) in F.items():
+            pc = bin(U).count("1")
+            cand = [(deg_out[i] if ef[i] > 0 else deg_in[i], i) for i in range(M) if ef[i] != 0]
+            _, piv = min(cand)
+            e = ef[piv]
+            for k in range(N):
+                s = S_int[piv][k]
+                if not ((s < 0) if e > 0 else (s > 0)):
+                    continue
+                if twin[k] >= 0 and (U >> twin[k]) & 1:
+                    continue
+                in_u = (U >> k) & 1
+                if not in_u and pc + 1 > max_len:
+                    continue
+                if in_u and sec + 1 > max_secondary:
+                    continue
+                ctr["expansions"] += 1
+                g = gcd(abs(e), abs(s))
+                a, c = abs(s) // g, abs(e) // g
+                raw = [a * ef[i] + c * S_int[i][k] for i in range(M)]
+                nef, zero = _normalise(raw)
+                if any(abs(x) > INT32_MAX for x in nef):
+                    ctr["overflow"] += 1
+                    continue
+                U2 = U | (1 << k)
+                # S_int v = scale * EF, so flux c on k is c * scale in v's units
+                v2 = {kk: a * vv for kk, vv in v.items()}
+                v2[k] = v2.get(k, 0) + c * scale
+                g2 = gcd(*[abs(x) for x in raw]) if any(raw) else 1
+                check_invariant(U2, nef, v2)
+                if zero:
+                    ctr["balanced"] += 1
+                    judge(U2, level)
+                    continue
+                if any((E & ~U2) == 0 for E, lv in results if lv < level):
+                    ctr["pruned"] += 1
+                    continue
+                key = (U2, nef)
+                if key not in C or C[key][0] > sec + in_u:
+                    C[key] = (sec + in_u, v2, scale * g2)
+        F = C
+        ctr["levels"] = level + 1
+        if max_frontier > 0 and len(F) > max_frontier:
+            ctr["status"] |= TRUNCATED
+            break
+        ctr["frontier"] += len(F)
+        ctr["frontier_max"] = max(ctr["frontier_max"], len(F))
+        if max_results > 0 and ctr["results"] >= max_results:
+            ctr["status"] |= CAPPED
+            break
+    return finish()

@@ -1,0 +1,214 @@
+"""Pins of the CPU oracle to things other than itself (no GPU needed).
+
+* hand-worked networks (tests/golden/handworked.json, derived by hand from
+  Def. 2-3, Eq. 2-4 and the exhaustive restatement of Alg. 3);
+* the exact rank routine against sympy, including the arbitrary-precision
+  fallback;
+* Type I networks (Lemma 2): results equal the simple paths and simple
+  cycles of the reaction digraph, enumerated by networkx;
+* tiny random networks: every result is an elementary flux mode (exact
+  sympy null space), and results are a subset of the brute-force EFM set;
+* the overflow rule on a chain whose flux grows by 4 per step.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1804_02867_gb300 import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _handworked():
+    with open(os.path.join(HERE, "golden", "handworked.json")) as f:
+        return json.load(f)["cases"]
+
+
+@pytest.mark.parametrize("case", _handworked(), ids=lambda c: c["name"])
+def test_handworked(oracle_lib, case):
+    net = synth.Network.from_dense(case["S"], case["reversible"], case["external"])
+    lim = oracle_lib.Limits(case["max_len"], case["max_secondary"], 0, 0)
+    sup, ctr = oracle_lib.enumerate_pathways(net, case["target"], lim)
+    assert oracle_lib.supports_to_lists(sup) == [tuple(x) for x in case["expected"]]
+    for k, v in case.get("counters", {}).items():
+        assert ctr[k] == v, (k, ctr)
+
+
+def test_handworked_python_reference_agrees(oracle_lib):
+    from oracle import reference
+
+    for case in _handworked():
+        net = synth.Network.from_dense(case["S"], case["reversible"], case["external"])
+        res, ctr = reference.enumerate_reference(net, case["target"], case["max_len"], case["max_secondary"])
+        got = [tuple(k for k in range(64) if (U >> k) & 1) for U in res]
+        assert got == [tuple(x) for x in case["expected"]], case["name"]
+        for k, v in case.get("counters", {}).items():
+            assert ctr[k] == v, (case["name"], k)
+
+
+def test_rank_matches_sympy(oracle_lib):
+    import sympy
+
+    rng = np.random.default_rng(7)
+    for trial in range(300):
+        r, c = int(rng.integers(1, 9)), int(rng.integers(1, 9))
+        k = int(rng.integers(1, min(r, c) + 1))
+        A = rng.integers(-3, 4, size=(r, k)) @ rng.integers(-3, 4, size=(k, c))
+        if trial % 3 == 0:
+            A = rng.integers(-2, 3, size=(r, c))
+        want = sympy.Matrix(A.tolist()).rank()
+        assert oracle_lib.rank(A) == want
+        assert oracle_lib.rank(A, force_big=True) == want
+
+
+def test_rank_bigint_fallback_on_huge_minors(oracle_lib):
+    """Entries near 2^30 make 12x12 minors far exceed 2^127, so the __int128
+    elimination overflows and the arbitrary-precision path decides."""
+    import sympy
+
+    rng = np.random.default_rng(11)
+    for trial in range(6):
+        n = 12
+        k = 12 if trial % 2 == 0 else 9
+        B = rng.integers(-(2**15), 2**15, size=(n, k))
+        C = rng.integers(-(2**14), 2**14, size=(k, n))
+        A = B @ C
+        want = sympy.Matrix(A.tolist()).rank()
+        assert oracle_lib.rank(A) == want
+
+
+def _type1_expected(net, target, max_len):
+    """Simple source-to-sink paths and simple cycles of the bipartite
+    metabolite/column digraph that contain a column producing the target."""
+    import networkx as nx
+
+    from oracle import bruteforce
+
+    S_int, twin, full = bruteforce.split(net)
+    M, N = S_int.shape
+    G = nx.DiGraph()
+    G.add_node("src")
+    G.add_node("snk")
+    for k in range(N):
+        subs = [i for i in range(M) if S_int[i, k] < 0]
+        prods = [i for i in range(M) if S_int[i, k] > 0]
+        assert len(subs) <= 1 and len(prods) <= 1
+        G.add_edge(("m", subs[0]) if subs else "src", ("c", k))
+        G.add_edge(("c", k), ("m", prods[0]) if prods else "snk")
+    found = set()
+    for path in nx.all_simple_paths(G, "src", "snk"):
+        found.add(tuple(sorted(n[1] for n in path if isinstance(n, tuple) and n[0] == "c")))
+    H = G.copy()
+    H.remove_nodes_from(["src", "snk"])
+    for cyc in nx.simple_cycles(H):
+        found.add(tuple(sorted(n[1] for n in cyc if n[0] == "c")))
+    seeds = bruteforce.seeds_of(net, target)
+    out = []
+    for cols in found:
+        if len(cols) > max_len:
+            continue
+        if any(twin[a] in cols for a in cols if twin[a] >= 0):
+            continue
+        if not seeds.intersection(cols):
+            continue
+        out.append(cols)
+    return sorted(out, key=lambda c: (len(c), c))
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_type1_equals_simple_paths_and_cycles(oracle_lib, seed):
+    net = synth.type1(seed)
+    for t in list(net.targets) + [-1]:
+        for L in (3, 6, 40):
+            sup, ctr = oracle_lib.enumerate_pathways(net, t, oracle_lib.Limits(L, 0, 0, 0))
+            assert oracle_lib.supports_to_lists(sup) == _type1_expected(net, t, L), (t, L)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_tiny_results_are_efms_and_within_bruteforce(oracle_lib, seed):
+    from oracle import bruteforce
+
+    net = synth.tiny(seed)
+    S_int, twin, full = bruteforce.split(net)
+    efms = set(bruteforce.efm_supports(net))
+    recall = []
+    for t in list(net.targets) + [-1]:
+        L = 8
+        sup, ctr = oracle_lib.enumerate_pathways(net, t, oracle_lib.Limits(L, 2, 0, 0))
+        res = oracle_lib.supports_to_lists(sup)
+        seeds = bruteforce.seeds_of(net, t)
+        truth = {e for e in efms if len(e) <= L and seeds.intersection(e)}
+        for cols in res:
+            # precision: each result is an EFM (exact), within limits
+            assert bruteforce.is_efm_support(S_int, cols)
+            assert len(cols) <= L and seeds.intersection(cols)
+            assert not any(twin[a] in cols for a in cols if twin[a] >= 0)
+            assert cols in truth
+        recall.append((len(res), len(truth)))
+    assert sum(r for r, _ in recall) > 0
+    print("recall (found, true) per target:", recall)
+
+
+def test_overflow_chain(oracle_lib):
+    """Chain t <- X0 <- 4 X1 <- 16 X2 ...: the shortfall on X_i is 4^i while a
+    second shortfall (W, two inputs) keeps the gcd at 1, so the child
+    reaching X16 (4^16 > 2^31 - 1) is dropped as overflow."""
+    n = 17  # X0..X16
+    mets = n + 1 + 3  # X*, W, t, S, S2
+    W_, t, Sx, S2 = n, n + 1, n + 2, n + 3
+    cols = []
+    c = np.zeros(mets, dtype=np.int64)
+    c[0], c[W_], c[t] = -1, -1, 1  # r0: X0 + W -> t
+    cols.append(c)
+    for i in range(1, n):  # r_i: 4 X_i -> X_{i-1}
+        c = np.zeros(mets, dtype=np.int64)
+        c[i], c[i - 1] = -4, 1
+        cols.append(c)
+    c = np.zeros(mets, dtype=np.int64)
+    c[Sx], c[n - 1] = -1, 1  # S -> X16
+    cols.append(c)
+    for src in (Sx, S2):  # two inputs of W
+        c = np.zeros(mets, dtype=np.int64)
+        c[src], c[W_] = -1, 1
+        cols.append(c)
+    S = np.stack(cols, axis=1)
+    ext = np.zeros(mets, dtype=np.uint8)
+    ext[[t, Sx, S2]] = 1
+    net = synth.Network.from_dense(S, np.zeros(S.shape[1], np.uint8), ext)
+    sup, ctr = oracle_lib.enumerate_pathways(net, t, oracle_lib.Limits(40, 0, 0, 0))
+    assert ctr["overflow"] == 1 and ctr["status"] & 4
+    assert ctr["expansions"] == 16 and len(sup) == 0
+    # a shorter length limit stops before the overflowing step
+    sup, ctr = oracle_lib.enumerate_pathways(net, t, oracle_lib.Limits(10, 0, 0, 0))
+    assert ctr["overflow"] == 0 and ctr["expansions"] == 9
+
+
+def test_truncation_and_cap_are_level_granular(oracle_lib):
+    net = synth.tiny(3)
+    full, cf = oracle_lib.enumerate_pathways(net, -1, oracle_lib.Limits(8, 1, 0, 0))
+    assert cf["status"] == 0
+    # cap: stop after the level where the count reaches the cap, keep the smallest
+    cap = 5
+    sup, c = oracle_lib.enumerate_pathways(net, -1, oracle_lib.Limits(8, 1, cap, 0))
+    assert c["status"] & 2 and len(sup) == cap
+    got = oracle_lib.supports_to_lists(sup)
+    assert got == sorted(got, key=lambda x: (len(x), x))
+    # truncation: stop before expanding a frontier larger than the budget
+    sup, t = oracle_lib.enumerate_pathways(net, -1, oracle_lib.Limits(8, 1, 0, 50))
+    assert t["status"] & 1 and t["frontier_max"] <= 50
+    assert set(oracle_lib.supports_to_lists(sup)) <= set(oracle_lib.supports_to_lists(full))
+
+
+def test_invalid_inputs_rejected(oracle_lib):
+    net = synth.tiny(0)
+    bad = synth.Network(net.n_met, net.n_rxn, net.row_ptr.copy(), net.col_idx.copy(), net.coef.copy(),
+                        net.reversible, net.external)
+    bad.coef[0] = 0
+    with pytest.raises(RuntimeError):
+        oracle_lib.enumerate_pathways(bad, -1, oracle_lib.Limits(8, 1, 0, 0))
+    with pytest.raises(RuntimeError):
+        oracle_lib.enumerate_pathways(net, net.n_met, oracle_lib.Limits(8, 1, 0, 0))
+    with pytest.raises(RuntimeError):
+        oracle_lib.enumerate_pathways(net, -1, oracle_lib.Limits(65, 1, 0, 0))
