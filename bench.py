@@ -1,0 +1,366 @@
+#!/usr/bin/env python3
+"""Benchmark of the flux-balanced pathway traversal on one GB300.
+
+Workload (the core-shaped network): 72 metabolites (58 internal), 95
+reactions (19 reversible, 114 split columns, 128-bit supports), all pathways
+to each of its 8 target externals, max_len 30, max_secondary 4, frontier
+budget 2^26 states per level.  One step = efm_find_pathways over the 8
+targets (seed, then per level: expand + dedup + prune, minimality test),
+with the network already resident on the device.
+
+Metric: materialised children (AND updates, before deduplication) per
+second, whole job; balanced pathways per second alongside.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica on its own
+GPU (the traversal of one target does not shard); rank 0 prints one JSON
+line with the sum of work over the max of the ranks' times.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "partial-pathway expansions/sec and balanced pathways/sec at 1 GB300; first-K time vs plain"
+UNIT = "expansions/s"
+MAX_LEN, MAX_SEC = 30, 4
+BUDGET = 2**26
+CPU_SAMPLE_BUDGET = 2**20
+REF_STEP_BUDGET = 2**17
+L2_BYTES = 129 * 2**20
+
+
+def workload_config(budget):
+    return {
+        "workload": "core-72x95 (58 internal, 114 split columns), 8 target externals",
+        "max_len": MAX_LEN, "max_secondary": MAX_SEC, "max_frontier": budget,
+        "support_bits": 128, "balance": "int32 x 58",
+        "l2": "frontier arenas far exceed L2 (up to 2^26 states x 276 B); L2 also flushed between steps",
+        "parallelism": "replicas",
+    }
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--budget", type=int, default=BUDGET)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def profile_traffic():
+    """Per-launch DRAM traffic of the expansion kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "expand_kernel_core.md")
+    src = os.path.join(ROOT, "paper_1804_02867_gb300", "csrc", "efm_kernels.cu")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    m_tr = re.search(r"dram_bytes_per_launch_full_scale:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_tr or m_sha.group(1) != sha:
+        return None
+    return float(m_tr.group(1))
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(net, budget, threads):
+    """Run the CPU oracle over the 8 targets on `threads` host threads."""
+    import oracle
+
+    oracle.build()
+    lim = oracle.Limits(MAX_LEN, MAX_SEC, 0, budget)
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        outs = list(ex.map(lambda t: oracle.enumerate_pathways(net, t, lim), net.targets))
+    dt = time.perf_counter() - t0
+    exp = sum(c["expansions"] for _, c in outs)
+    res = sum(len(s) for s, _ in outs)
+    return exp, res, dt
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, as it stands, on the host cores."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1804_02867_gb300 import synth
+
+    net = synth.core()
+    threads = min(os.cpu_count() or 1, len(net.targets))
+    for _ in range(args.warmup):
+        oracle_sample(net, REF_STEP_BUDGET, threads)
+    tot_exp, tot_res, tot_t, times = 0, 0, 0.0, []
+    for _ in range(args.steps):
+        e, r, dt = oracle_sample(net, REF_STEP_BUDGET, threads)
+        tot_exp += e
+        tot_res += r
+        tot_t += dt
+        times.append(dt)
+    value = tot_exp / tot_t
+    sample = f"core-72x95, 8 targets, max_len {MAX_LEN}, max_secondary {MAX_SEC}, frontier budget {REF_STEP_BUDGET}"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (seeded core-shaped network)", "config": workload_config(REF_STEP_BUDGET),
+        "balanced_pathways_per_s": tot_res / tot_t,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_1804_02867_gb300 import build as libbuild
+    from paper_1804_02867_gb300 import efmgraph, synth
+
+    libbuild.build()
+    efmgraph.load_library()
+    net = synth.core()
+    targets = list(net.targets)
+    stream = torch.cuda.current_stream()
+    budget = args.budget
+
+    # CPU baseline first, before heavy GPU use (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        threads = min(os.cpu_count() or 1, len(targets))
+        e, r, dt = oracle_sample(net, CPU_SAMPLE_BUDGET, threads)
+        cpu = {"value": e / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"core-72x95, 8 targets in parallel, max_len {MAX_LEN}, max_secondary {MAX_SEC}, "
+                         f"frontier budget {CPU_SAMPLE_BUDGET} (GPU: {budget}); {e} expansions in {dt:.1f} s",
+               "balanced_pathways_per_s": r / dt}
+
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
+    nw = efmgraph.Network(net, stream)
+
+    def step():
+        job, _ = efmgraph.efm_find_pathways(nw.handle, targets, MAX_LEN, MAX_SEC, 0, budget)
+        exp = res = 0
+        kl = 0
+        tms = ems = eb = 0.0
+        el = 0
+        for i in range(len(targets)):
+            _, ctr, _ = efmgraph.efm_fetch_results(job, i, copy=False)
+            tm = efmgraph.efm_job_timing(job, i)
+            exp += ctr["expansions"]
+            res += ctr["results"]
+            kl += tm["kernel_launches"]
+            ems += tm["expand_ms"]
+            eb += tm["expand_bytes"]
+            el += tm["expand_launches"]
+        efmgraph.efm_free_job(job)
+        return exp, res, kl, ems, eb, el
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    tot_exp = tot_res = tot_kl = tot_el = 0
+    tot_ms = tot_ems = tot_eb = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1)  # evict L2 between timed steps (not timed)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        e, r, kl, ems, eb, el = step()
+        ev1.record(stream)
+        ev1.synchronize()
+        tot_ms += ev0.elapsed_time(ev1)
+        tot_exp += e
+        tot_res += r
+        tot_kl += kl
+        tot_ems += ems
+        tot_eb += eb
+        tot_el += el
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if ws > 1:
+        torch.distributed.barrier()
+
+    # end to end through the C-ABI: host arrays in (pinned), results out (pinned)
+    arrs = [net.row_ptr, net.col_idx, net.coef, net.reversible, net.external]
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in arrs]
+    h2d = sum(p.numel() * p.element_size() for p in pinned) + 4 * len(targets)
+    e2e_steps = max(1, min(args.steps, 3))
+    e2e_t = 0.0
+    e2e_exp = 0
+    d2h = 0
+    for _ in range(e2e_steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        views = [p.numpy() for p in pinned]
+        h = efmgraph.efm_load_network(net.n_met, net.n_rxn, *views, stream)
+        job, _ = efmgraph.efm_find_pathways(h, targets, MAX_LEN, MAX_SEC, 0, budget)
+        step_d2h = 0
+        for i in range(len(targets)):
+            sup, ctr, _ = efmgraph.efm_fetch_results(job, i)
+            e2e_exp += ctr["expansions"]
+            step_d2h += sup.nbytes + 11 * 8
+        efmgraph.efm_free_job(job)
+        efmgraph.efm_free_net(h)
+        torch.cuda.synchronize()
+        e2e_t += time.perf_counter() - t0
+        d2h = step_d2h
+
+    # max over ranks of the device time; sum of work over ranks
+    if ws > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([tot_ms, e2e_t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        w = torch.tensor([tot_exp, tot_res, e2e_exp], device="cuda", dtype=torch.float64)
+        dist.all_reduce(w, op=dist.ReduceOp.SUM)
+        tot_ms, e2e_t = float(t[0]), float(t[1])
+        tot_exp, tot_res, e2e_exp = int(w[0]), int(w[1]), int(w[2])
+    nw.close()
+    if rank != 0:
+        return
+    peaks, peak_kind = measured_peaks()
+    achieved = (tot_eb / (tot_ems * 1e-3)) / 1e9 if tot_ems > 0 else 0.0
+    traffic = profile_traffic()
+    line = {
+        "metric": METRIC,
+        "value": tot_exp / (tot_ms * 1e-3),
+        "unit": UNIT,
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": tot_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32",
+        "data": "synthetic (seeded core-shaped network, no dataset)",
+        "config": workload_config(budget),
+        "balanced_pathways_per_s": tot_res / (tot_ms * 1e-3),
+        "expansions_per_step": tot_exp / args.steps / max(ws, 1),
+        "results_per_step": tot_res / args.steps / max(ws, 1),
+        "roofline": {
+            "kernel": "expand_kernel<2>",
+            "bound": "hbm",
+            "achieved": achieved,
+            "peak": float(peaks["hbm_gbs"]),
+            "unit": "GB/s",
+            "frac": achieved / float(peaks["hbm_gbs"]),
+            "traffic": (traffic * tot_el / max(tot_el, 1)) if traffic else None,
+            "peak_kind": f"{peak_kind} HBM copy bandwidth",
+            "launches": tot_el,
+            "avg_launch_ms": tot_ems / max(tot_el, 1),
+            "alg_bytes_per_launch": tot_eb / max(tot_el, 1),
+            "expand_share_of_step": tot_ems / tot_ms if tot_ms else None,
+        },
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_exp / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": tot_kl,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,166 @@
+/*
+ * efmgraph.h -- C-ABI of the GB300 flux-balanced pathway library.
+ *
+ * The library enumerates flux-balanced, elementary pathways of a metabolic
+ * network by exhaustive traversal of its AND/OR graph (metabolites are OR
+ * nodes, reactions AND nodes; Sec. 2.2, Def. 4-7).  Input: the
+ * stoichiometric matrix S (Sec. 2.1) with reversibility and external flags.
+ * Output: the set of minimal flux-balanced pathways (Alg. 1 input/output),
+ * each reported as its reaction support over split columns.
+ *
+ * Conventions
+ *  - Every function returns 0 on success, a negative EFM_E* code on error
+ *    (no partial results are then defined), or for efm_find_pathways /
+ *    efm_fetch_results possibly a positive combination of EFM_TRUNCATED,
+ *    EFM_CAPPED, EFM_OVERFLOW_DROPPED (completed with warnings).
+ *  - Nothing is thrown across this boundary.  Handles are not thread-safe:
+ *    use one handle from one host thread at a time.
+ *  - All host arrays passed in are copied before the call returns; the
+ *    caller keeps ownership.  Device memory is owned by the library and
+ *    released by the matching efm_free_*.
+ *  - Split columns: reaction j gives column "forward j"; a reversible
+ *    reaction also gives the next column "reverse j" (the direction of
+ *    Def. 6).  efm_column_map() returns the mapping.
+ *  - Supports are bitsets of W = ceil(N / 64) little-endian uint64 words,
+ *    column k at bit (k % 64) of word (k / 64).
+ */
+#ifndef EFMGRAPH_H
+#define EFMGRAPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define EFM_OK 0
+#define EFM_EINVAL (-1)      /* bad argument or malformed network */
+#define EFM_ENOMEM (-2)      /* device or host allocation failed */
+#define EFM_ECAPACITY (-3)   /* a device buffer limit was exceeded */
+#define EFM_ETIMEOUT (-4)    /* a bounded device-side wait gave up */
+#define EFM_ECUDA (-5)       /* a CUDA runtime call failed */
+#define EFM_EUNSUPPORTED (-6) /* outside the supported sizes (see limits) */
+
+#define EFM_TRUNCATED 1        /* a level's frontier exceeded max_frontier */
+#define EFM_CAPPED 2           /* max_results reached; smallest kept */
+#define EFM_OVERFLOW_DROPPED 4 /* some child balances left the int32 range */
+
+/* ---- supported sizes --------------------------------------------------- */
+#define EFM_MAX_COLUMNS 4096   /* split columns N (support width 64 words) */
+#define EFM_MAX_INTERNAL 1024  /* internal metabolites */
+#define EFM_MAX_LEN 64         /* max_len (pathway length in columns) */
+#define EFM_MAX_COEF 524287    /* |stoichiometric coefficient| */
+
+typedef struct efm_net efm_net; /* opaque, library-owned */
+typedef struct efm_job efm_job; /* opaque, library-owned */
+
+/* Limits of one traversal (the MAX_LOOP bound of Sec. 3.2 and the length
+ * bound L of Alg. 1, plus level-granular budgets). */
+typedef struct {
+    int32_t max_len;       /* max |U| in split columns, 1..EFM_MAX_LEN */
+    int32_t max_secondary; /* max secondary steps per pathway (Def. 10, Eq. 4), >= 0 */
+    int64_t max_results;   /* <= 0: no cap; else stop after the level reaching it (EFM_CAPPED) */
+    int64_t max_frontier;  /* <= 0: no budget; else stop when a level exceeds it (EFM_TRUNCATED) */
+    int32_t first_k;       /* reserved, must be 0 */
+    int32_t proposal;      /* reserved, must be 0 */
+} efm_limits;
+
+/* Counters of one (network, target) traversal; the same definitions as the
+ * CPU oracle's.  frontier / frontier_max exclude a truncated level. */
+typedef struct {
+    int64_t levels;       /* levels executed (level 0 = seeds) */
+    int64_t seeds;        /* seed pathways created (INIT) */
+    int64_t expansions;   /* children materialised by the AND update (Eq. 3/4) */
+    int64_t overflow;     /* children dropped: balance outside int32 */
+    int64_t balanced;     /* balanced pathways produced (with multiplicity) */
+    int64_t candidates;   /* distinct balanced supports judged */
+    int64_t results;      /* supports accepted as elementary (before capping) */
+    int64_t pruned;       /* children dropped: support contains a result */
+    int64_t frontier;     /* sum over levels of distinct frontier states */
+    int64_t frontier_max; /* largest level frontier */
+    int64_t status;       /* EFM_TRUNCATED | EFM_CAPPED | EFM_OVERFLOW_DROPPED */
+} efm_counters;
+
+/* Load a network (Alg. 1 "convert S to the MG graph and copy it to the GPU").
+ *  n_met, n_rxn          : S is n_met x n_rxn
+ *  row_ptr[n_met + 1]    : CSR by metabolite; row_ptr[0] = 0, non-decreasing
+ *  col_idx[nnz]          : reaction index in [0, n_rxn), unique within a row
+ *  coef[nnz]             : net coefficient S[m][j] (Sec. 2.1), nonzero,
+ *                          |coef| <= EFM_MAX_COEF
+ *  reversible[n_rxn]     : 1 = reversible (split into two columns)
+ *  external[n_met]       : 1 = external metabolite (not balanced, Def. 2)
+ *  cuda_stream           : cudaStream_t (0 = legacy default) used by every
+ *                          later call on this network and its jobs
+ *  out                   : receives the handle
+ * Errors: EFM_EINVAL for a malformed CSR, zero or out-of-range
+ * coefficients, N > EFM_MAX_COLUMNS or internal > EFM_MAX_INTERNAL;
+ * EFM_ENOMEM / EFM_ECUDA on allocation or copy failure. */
+int efm_load_network(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, const int32_t *col_idx,
+                     const int32_t *coef, const uint8_t *reversible, const uint8_t *external,
+                     uintptr_t cuda_stream, efm_net **out);
+
+/* Split-column count N and support width W of a loaded network. */
+int efm_network_shape(const efm_net *net, int32_t *n_columns, int32_t *words_per_set,
+                      int32_t *n_internal);
+
+/* Column map: orig_rxn[N] = reaction of each split column, dir[N] = +1
+ * forward / -1 reverse.  Either pointer may be NULL. */
+int efm_column_map(const efm_net *net, int32_t *orig_rxn, int8_t *dir);
+
+/* Enumerate the pathways of each target (Prop. 1: pathways seeded by the
+ * reactions producing the target; -1 = every column).  Runs the level loop
+ * of seed -> expand (OR branches, AND update, ballot/popc tests, hash dedup
+ * and compaction, superset pruning) -> exact mod-p minimality test on the
+ * network's stream and returns when all targets are done.
+ *  targets[n_targets]    : metabolite indices in [0, n_met) or -1
+ *  limits                : see efm_limits (first_k and proposal must be 0)
+ *  model                 : reserved, must be NULL
+ *  out                   : receives the job handle (results stay on device
+ *                          until fetched or freed)
+ * Returns the OR of the warning flags over all targets, or an error. */
+int efm_find_pathways(efm_net *net, const int32_t *targets, int32_t n_targets, const efm_limits *limits,
+                      const void *model, efm_job **out);
+
+/* Copy the results of target number `job_target_idx` (0-based position in
+ * the targets array) into `supports` (host memory, capacity rows of W
+ * words), sorted by (|U|, ascending column list).  supports == NULL is a
+ * size query: *n_out receives the row count.  Rows beyond `capacity` are
+ * not written (EFM_ECAPACITY is returned and *n_out holds the count).
+ * words_per_set and ctr may be NULL.  Returns the target's warning flags. */
+int efm_fetch_results(efm_job *job, int32_t job_target_idx, uint64_t *supports, int64_t capacity,
+                      int64_t *n_out, int32_t *words_per_set, efm_counters *ctr);
+
+/* Measurements of one target's traversal, for the benchmark's roofline:
+ *  total_ms          device time of the whole traversal (CUDA events on the
+ *                    network's stream, seeds to sorted results)
+ *  expand_ms         summed device time of the expansion kernel launches
+ *  expand_launches   number of expansion kernel launches (one per level)
+ *  expand_bytes      algorithmic bytes those launches must move: each parent
+ *                    state read once, each new distinct state written once
+ *                    (state = 8 W + 4 M + 4 bytes), 16 bytes of hash slot
+ *                    traffic per child
+ *  kernel_launches   every kernel this library launched for the target
+ * Any output pointer may be NULL. */
+int efm_job_timing(const efm_job *job, int32_t job_target_idx, double *total_ms, double *expand_ms,
+                   int64_t *expand_launches, double *expand_bytes, int64_t *kernel_launches);
+
+void efm_free_job(efm_job *job);
+void efm_free_net(efm_net *net);
+
+/* Human-readable name of a status code. */
+const char *efm_status_str(int code);
+
+/* Optional device allocator (e.g. PyTorch's caching allocator).  alloc
+ * returns device memory of `bytes` usable on `stream` or NULL; free
+ * releases it.  Passing NULL functions restores cudaMallocAsync /
+ * cudaFreeAsync.  Set before loading networks. */
+typedef void *(*efm_alloc_fn)(size_t bytes, uintptr_t stream, void *ctx);
+typedef void (*efm_free_fn)(void *ptr, size_t bytes, uintptr_t stream, void *ctx);
+int efm_set_allocator(efm_alloc_fn alloc, efm_free_fn free_fn, void *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EFMGRAPH_H */

@@ -1,0 +1,650 @@
+// efm_api.cu -- the C-ABI: network preprocessing, the level loop driving the
+// kernels, and result delivery.  Every step of the traversal runs in the
+// kernels of efm_kernels.cu; this file only prepares static data, sizes
+// buffers, launches and reads back one counter block per level.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "efm_internal.cuh"
+
+using namespace efm;
+
+namespace {
+
+efm_alloc_fn g_alloc = nullptr;
+efm_free_fn g_free = nullptr;
+void *g_ctx = nullptr;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+bool dev_alloc(DevBuf &b, size_t bytes, cudaStream_t s)
+{
+    b.bytes = bytes ? bytes : 16;
+    if (g_alloc) {
+        b.p = g_alloc(b.bytes, (uintptr_t)s, g_ctx);
+        return b.p != nullptr;
+    }
+    if (cudaMallocAsync(&b.p, b.bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return false;
+    }
+    return true;
+}
+
+void dev_free(DevBuf &b, cudaStream_t s)
+{
+    if (!b.p) return;
+    if (g_free)
+        g_free(b.p, b.bytes, (uintptr_t)s, g_ctx);
+    else
+        cudaFreeAsync(b.p, s);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+int pick_epl(int M)
+{
+    const int need = std::max(1, (M + 31) / 32);
+    const int opts[] = {1, 2, 4, 8, 16, 28, 32};
+    for (int o : opts)
+        if (o >= need) return o;
+    return -1;
+}
+
+uint64_t next_pow2(uint64_t x)
+{
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+struct efm_net {
+    int n_met = 0, n_rxn = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<int32_t> col_rxn;
+    std::vector<int8_t> col_dir;
+    NetView nv{};
+    DevBuf blob, metptr, metent;
+    int sm_count = 0;
+};
+
+struct TargetOut {
+    DevBuf sup;
+    int64_t n = 0;
+    efm_counters ctr{};
+    int status = 0;
+    double total_ms = 0.0, expand_ms = 0.0, expand_bytes = 0.0;
+    int64_t expand_launches = 0, kernel_launches = 0;
+};
+
+struct efm_job {
+    efm_net *net = nullptr;
+    std::vector<TargetOut> out;
+};
+
+extern "C" int efm_set_allocator(efm_alloc_fn alloc, efm_free_fn free_fn, void *ctx)
+{
+    if ((alloc == nullptr) != (free_fn == nullptr)) return EFM_EINVAL;
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_ctx = ctx;
+    return EFM_OK;
+}
+
+extern "C" const char *efm_status_str(int code)
+{
+    switch (code) {
+    case EFM_OK: return "ok";
+    case EFM_EINVAL: return "invalid argument";
+    case EFM_ENOMEM: return "out of memory";
+    case EFM_ECAPACITY: return "device buffer capacity exceeded";
+    case EFM_ETIMEOUT: return "bounded device wait expired";
+    case EFM_ECUDA: return "CUDA runtime error";
+    case EFM_EUNSUPPORTED: return "unsupported size";
+    default: break;
+    }
+    if (code > 0) {
+        switch (code & 7) {
+        case EFM_TRUNCATED: return "completed: truncated";
+        case EFM_CAPPED: return "completed: capped";
+        case EFM_OVERFLOW_DROPPED: return "completed: overflow dropped";
+        default: return "completed with warnings";
+        }
+    }
+    return "unknown status";
+}
+
+extern "C" int efm_load_network(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, const int32_t *col_idx,
+                                const int32_t *coef, const uint8_t *reversible, const uint8_t *external,
+                                uintptr_t cuda_stream, efm_net **out)
+{
+    if (!out) return EFM_EINVAL;
+    *out = nullptr;
+    if (n_met <= 0 || n_rxn <= 0 || !row_ptr || !reversible || !external) return EFM_EINVAL;
+    if (row_ptr[0] != 0) return EFM_EINVAL;
+    const int64_t nnz = row_ptr[n_met];
+    if (nnz > 0 && (!col_idx || !coef)) return EFM_EINVAL;
+    std::vector<int32_t> mark(n_rxn, -1);
+    for (int m = 0; m < n_met; ++m) {
+        if (row_ptr[m + 1] < row_ptr[m]) return EFM_EINVAL;
+        for (int p = row_ptr[m]; p < row_ptr[m + 1]; ++p) {
+            const int j = col_idx[p];
+            if (j < 0 || j >= n_rxn) return EFM_EINVAL;
+            if (coef[p] == 0 || coef[p] > EFM_MAX_COEF || coef[p] < -EFM_MAX_COEF) return EFM_EINVAL;
+            if (mark[j] == m) return EFM_EINVAL;  // duplicate entry in a row
+            mark[j] = m;
+        }
+    }
+    auto *net = new (std::nothrow) efm_net();
+    if (!net) return EFM_ENOMEM;
+    net->n_met = n_met;
+    net->n_rxn = n_rxn;
+    net->stream = (cudaStream_t)cuda_stream;
+    // split columns (direction of Def. 6): forward, then reverse if reversible
+    std::vector<int> first_col(n_rxn);
+    int N = 0;
+    for (int j = 0; j < n_rxn; ++j) {
+        first_col[j] = N;
+        net->col_rxn.push_back(j);
+        net->col_dir.push_back(1);
+        ++N;
+        if (reversible[j]) {
+            net->col_rxn.push_back(j);
+            net->col_dir.push_back(-1);
+            ++N;
+        }
+    }
+    std::vector<int> int_row(n_met, -1);
+    int M = 0;
+    for (int m = 0; m < n_met; ++m)
+        if (!external[m]) int_row[m] = M++;
+    const int EPL = pick_epl(M);
+    if (N > EFM_MAX_COLUMNS || M > EFM_MAX_INTERNAL || EPL < 0) {
+        delete net;
+        return EFM_EINVAL;
+    }
+    // S_int by column (rows ascending) and by internal row (columns ascending)
+    std::vector<std::vector<std::pair<int, int32_t>>> col(N), cons(M), prod(M);
+    std::vector<std::vector<std::pair<int, int32_t>>> metrow(n_met);
+    for (int m = 0; m < n_met; ++m) {
+        for (int p = row_ptr[m]; p < row_ptr[m + 1]; ++p) {
+            const int j = col_idx[p];
+            const int f = first_col[j];
+            metrow[m].push_back({f, coef[p]});
+            if (reversible[j]) metrow[m].push_back({f + 1, -coef[p]});
+            if (int_row[m] < 0) continue;
+            col[f].push_back({int_row[m], coef[p]});
+            if (reversible[j]) col[f + 1].push_back({int_row[m], -coef[p]});
+        }
+    }
+    std::vector<uint32_t> hbits(N, 0);
+    for (int k = 0; k < N; ++k) {
+        std::sort(col[k].begin(), col[k].end());
+        uint64_t nsq = 0;
+        for (auto &e : col[k]) {
+            nsq += (uint64_t)((int64_t)e.second * e.second);
+            if (e.second < 0) cons[e.first].push_back({k, -e.second});
+            if (e.second > 0) prod[e.first].push_back({k, e.second});
+        }
+        hbits[k] = nsq <= 1 ? 0u : (uint32_t)(64 - __builtin_clzll(nsq - 1));
+    }
+    // blob assembly
+    std::vector<uint32_t> blob;
+    NetView &nv = net->nv;
+    auto put_csr = [&](std::vector<std::vector<std::pair<int, int32_t>>> &lists, int &o_ptr, int &o_ent) {
+        o_ptr = (int)blob.size();
+        uint32_t acc = 0;
+        for (auto &l : lists) {
+            blob.push_back(acc);
+            acc += (uint32_t)l.size();
+        }
+        blob.push_back(acc);
+        o_ent = (int)blob.size();
+        for (auto &l : lists)
+            for (auto &e : l) blob.push_back(ent_pack(e.first, e.second));
+    };
+    put_csr(col, nv.o_colptr, nv.o_colent);
+    put_csr(cons, nv.o_consptr, nv.o_consent);
+    put_csr(prod, nv.o_prodptr, nv.o_prodent);
+    nv.o_twin = (int)blob.size();
+    for (int k = 0; k < N; ++k) {
+        int tw = -1;
+        if (k + 1 < N && net->col_rxn[k + 1] == net->col_rxn[k]) tw = k + 1;
+        if (k > 0 && net->col_rxn[k - 1] == net->col_rxn[k]) tw = k - 1;
+        blob.push_back((uint32_t)tw);
+    }
+    nv.o_keypos = (int)blob.size();
+    for (int r = 0; r < M; ++r) blob.push_back(((uint32_t)cons[r].size() << 16) | (uint32_t)r);
+    nv.o_keyneg = (int)blob.size();
+    for (int r = 0; r < M; ++r) blob.push_back(((uint32_t)prod[r].size() << 16) | (uint32_t)r);
+    nv.o_hbits = (int)blob.size();
+    for (int k = 0; k < N; ++k) blob.push_back(hbits[k]);
+    while (blob.size() % 4) blob.push_back(0);
+    std::vector<int32_t> mptr(n_met + 1, 0);
+    std::vector<uint32_t> ment;
+    for (int m = 0; m < n_met; ++m) {
+        for (auto &e : metrow[m]) ment.push_back(ent_pack(e.first, e.second));
+        mptr[m + 1] = (int32_t)ment.size();
+    }
+    if (ment.empty()) ment.push_back(0);
+    nv.blob_words = (int)blob.size();
+    nv.M = M;
+    nv.N = N;
+    nv.W = (N + 63) / 64;
+    nv.EPL = EPL;
+    nv.Mpad = 32 * EPL;
+    nv.n_met = n_met;
+    cudaStream_t s = net->stream;
+    int rc = EFM_OK;
+    if (!dev_alloc(net->blob, blob.size() * 4, s) || !dev_alloc(net->metptr, mptr.size() * 4, s) ||
+        !dev_alloc(net->metent, ment.size() * 4, s)) {
+        rc = EFM_ENOMEM;
+    } else if (cudaMemcpyAsync(net->blob.p, blob.data(), blob.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+               cudaMemcpyAsync(net->metptr.p, mptr.data(), mptr.size() * 4, cudaMemcpyHostToDevice, s) !=
+                   cudaSuccess ||
+               cudaMemcpyAsync(net->metent.p, ment.data(), ment.size() * 4, cudaMemcpyHostToDevice, s) !=
+                   cudaSuccess ||
+               cudaStreamSynchronize(s) != cudaSuccess) {
+        rc = EFM_ECUDA;
+    }
+    int dev = 0;
+    if (rc == EFM_OK && (cudaGetDevice(&dev) != cudaSuccess ||
+                         cudaDeviceGetAttribute(&net->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess))
+        rc = EFM_ECUDA;
+    if (rc == EFM_OK && !g_alloc) {
+        // keep freed arenas in this process's stream-ordered pool between jobs
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    }
+    if (rc != EFM_OK) {
+        cudaGetLastError();
+        dev_free(net->blob, s);
+        dev_free(net->metptr, s);
+        dev_free(net->metent, s);
+        delete net;
+        return rc;
+    }
+    nv.blob = (const uint32_t *)net->blob.p;
+    nv.metptr = (const int32_t *)net->metptr.p;
+    nv.metent = (const uint32_t *)net->metent.p;
+    *out = net;
+    return EFM_OK;
+}
+
+extern "C" int efm_network_shape(const efm_net *net, int32_t *n_columns, int32_t *words_per_set, int32_t *n_internal)
+{
+    if (!net) return EFM_EINVAL;
+    if (n_columns) *n_columns = net->nv.N;
+    if (words_per_set) *words_per_set = net->nv.W;
+    if (n_internal) *n_internal = net->nv.M;
+    return EFM_OK;
+}
+
+extern "C" int efm_column_map(const efm_net *net, int32_t *orig_rxn, int8_t *dir)
+{
+    if (!net) return EFM_EINVAL;
+    for (int k = 0; k < net->nv.N; ++k) {
+        if (orig_rxn) orig_rxn[k] = net->col_rxn[k];
+        if (dir) dir[k] = net->col_dir[k];
+    }
+    return EFM_OK;
+}
+
+extern "C" void efm_free_net(efm_net *net)
+{
+    if (!net) return;
+    cudaStream_t s = net->stream;
+    dev_free(net->blob, s);
+    dev_free(net->metptr, s);
+    dev_free(net->metent, s);
+    cudaStreamSynchronize(s);
+    delete net;
+}
+
+namespace {
+
+// Device buffers of one traversal, reused across the targets of a job.
+struct Work {
+    DevBuf U[2], B[2], meta[2];
+    DevBuf slots, cslots, cand, res, bcnt, bfill, bptr, bidx, ctr, sortidx;
+    int64_t F_cap = 0, cand_cap = 0, res_cap = 0, bidx_cap = 0;
+    uint64_t slot_cap = 0, cslot_cap = 0, sort_cap = 0;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+void free_work(Work &w, cudaStream_t s)
+{
+    for (int i = 0; i < 2; ++i) {
+        dev_free(w.U[i], s);
+        dev_free(w.B[i], s);
+        dev_free(w.meta[i], s);
+    }
+    DevBuf *bufs[] = {&w.slots, &w.cslots, &w.cand, &w.res, &w.bcnt, &w.bfill, &w.bptr, &w.bidx, &w.ctr, &w.sortidx};
+    for (DevBuf *b : bufs) dev_free(*b, s);
+    for (auto &e : w.ev)
+        if (e) cudaEventDestroy(e);
+}
+
+int alloc_work(Work &w, const efm_net *net, const efm_limits &lim, int total_warps, cudaStream_t s)
+{
+    const NetView &nv = net->nv;
+    const int64_t default_cap = (int64_t)1 << 22;
+    w.F_cap = lim.max_frontier > 0 ? lim.max_frontier + 1 : default_cap;
+    w.cand_cap = (int64_t)1 << 20;
+    w.res_cap = w.cand_cap;
+    w.bidx_cap = w.res_cap * (int64_t)lim.max_len;
+    w.slot_cap = next_pow2(2 * (uint64_t)w.F_cap + 2 * (uint64_t)total_warps);
+    w.cslot_cap = next_pow2(2 * (uint64_t)w.cand_cap);
+    const size_t W = (size_t)nv.W, Mpad = (size_t)nv.Mpad, F = (size_t)w.F_cap;
+    bool ok = true;
+    for (int i = 0; i < 2; ++i) {
+        ok = ok && dev_alloc(w.U[i], F * W * 8, s);
+        ok = ok && dev_alloc(w.B[i], F * Mpad * 4, s);
+        ok = ok && dev_alloc(w.meta[i], F * 4, s);
+    }
+    ok = ok && dev_alloc(w.slots, w.slot_cap * 8, s);
+    ok = ok && dev_alloc(w.cslots, w.cslot_cap * 8, s);
+    ok = ok && dev_alloc(w.cand, (size_t)w.cand_cap * W * 8, s);
+    ok = ok && dev_alloc(w.res, (size_t)w.res_cap * W * 8, s);
+    ok = ok && dev_alloc(w.bcnt, (size_t)nv.N * 4, s);
+    ok = ok && dev_alloc(w.bfill, (size_t)nv.N * 4, s);
+    ok = ok && dev_alloc(w.bptr, (size_t)(nv.N + 1) * 4, s);
+    ok = ok && dev_alloc(w.bidx, (size_t)w.bidx_cap * 4, s);
+    ok = ok && dev_alloc(w.ctr, C_COUNT * 8, s);
+    for (auto &e : w.ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return EFM_ENOMEM;
+    }
+    return EFM_OK;
+}
+
+int err_from_bits(unsigned long long e)
+{
+    if (e & ERR_TIMEOUT) return EFM_ETIMEOUT;
+    if (e & (ERR_CAND_CAP | ERR_RES_CAP | ERR_TABLE_FULL)) return EFM_ECAPACITY;
+    if (e & (ERR_PRIMES | ERR_LEN)) return EFM_EUNSUPPORTED;
+    return EFM_OK;
+}
+
+#define CK(x)                         \
+    do {                              \
+        if ((x) != cudaSuccess) {     \
+            cudaGetLastError();       \
+            return EFM_ECUDA;         \
+        }                             \
+    } while (0)
+
+// One (network, target) traversal.  Level 0 = seeds; level l expands F_{l-1}.
+int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetOut &out)
+{
+    const NetView &nv = net->nv;
+    cudaStream_t s = net->stream;
+    const int grid = expand_grid(nv, net->sm_count);
+    const int total_warps = grid * kExpandWarps;
+    unsigned long long *ctr = (unsigned long long *)w.ctr.p;
+    unsigned long long h[C_COUNT];
+    efm_counters &c = out.ctr;
+    memset(&c, 0, sizeof(c));
+
+    LevelArgs a{};
+    a.slots = (unsigned long long *)w.slots.p;
+    a.cslots = (unsigned long long *)w.cslots.p;
+    a.cslot_mask = w.cslot_cap - 1;
+    a.cand = (uint64_t *)w.cand.p;
+    a.cand_cap = w.cand_cap;
+    a.res = (const uint64_t *)w.res.p;
+    a.bptr = (const int32_t *)w.bptr.p;
+    a.bidx = (const int32_t *)w.bidx.p;
+    a.max_len = lim.max_len;
+    a.max_sec = lim.max_secondary;
+    a.ctr = ctr;
+    auto arena = [&](int i) {
+        Arena r;
+        r.U = (uint64_t *)w.U[i].p;
+        r.B = (int32_t *)w.B[i].p;
+        r.meta = (uint32_t *)w.meta[i].p;
+        r.cap = w.F_cap;
+        return r;
+    };
+
+    CK(cudaMemsetAsync(ctr, 0, C_COUNT * 8, s));
+    CK(cudaMemsetAsync(w.cslots.p, 0xFF, w.cslot_cap * 8, s));
+    CK(cudaMemsetAsync(w.bptr.p, 0, (size_t)(nv.N + 1) * 4, s));
+    CK(cudaEventRecord(w.ev[0], s));
+
+    // level 0: seeds
+    int cur = 0;
+    a.level = 0;
+    a.child = arena(cur);
+    CK(launch_seed(nv, a, target, s));
+    out.kernel_launches += 1;
+    AcceptArgs acc{};
+    acc.cand = (const uint64_t *)w.cand.p;
+    acc.res = (uint64_t *)w.res.p;
+    acc.res_cap = w.res_cap;
+    acc.ctr = ctr;
+    auto read_ctr = [&]() -> int {
+        if (cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            return EFM_ECUDA;
+        }
+        return err_from_bits(h[C_ERR]);
+    };
+    int rc = read_ctr();
+    if (rc) return rc;
+    acc.cand_begin = 0;
+    acc.cand_end = (int64_t)h[C_CAND_N];
+    CK(launch_accept(nv, acc, s));
+    out.kernel_launches += acc.cand_end > acc.cand_begin ? 1 : 0;
+    if ((rc = read_ctr())) return rc;
+    int64_t cand_done = (int64_t)h[C_CAND_N];
+    int64_t res_n = (int64_t)std::min<unsigned long long>(h[C_RES_N], (unsigned long long)w.res_cap);
+    int64_t n_front = (int64_t)h[C_NEXT];
+    uint64_t deg_sum = h[C_DEGSUM];
+    int status = 0;
+    c.levels = 1;
+    bool stop = false;
+    if (lim.max_frontier > 0 && n_front > lim.max_frontier) {
+        status |= EFM_TRUNCATED;
+        stop = true;
+    } else if (n_front > w.F_cap) {
+        return EFM_ECAPACITY;
+    } else {
+        c.frontier += n_front;
+        c.frontier_max = std::max<int64_t>(c.frontier_max, n_front);
+        if (lim.max_results > 0 && (int64_t)h[C_RES] >= lim.max_results) {
+            status |= EFM_CAPPED;
+            stop = true;
+        }
+    }
+    int64_t res_prev_level_begin = 0;  // results accepted by the previous level
+    unsigned long long exp_before = 0;
+    int64_t buckets_built_for = 0;
+    float ms = 0.f;
+    for (int level = 1; !stop && n_front > 0; ++level) {
+        // buckets over every accepted result so far (all of them come from levels < `level`)
+        if (res_n != buckets_built_for) {
+            CK(launch_buckets(nv, (const uint64_t *)w.res.p, res_n, (int32_t *)w.bcnt.p, (int32_t *)w.bptr.p,
+                              (int32_t *)w.bfill.p, (int32_t *)w.bidx.p, s));
+            out.kernel_launches += res_n > 0 ? 3 : 1;
+            buckets_built_for = res_n;
+        }
+        const uint64_t bound = std::min<uint64_t>(deg_sum, (uint64_t)w.F_cap);
+        const uint64_t nslots = std::min<uint64_t>(w.slot_cap, next_pow2(2 * bound + 2 * (uint64_t)total_warps));
+        CK(cudaMemsetAsync(w.slots.p, 0xFF, nslots * 8, s));
+        CK(cudaMemsetAsync(ctr + C_NEXT, 0, 2 * 8, s));
+        a.par = arena(cur);
+        a.n_par = n_front;
+        a.child = arena(cur ^ 1);
+        a.slot_mask = nslots - 1;
+        a.level = level;
+        a.recent_begin = res_prev_level_begin;
+        a.recent_end = res_n;
+        CK(cudaEventRecord(w.ev[2], s));
+        CK(launch_expand(nv, a, grid, s));
+        CK(cudaEventRecord(w.ev[3], s));
+        if ((rc = read_ctr())) return rc;
+        CK(cudaEventElapsedTime(&ms, w.ev[2], w.ev[3]));
+        out.expand_ms += ms;
+        out.expand_launches += 1;
+        out.kernel_launches += 1;
+        {
+            const double state_bytes = 8.0 * nv.W + 4.0 * nv.M + 4.0;
+            const double n_new = (double)std::min<unsigned long long>(h[C_NEXT], (unsigned long long)w.F_cap);
+            const double n_child = (double)(h[C_EXP] - exp_before);
+            out.expand_bytes += state_bytes * ((double)n_front + n_new) + 16.0 * n_child;
+            exp_before = h[C_EXP];
+        }
+        acc.cand_begin = cand_done;
+        acc.cand_end = (int64_t)h[C_CAND_N];
+        CK(launch_accept(nv, acc, s));
+        out.kernel_launches += acc.cand_end > acc.cand_begin ? 1 : 0;
+        if ((rc = read_ctr())) return rc;
+        cand_done = (int64_t)h[C_CAND_N];
+        res_prev_level_begin = res_n;
+        res_n = (int64_t)std::min<unsigned long long>(h[C_RES_N], (unsigned long long)w.res_cap);
+        n_front = (int64_t)h[C_NEXT];
+        deg_sum = h[C_DEGSUM];
+        c.levels = level + 1;
+        cur ^= 1;
+        if (lim.max_frontier > 0 && n_front > lim.max_frontier) {
+            status |= EFM_TRUNCATED;
+            break;
+        }
+        if (n_front > w.F_cap) return EFM_ECAPACITY;
+        c.frontier += n_front;
+        c.frontier_max = std::max<int64_t>(c.frontier_max, n_front);
+        if (lim.max_results > 0 && (int64_t)h[C_RES] >= lim.max_results) {
+            status |= EFM_CAPPED;
+            break;
+        }
+    }
+    if ((int64_t)h[C_RES_N] > w.res_cap) return EFM_ECAPACITY;
+    // output: sorted by (|U|, column list), capped
+    const int64_t n_keep = lim.max_results > 0 ? std::min<int64_t>(res_n, lim.max_results) : res_n;
+    const uint64_t n2 = next_pow2((uint64_t)std::max<int64_t>(res_n, 1));
+    if (n2 > w.sort_cap) {
+        dev_free(w.sortidx, s);
+        if (!dev_alloc(w.sortidx, n2 * 4, s)) return EFM_ENOMEM;
+        w.sort_cap = n2;
+    }
+    if (!dev_alloc(out.sup, (size_t)std::max<int64_t>(n_keep, 1) * nv.W * 8, s)) return EFM_ENOMEM;
+    CK(launch_sort_results((const uint64_t *)w.res.p, res_n, nv.W, (uint32_t *)w.sortidx.p, (int64_t)n2,
+                           (uint64_t *)out.sup.p, n_keep, s));
+    if (res_n > 0 && n_keep > 0) {
+        int lg = 0;
+        while ((1ull << lg) < n2) ++lg;
+        out.kernel_launches += 2 + (int64_t)lg * (lg + 1) / 2;
+    }
+    CK(cudaEventRecord(w.ev[1], s));
+    CK(cudaEventSynchronize(w.ev[1]));
+    CK(cudaEventElapsedTime(&ms, w.ev[0], w.ev[1]));
+    out.total_ms = ms;
+    out.n = n_keep;
+    c.seeds = (int64_t)h[C_SEEDS];
+    c.expansions = (int64_t)h[C_EXP];
+    c.overflow = (int64_t)h[C_OVF];
+    c.balanced = (int64_t)h[C_BAL];
+    c.candidates = (int64_t)h[C_CAND_N];
+    c.results = (int64_t)h[C_RES];
+    c.pruned = (int64_t)h[C_PRUNED];
+    if (c.overflow) status |= EFM_OVERFLOW_DROPPED;
+    c.status = status;
+    out.status = status;
+    return EFM_OK;
+}
+
+}  // namespace
+
+extern "C" int efm_find_pathways(efm_net *net, const int32_t *targets, int32_t n_targets, const efm_limits *limits,
+                                 const void *model, efm_job **out)
+{
+    if (!out) return EFM_EINVAL;
+    *out = nullptr;
+    if (!net || !targets || n_targets <= 0 || !limits || model) return EFM_EINVAL;
+    const efm_limits lim = *limits;
+    if (lim.max_len < 1 || lim.max_len > EFM_MAX_LEN || lim.max_secondary < 0 || lim.first_k != 0 ||
+        lim.proposal != 0)
+        return EFM_EINVAL;
+    for (int i = 0; i < n_targets; ++i)
+        if (targets[i] < -1 || targets[i] >= net->n_met) return EFM_EINVAL;
+    auto *job = new (std::nothrow) efm_job();
+    if (!job) return EFM_ENOMEM;
+    job->net = net;
+    job->out.resize(n_targets);
+    Work w;
+    const int total_warps = expand_grid(net->nv, net->sm_count) * kExpandWarps;
+    int rc = alloc_work(w, net, lim, total_warps, net->stream);
+    int flags = 0;
+    for (int i = 0; rc == EFM_OK && i < n_targets; ++i) {
+        rc = run_target(net, w, lim, targets[i], job->out[i]);
+        flags |= job->out[i].status;
+    }
+    free_work(w, net->stream);
+    if (cudaStreamSynchronize(net->stream) != cudaSuccess && rc == EFM_OK) rc = EFM_ECUDA;
+    if (rc != EFM_OK) {
+        cudaGetLastError();
+        efm_free_job(job);
+        return rc;
+    }
+    *out = job;
+    return flags;
+}
+
+extern "C" int efm_fetch_results(efm_job *job, int32_t idx, uint64_t *supports, int64_t capacity, int64_t *n_out,
+                                 int32_t *words_per_set, efm_counters *ctr)
+{
+    if (!job || idx < 0 || idx >= (int32_t)job->out.size()) return EFM_EINVAL;
+    TargetOut &o = job->out[idx];
+    const int W = job->net->nv.W;
+    if (n_out) *n_out = o.n;
+    if (words_per_set) *words_per_set = W;
+    if (ctr) *ctr = o.ctr;
+    if (!supports) return o.status;
+    if (capacity < o.n) return EFM_ECAPACITY;
+    if (o.n > 0) {
+        if (cudaMemcpyAsync(supports, o.sup.p, (size_t)o.n * W * 8, cudaMemcpyDeviceToHost, job->net->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(job->net->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return EFM_ECUDA;
+        }
+    }
+    return o.status;
+}
+
+extern "C" int efm_job_timing(const efm_job *job, int32_t idx, double *total_ms, double *expand_ms,
+                              int64_t *expand_launches, double *expand_bytes, int64_t *kernel_launches)
+{
+    if (!job || idx < 0 || idx >= (int32_t)job->out.size()) return EFM_EINVAL;
+    const TargetOut &o = job->out[idx];
+    if (total_ms) *total_ms = o.total_ms;
+    if (expand_ms) *expand_ms = o.expand_ms;
+    if (expand_launches) *expand_launches = o.expand_launches;
+    if (expand_bytes) *expand_bytes = o.expand_bytes;
+    if (kernel_launches) *kernel_launches = o.kernel_launches;
+    return EFM_OK;
+}
+
+extern "C" void efm_free_job(efm_job *job)
+{
+    if (!job) return;
+    cudaStream_t s = job->net ? job->net->stream : nullptr;
+    for (auto &o : job->out) dev_free(o.sup, s);
+    cudaStreamSynchronize(s);
+    delete job;
+}

@@ -1,0 +1,102 @@
+// efm_internal.cuh -- shared declarations of the CUDA path (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/efmgraph.h"
+
+namespace efm {
+
+constexpr int kMaxW = 64;           // support words (EFM_MAX_COLUMNS / 64)
+constexpr int kExpandWarps = 8;     // warps per CTA of the expansion kernel
+constexpr int kAcceptWarps = 4;     // warps per CTA of the minimality kernel
+constexpr unsigned long long kEmpty = ~0ull;
+constexpr uint32_t kPending = 0xFFFFFFFFu;
+constexpr uint32_t kOverflowIdx = 0xFFFFFFFEu;
+constexpr int kNumPrimes = 24;
+constexpr int kStageLimitBytes = 96 * 1024;  // static network staged in smem up to this size
+
+// device error bits (ctr[C_ERR])
+enum : unsigned { ERR_TIMEOUT = 1u, ERR_CAND_CAP = 2u, ERR_RES_CAP = 4u, ERR_TABLE_FULL = 8u,
+                  ERR_PRIMES = 16u, ERR_LEN = 32u };
+
+// device counter block (unsigned long long each)
+enum {
+    C_LEVELS = 0, C_SEEDS, C_EXP, C_OVF, C_BAL, C_CAND, C_RES, C_PRUNED, C_FRONTIER, C_FRONTIER_MAX, C_STATUS,
+    C_NEXT = 12,  // states allocated in the arena being written
+    C_DEGSUM,     // sum of pivot degrees of the states written (children bound of the next level)
+    C_CAND_N,     // candidate list length (cumulative)
+    C_RES_N,      // result list length (cumulative)
+    C_ERR,        // ERR_* bits
+    C_COUNT = 32
+};
+
+// Static network, packed into one 16-byte aligned word array (the "blob").
+// Packed entry: (index << 20) | (coefficient & 0xFFFFF), index < 4096,
+// coefficient a signed 20-bit value.
+struct NetView {
+    const uint32_t *blob;  // device
+    int blob_words;        // multiple of 4
+    int M, N, W, Mpad, EPL;
+    int o_colptr, o_colent;    // S_int by column: rows with coefficients
+    int o_consptr, o_consent;  // per internal row: consuming columns, |coef|
+    int o_prodptr, o_prodent;  // per internal row: producing columns, |coef|
+    int o_twin;                // per column: twin column or -1 (as int32)
+    int o_keypos, o_keyneg;    // per internal row: (degree << 16) | row
+    int o_hbits;               // per column: ceil(log2(|S_int[:,k]|^2))
+    const int32_t *metptr;     // full S rows over split columns (seeds), [n_met + 1]
+    const uint32_t *metent;    // packed (column, coefficient)
+    int n_met;
+};
+
+__host__ __device__ inline int ent_index(uint32_t e) { return (int)(e >> 20); }
+__host__ __device__ inline int32_t ent_coef(uint32_t e) { return ((int32_t)(e << 12)) >> 12; }
+__host__ inline uint32_t ent_pack(int idx, int32_t coef) {
+    return ((uint32_t)idx << 20) | ((uint32_t)coef & 0xFFFFFu);
+}
+
+// One arena of pathway states, structure of arrays.
+struct Arena {
+    uint64_t *U;     // [cap][W]
+    int32_t *B;      // [cap][Mpad]
+    uint32_t *meta;  // [cap]: (pivot degree << 16) | pivot row
+    int64_t cap;
+};
+
+struct LevelArgs {
+    Arena par;
+    int64_t n_par;
+    Arena child;
+    unsigned long long *slots;  // state hash table
+    uint64_t slot_mask;
+    unsigned long long *cslots; // balanced-support hash table
+    uint64_t cslot_mask;
+    uint64_t *cand;             // [cand_cap][W]
+    int64_t cand_cap;
+    const uint64_t *res;        // [res_cap][W]
+    const int32_t *bptr;        // [N + 1] result buckets by column
+    const int32_t *bidx;
+    int64_t recent_begin, recent_end;  // results of the previous level
+    int level, max_len, max_sec;
+    unsigned long long *ctr;
+};
+
+struct AcceptArgs {
+    const uint64_t *cand;
+    int64_t cand_begin, cand_end;
+    uint64_t *res;
+    int64_t res_cap;
+    unsigned long long *ctr;
+};
+
+// kernels (efm_kernels.cu)
+cudaError_t launch_seed(const NetView &nv, const LevelArgs &a, int target, cudaStream_t s);
+cudaError_t launch_expand(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_accept(const NetView &nv, const AcceptArgs &a, cudaStream_t s);
+cudaError_t launch_buckets(const NetView &nv, const uint64_t *res, int64_t n_res, int32_t *bcnt, int32_t *bptr,
+                           int32_t *bfill, int32_t *bidx, cudaStream_t s);
+cudaError_t launch_sort_results(const uint64_t *res, int64_t n, int W, uint32_t *idx, int64_t n_pow2,
+                                uint64_t *out, int64_t n_keep, cudaStream_t s);
+int expand_grid(const NetView &nv, int sm_count);
+
+}  // namespace efm

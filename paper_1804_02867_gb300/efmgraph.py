@@ -1,0 +1,265 @@
+"""Thin ctypes binding over the C-ABI in include/efmgraph.h.
+
+Argument marshalling only: every step of the traversal runs in the CUDA
+kernels of libefmgraph.so.  Importing this module on a machine without the
+built library raises -- there is no CPU fallback.
+
+The C functions are exposed under their C names (efm_load_network, ...);
+`Network` and `enumerate_targets` are conveniences that call exactly those.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+EFM_TRUNCATED, EFM_CAPPED, EFM_OVERFLOW_DROPPED = 1, 2, 4
+COUNTER_FIELDS = ("levels", "seeds", "expansions", "overflow", "balanced", "candidates", "results", "pruned",
+                  "frontier", "frontier_max", "status")
+EXPORTS = ("efm_load_network", "efm_network_shape", "efm_column_map", "efm_find_pathways", "efm_fetch_results",
+           "efm_job_timing", "efm_free_job", "efm_free_net", "efm_status_str", "efm_set_allocator")
+
+
+class efm_limits(ctypes.Structure):
+    _fields_ = [("max_len", ctypes.c_int32), ("max_secondary", ctypes.c_int32), ("max_results", ctypes.c_int64),
+                ("max_frontier", ctypes.c_int64), ("first_k", ctypes.c_int32), ("proposal", ctypes.c_int32)]
+
+
+class efm_counters(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in COUNTER_FIELDS]
+
+
+class EfmError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {status_str(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+_P = ctypes.POINTER
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(path: str | None = None):
+    """Load libefmgraph.so (built in-tree by build.build()).  Raises if the
+    library is missing: the product path has no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"{path} not built; run paper_1804_02867_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    lib.efm_load_network.argtypes = [ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_int32), _P(ctypes.c_int32),
+                                     _P(ctypes.c_int32), _P(ctypes.c_uint8), _P(ctypes.c_uint8), ctypes.c_size_t,
+                                     _P(ctypes.c_void_p)]
+    lib.efm_load_network.restype = ctypes.c_int
+    lib.efm_network_shape.argtypes = [ctypes.c_void_p, _P(ctypes.c_int32), _P(ctypes.c_int32), _P(ctypes.c_int32)]
+    lib.efm_network_shape.restype = ctypes.c_int
+    lib.efm_column_map.argtypes = [ctypes.c_void_p, _P(ctypes.c_int32), _P(ctypes.c_int8)]
+    lib.efm_column_map.restype = ctypes.c_int
+    lib.efm_find_pathways.argtypes = [ctypes.c_void_p, _P(ctypes.c_int32), ctypes.c_int32, _P(efm_limits),
+                                      ctypes.c_void_p, _P(ctypes.c_void_p)]
+    lib.efm_find_pathways.restype = ctypes.c_int
+    lib.efm_fetch_results.argtypes = [ctypes.c_void_p, ctypes.c_int32, _P(ctypes.c_uint64), ctypes.c_int64,
+                                      _P(ctypes.c_int64), _P(ctypes.c_int32), _P(efm_counters)]
+    lib.efm_fetch_results.restype = ctypes.c_int
+    lib.efm_job_timing.argtypes = [ctypes.c_void_p, ctypes.c_int32, _P(ctypes.c_double), _P(ctypes.c_double),
+                                   _P(ctypes.c_int64), _P(ctypes.c_double), _P(ctypes.c_int64)]
+    lib.efm_job_timing.restype = ctypes.c_int
+    lib.efm_free_job.argtypes = [ctypes.c_void_p]
+    lib.efm_free_job.restype = None
+    lib.efm_free_net.argtypes = [ctypes.c_void_p]
+    lib.efm_free_net.restype = None
+    lib.efm_status_str.argtypes = [ctypes.c_int]
+    lib.efm_status_str.restype = ctypes.c_char_p
+    lib.efm_set_allocator.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.efm_set_allocator.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def status_str(code: int) -> str:
+    return load_library().efm_status_str(int(code)).decode()
+
+
+def _arr(a, dt, ct):
+    a = np.ascontiguousarray(a, dtype=dt)
+    return a, a.ctypes.data_as(_P(ct))
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+# --- C-ABI calls under their C names ---------------------------------------
+
+def efm_load_network(n_met, n_rxn, row_ptr, col_idx, coef, reversible, external, stream=None) -> int:
+    lib = load_library()
+    rp, prp = _arr(row_ptr, np.int32, ctypes.c_int32)
+    ci, pci = _arr(col_idx, np.int32, ctypes.c_int32)
+    cf, pcf = _arr(coef, np.int32, ctypes.c_int32)
+    rv, prv = _arr(reversible, np.uint8, ctypes.c_uint8)
+    ex, pex = _arr(external, np.uint8, ctypes.c_uint8)
+    h = ctypes.c_void_p()
+    rc = lib.efm_load_network(int(n_met), int(n_rxn), prp, pci, pcf, prv, pex, _stream_handle(stream),
+                              ctypes.byref(h))
+    if rc != 0:
+        raise EfmError(rc, "efm_load_network")
+    return h.value
+
+
+def efm_network_shape(net) -> tuple:
+    n, w, m = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    rc = load_library().efm_network_shape(net, ctypes.byref(n), ctypes.byref(w), ctypes.byref(m))
+    if rc != 0:
+        raise EfmError(rc, "efm_network_shape")
+    return n.value, w.value, m.value
+
+
+def efm_column_map(net):
+    n, _, _ = efm_network_shape(net)
+    rx = np.zeros(n, dtype=np.int32)
+    d = np.zeros(n, dtype=np.int8)
+    rc = load_library().efm_column_map(net, rx.ctypes.data_as(_P(ctypes.c_int32)), d.ctypes.data_as(_P(ctypes.c_int8)))
+    if rc != 0:
+        raise EfmError(rc, "efm_column_map")
+    return rx, d
+
+
+def efm_find_pathways(net, targets, max_len, max_secondary, max_results=0, max_frontier=0):
+    """Returns (job handle, warning flags)."""
+    tg, ptg = _arr(targets, np.int32, ctypes.c_int32)
+    lim = efm_limits(int(max_len), int(max_secondary), int(max_results), int(max_frontier), 0, 0)
+    job = ctypes.c_void_p()
+    rc = load_library().efm_find_pathways(net, ptg, len(tg), ctypes.byref(lim), None, ctypes.byref(job))
+    if rc < 0:
+        raise EfmError(rc, "efm_find_pathways")
+    return job.value, rc
+
+
+def efm_fetch_results(job, idx, copy=True, out=None):
+    """Returns (supports uint64[n, W] or None if copy is False, counters
+    dict, flags).  `out` may supply the host buffer (e.g. pinned memory)."""
+    lib = load_library()
+    n = ctypes.c_int64()
+    w = ctypes.c_int32()
+    ctr = efm_counters()
+    rc = lib.efm_fetch_results(job, int(idx), None, 0, ctypes.byref(n), ctypes.byref(w), ctypes.byref(ctr))
+    if rc < 0:
+        raise EfmError(rc, "efm_fetch_results")
+    counters = {f: int(getattr(ctr, f)) for f in COUNTER_FIELDS}
+    if not copy:
+        return None, counters, rc
+    if out is None or out.shape[0] < n.value or out.dtype != np.uint64 or not out.flags.c_contiguous:
+        out = np.zeros((n.value, w.value), dtype=np.uint64)
+    else:
+        out = out[:n.value]
+    rc = lib.efm_fetch_results(job, int(idx), out.ctypes.data_as(_P(ctypes.c_uint64)), n.value, ctypes.byref(n),
+                               None, None)
+    if rc < 0:
+        raise EfmError(rc, "efm_fetch_results")
+    return out, counters, rc
+
+
+def efm_job_timing(job, idx):
+    """Returns dict(total_ms, expand_ms, expand_launches, expand_bytes, kernel_launches)."""
+    t, e, n, b, k = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_int64()
+    rc = load_library().efm_job_timing(job, int(idx), ctypes.byref(t), ctypes.byref(e), ctypes.byref(n),
+                                       ctypes.byref(b), ctypes.byref(k))
+    if rc != 0:
+        raise EfmError(rc, "efm_job_timing")
+    return dict(total_ms=t.value, expand_ms=e.value, expand_launches=n.value, expand_bytes=b.value,
+                kernel_launches=k.value)
+
+
+def efm_free_job(job):
+    if job:
+        load_library().efm_free_job(job)
+
+
+def efm_free_net(net):
+    if net:
+        load_library().efm_free_net(net)
+
+
+# --- PyTorch caching allocator as the library's device allocator -------------
+
+_ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_void_p)
+_keep = []
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through torch's caching
+    allocator (so the library shares the PyTorch memory pool)."""
+    import torch
+
+    dev = torch.cuda.current_device()
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(stream))
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = _ALLOC_T(_alloc), _FREE_T(_free)
+    _keep[:] = [a, f]
+    rc = load_library().efm_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), None)
+    if rc != 0:
+        raise EfmError(rc, "efm_set_allocator")
+
+
+# --- conveniences ------------------------------------------------------------
+
+class Network:
+    """A loaded network (owns the C handle)."""
+
+    def __init__(self, net, stream=None):
+        self.src = net
+        self.handle = efm_load_network(net.n_met, net.n_rxn, net.row_ptr, net.col_idx, net.coef, net.reversible,
+                                       net.external, stream)
+        self.n_columns, self.words, self.n_internal = efm_network_shape(self.handle)
+
+    def close(self):
+        efm_free_net(self.handle)
+        self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def enumerate_targets(network: Network, targets, max_len, max_secondary, max_results=0, max_frontier=0,
+                      timing=False):
+    """Run efm_find_pathways over `targets` and fetch every target's result.
+    Returns a list of (supports, counters[, timing dict])."""
+    job, _ = efm_find_pathways(network.handle, list(targets), max_len, max_secondary, max_results, max_frontier)
+    try:
+        out = []
+        for i in range(len(targets)):
+            sup, ctr, _ = efm_fetch_results(job, i)
+            if timing:
+                out.append((sup, ctr, efm_job_timing(job, i)))
+            else:
+                out.append((sup, ctr))
+        return out
+    finally:
+        efm_free_job(job)
