@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--budget", type=int, default=BUDGET)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--targets", type=str, default="",
+                    help="comma-separated positions among the 8 targets (profiling a smaller case)")
     return ap.parse_args()
 
 
@@ -207,6 +209,8 @@ def run_ours(args):
     efmgraph.load_library()
     net = synth.core()
     targets = list(net.targets)
+    if args.targets:
+        targets = [targets[int(i)] for i in args.targets.split(",")]
     stream = torch.cuda.current_stream()
     budget = args.budget
 
