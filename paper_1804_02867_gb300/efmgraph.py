@@ -20,7 +20,9 @@ EFM_TRUNCATED, EFM_CAPPED, EFM_OVERFLOW_DROPPED = 1, 2, 4
 COUNTER_FIELDS = ("levels", "seeds", "expansions", "overflow", "balanced", "candidates", "results", "pruned",
                   "frontier", "frontier_max", "status")
 EXPORTS = ("efm_load_network", "efm_network_shape", "efm_column_map", "efm_find_pathways", "efm_fetch_results",
-           "efm_job_timing", "efm_free_job", "efm_free_net", "efm_status_str", "efm_set_allocator")
+           "efm_job_timing", "efm_free_job", "efm_free_net", "efm_status_str", "efm_set_allocator",
+           "efm_sort_supports_noalloc")
+EFM_NOALLOC_MAX_ROWS = 1 << 20
 
 
 class efm_limits(ctypes.Structure):
@@ -81,6 +83,9 @@ def load_library(path: str | None = None):
     lib.efm_status_str.restype = ctypes.c_char_p
     lib.efm_set_allocator.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.efm_set_allocator.restype = ctypes.c_int
+    lib.efm_sort_supports_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                                              ctypes.c_size_t]
+    lib.efm_sort_supports_noalloc.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -193,6 +198,12 @@ def efm_free_job(job):
 def efm_free_net(net):
     if net:
         load_library().efm_free_net(net)
+
+
+def efm_sort_supports_noalloc(supports_in_ptr, n_rows, words_per_set, supports_out_ptr, stream=None) -> int:
+    """Device pointers in and out (caller-owned); returns the status code."""
+    return load_library().efm_sort_supports_noalloc(int(supports_in_ptr), int(n_rows), int(words_per_set),
+                                                    int(supports_out_ptr), _stream_handle(stream))
 
 
 # --- PyTorch caching allocator as the library's device allocator -------------
