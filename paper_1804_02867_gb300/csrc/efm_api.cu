@@ -3,6 +3,8 @@
 // kernels of efm_kernels.cu; this file only prepares static data, sizes
 // buffers, launches and reads back one counter block per level.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -228,6 +230,11 @@ extern "C" int efm_load_network(int32_t n_met, int32_t n_rxn, const int32_t *row
     nv.o_hbits = (int)blob.size();
     for (int k = 0; k < N; ++k) blob.push_back(hbits[k]);
     while (blob.size() % 4) blob.push_back(0);
+    // dense column-major copy of S_int (row k = column k over Mpad rows)
+    nv.o_dcols = (int)blob.size();
+    blob.resize(blob.size() + (size_t)N * 32 * EPL, 0u);
+    for (int k = 0; k < N; ++k)
+        for (auto &e : col[k]) blob[(size_t)nv.o_dcols + (size_t)k * 32 * EPL + e.first] = (uint32_t)e.second;
     std::vector<int32_t> mptr(n_met + 1, 0);
     std::vector<uint32_t> ment;
     for (int m = 0; m < n_met; ++m) {
@@ -345,7 +352,7 @@ int alloc_work(Work &w, const efm_net *net, const efm_limits &lim, int total_war
     w.cand_cap = (int64_t)1 << 20;
     w.res_cap = w.cand_cap;
     w.bidx_cap = w.res_cap * (int64_t)lim.max_len;
-    w.slot_cap = next_pow2(2 * (uint64_t)w.F_cap + 2 * (uint64_t)total_warps);
+    w.slot_cap = next_pow2(2 * (uint64_t)w.F_cap + 64 * (uint64_t)total_warps);
     w.cslot_cap = next_pow2(2 * (uint64_t)w.cand_cap);
     const size_t W = (size_t)nv.W, Mpad = (size_t)nv.Mpad, F = (size_t)w.F_cap;
     bool ok = true;
@@ -373,7 +380,8 @@ int alloc_work(Work &w, const efm_net *net, const efm_limits &lim, int total_war
 
 int err_from_bits(unsigned long long e)
 {
-    if (e & ERR_TIMEOUT) return EFM_ETIMEOUT;
+    if (e & (ERR_TIMEOUT | ERR_WATCHDOG)) return EFM_ETIMEOUT;
+    if (e & ERR_BOUNDS) return EFM_ECUDA;
     if (e & (ERR_CAND_CAP | ERR_RES_CAP | ERR_TABLE_FULL)) return EFM_ECAPACITY;
     if (e & (ERR_PRIMES | ERR_LEN)) return EFM_EUNSUPPORTED;
     return EFM_OK;
@@ -442,7 +450,12 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
             cudaGetLastError();
             return EFM_ECUDA;
         }
-        return err_from_bits(h[C_ERR]);
+        const int e = err_from_bits(h[C_ERR]);
+        if (e != EFM_OK && getenv("EFM_DEBUG"))
+            fprintf(stderr, "efm: device error bits %llx diag code %llu value %lld limit %lld level %lld\n",
+                    h[C_ERR], h[C_DIAG], (long long)h[C_DIAG + 1], (long long)h[C_DIAG + 2],
+                    (long long)h[C_DIAG + 3]);
+        return e;
     };
     int rc = read_ctr();
     if (rc) return rc;
@@ -476,6 +489,8 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
     int64_t buckets_built_for = 0;
     float ms = 0.f;
     for (int level = 1; !stop && n_front > 0; ++level) {
+        // every step adds a column or a secondary step, so depth is bounded
+        if (level > lim.max_len + lim.max_secondary + 1) return EFM_ETIMEOUT;
         // buckets over every accepted result so far (all of them come from levels < `level`)
         if (res_n != buckets_built_for) {
             CK(launch_buckets(nv, (const uint64_t *)w.res.p, res_n, (int32_t *)w.bcnt.p, (int32_t *)w.bptr.p,
@@ -484,7 +499,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
             buckets_built_for = res_n;
         }
         const uint64_t bound = std::min<uint64_t>(deg_sum, (uint64_t)w.F_cap);
-        const uint64_t nslots = std::min<uint64_t>(w.slot_cap, next_pow2(2 * bound + 2 * (uint64_t)total_warps));
+        const uint64_t nslots = std::min<uint64_t>(w.slot_cap, next_pow2(2 * bound + 64 * (uint64_t)total_warps));
         CK(cudaMemsetAsync(w.slots.p, 0xFF, nslots * 8, s));
         CK(cudaMemsetAsync(ctr + C_NEXT, 0, 2 * 8, s));
         a.par = arena(cur);

@@ -14,11 +14,11 @@ constexpr unsigned long long kEmpty = ~0ull;
 constexpr uint32_t kPending = 0xFFFFFFFFu;
 constexpr uint32_t kOverflowIdx = 0xFFFFFFFEu;
 constexpr int kNumPrimes = 24;
-constexpr int kStageLimitBytes = 96 * 1024;  // static network staged in smem up to this size
+constexpr int kStageLimitBytes = 72 * 1024;  // static network staged in smem up to this size
 
 // device error bits (ctr[C_ERR])
 enum : unsigned { ERR_TIMEOUT = 1u, ERR_CAND_CAP = 2u, ERR_RES_CAP = 4u, ERR_TABLE_FULL = 8u,
-                  ERR_PRIMES = 16u, ERR_LEN = 32u };
+                  ERR_PRIMES = 16u, ERR_LEN = 32u, ERR_WATCHDOG = 64u, ERR_BOUNDS = 128u };
 
 // device counter block (unsigned long long each)
 enum {
@@ -28,6 +28,7 @@ enum {
     C_CAND_N,     // candidate list length (cumulative)
     C_RES_N,      // result list length (cumulative)
     C_ERR,        // ERR_* bits
+    C_DIAG = 24,  // first bounds/watchdog record: code, value, limit, level
     C_COUNT = 32
 };
 
@@ -44,6 +45,7 @@ struct NetView {
     int o_twin;                // per column: twin column or -1 (as int32)
     int o_keypos, o_keyneg;    // per internal row: (degree << 16) | row
     int o_hbits;               // per column: ceil(log2(|S_int[:,k]|^2))
+    int o_dcols;               // dense S_int by column: N rows of Mpad int32 (16-byte aligned)
     const int32_t *metptr;     // full S rows over split columns (seeds), [n_met + 1]
     const uint32_t *metent;    // packed (column, coefficient)
     int n_met;
@@ -59,7 +61,7 @@ __host__ inline uint32_t ent_pack(int idx, int32_t coef) {
 struct Arena {
     uint64_t *U;     // [cap][W]
     int32_t *B;      // [cap][Mpad]
-    uint32_t *meta;  // [cap]: (pivot degree << 16) | pivot row
+    uint32_t *meta;  // [cap]: pivot row | pivot degree << 10 | |U| << 23
     int64_t cap;
 };
 

@@ -20,10 +20,13 @@
 // tested by Gaussian elimination modulo primes p = 2^31 - c, with enough
 // primes that their product exceeds the Hadamard bound of the columns.
 //
-// Layout: one warp owns one parent pathway; lane l holds balance entries
-// l, l + 32, ... (EPL per lane) and support words l, l + 32.  The static
-// network (CSR by column and by metabolite, twins, pivot keys) is staged
-// into shared memory with one bulk async copy (no multicast) when it fits.
+// Layout: a frontier is an arena of states, each a row of W support words,
+// a row of Mpad int32 extra-flux entries (16-byte aligned) and a meta word
+// (acting metabolite, its degree, |U|).  The expansion gives every lane its
+// own child; the seed and minimality kernels give a warp one item.  The
+// static network (CSR by column and by metabolite, twins, pivot keys) is
+// staged into shared memory with one bulk async copy (no multicast) when it
+// fits.
 #include "efm_internal.cuh"
 
 namespace efm {
@@ -86,21 +89,34 @@ __device__ __forceinline__ uint32_t gcd32(uint32_t a, uint32_t b)
 
 __device__ __forceinline__ uint64_t abs64(int64_t x) { return x < 0 ? (uint64_t)(-x) : (uint64_t)x; }
 
-template <int EPL>
-__device__ __forceinline__ int32_t pick(const int32_t (&v)[EPL], int i)
-{
-    int32_t r = v[0];
-#pragma unroll
-    for (int e = 1; e < EPL; ++e)
-        if (i == e) r = v[e];
-    return r;
-}
-
 __device__ __forceinline__ bool bit_of(const uint64_t *U, int k) { return (U[k >> 6] >> (k & 63)) & 1ull; }
 
 __device__ __forceinline__ unsigned long long load_volatile(unsigned long long *p)
 {
     return *(volatile unsigned long long *)p;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr uint64_t kWatchdogNs = 20ull * 1000000000ull;  // a level that runs longer gives up
+constexpr int kMaxRounds = 1 << 22;
+
+// Record the first failed self-check (code, offending value, its limit) and
+// raise the error bit; the caller skips the access.
+__device__ void record_diag(unsigned long long *ctr, unsigned bit, unsigned long long code, long long value,
+                            long long limit, int level)
+{
+    atomicOr(&ctr[C_ERR], (unsigned long long)bit);
+    if (atomicCAS(&ctr[C_DIAG], 0ull, code) == 0ull) {
+        ctr[C_DIAG + 1] = (unsigned long long)value;
+        ctr[C_DIAG + 2] = (unsigned long long)limit;
+        ctr[C_DIAG + 3] = (unsigned long long)level;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -155,24 +171,16 @@ __device__ const uint32_t *stage_blob(const NetView &nv, uint32_t *sblob, uint64
 }
 
 // ---------------------------------------------------------------------------
-// warp-cooperative hash sets
+// hash sets (publish-after-write slots)
+//
+// A slot is one 64-bit word: (tag << 32) | index.  An inserter claims an
+// empty slot with CAS as (tag, PENDING), writes the record, fences, then
+// publishes the index.  A prober whose tag matches waits (bounded) for the
+// index and compares the full record; records are never compared by tag
+// alone, so the set is exact.
 // ---------------------------------------------------------------------------
 
 enum { INS_NEW = 1, INS_DUP = 0, INS_ARENA_FULL = -1, INS_TIMEOUT = -2, INS_TABLE_FULL = -3 };
-
-// Spin until the slot's index is published.  Returns the slot value or
-// kEmpty on timeout.
-__device__ __forceinline__ unsigned long long wait_published(unsigned long long *slot, unsigned long long v, int lane)
-{
-    int spins = 0;
-    while ((uint32_t)v == kPending) {
-        if (++spins > kSpinLimit) return kEmpty;
-        __nanosleep(64);
-        if (lane == 0) v = load_volatile(slot);
-        v = __shfl_sync(FULL, v, 0);
-    }
-    return v;
-}
 
 __device__ __forceinline__ void slot_tag_pos(uint64_t h, uint64_t mask, uint64_t &pos, uint32_t &tag)
 {
@@ -182,171 +190,69 @@ __device__ __forceinline__ void slot_tag_pos(uint64_t h, uint64_t mask, uint64_t
     if (tag == 0xFFFFFFFFu) tag = 0xFFFFFFFEu;
 }
 
-// Insert a support set (balanced pathway) into the candidate set.
-// Lane l holds words l and l + 32 of U in u0 / u1.
-__device__ int insert_support(const LevelArgs &a, int W, uint64_t u0, uint64_t u1, int lane)
+// word w of the support U' = U (pu, or empty if null) plus column k
+__device__ __forceinline__ uint64_t child_word(const uint64_t *pu, int w, int k)
+{
+    uint64_t x = pu ? pu[w] : 0ull;
+    if (w == (k >> 6)) x |= 1ull << (k & 63);
+    return x;
+}
+
+// Insert the support U' = U + {k} of a balanced pathway into the set of
+// supports judged in this traversal (one thread).
+__device__ int insert_support(const LevelArgs &a, int W, const uint64_t *pu, int k)
 {
     uint64_t h = 0;
-    if (lane < W) h += mix64(u0 ^ (0x51ed27f3a5b1c3d9ull * (uint64_t)(lane + 1)));
-    if (lane + 32 < W) h += mix64(u1 ^ (0x51ed27f3a5b1c3d9ull * (uint64_t)(lane + 33)));
-    const uint32_t lo = __reduce_add_sync(FULL, (uint32_t)h);
-    const uint32_t hi = __reduce_add_sync(FULL, (uint32_t)(h >> 32));
+    for (int w = 0; w < W; ++w) h += mix64(child_word(pu, w, k) ^ (0x51ed27f3a5b1c3d9ull * (uint64_t)(w + 1)));
     uint64_t pos;
     uint32_t tag;
-    slot_tag_pos(((uint64_t)hi << 32) | lo, a.cslot_mask, pos, tag);
+    slot_tag_pos(h, a.cslot_mask, pos, tag);
     for (uint64_t probe = 0; probe <= a.cslot_mask; ++probe) {
-        unsigned long long v = 0;
-        if (lane == 0) v = atomicCAS(&a.cslots[pos], kEmpty, ((unsigned long long)tag << 32) | kPending);
-        v = __shfl_sync(FULL, v, 0);
+        unsigned long long v = atomicCAS(&a.cslots[pos], kEmpty, ((unsigned long long)tag << 32) | kPending);
         if (v == kEmpty) {
-            unsigned long long idx = 0;
-            if (lane == 0) idx = atomicAdd(&a.ctr[C_CAND_N], 1ull);
-            idx = __shfl_sync(FULL, idx, 0);
+            const unsigned long long idx = atomicAdd(&a.ctr[C_CAND_N], 1ull);
             if ((int64_t)idx >= a.cand_cap) {
-                if (lane == 0) {
-                    atomicOr(&a.ctr[C_ERR], (unsigned long long)ERR_CAND_CAP);
-                    atomicExch(&a.cslots[pos], ((unsigned long long)tag << 32) | kOverflowIdx);
-                }
+                atomicOr(&a.ctr[C_ERR], (unsigned long long)ERR_CAND_CAP);
+                atomicExch(&a.cslots[pos], ((unsigned long long)tag << 32) | kOverflowIdx);
                 return INS_ARENA_FULL;
             }
             uint64_t *dst = a.cand + (size_t)idx * W;
-            if (lane < W) dst[lane] = u0;
-            if (lane + 32 < W) dst[lane + 32] = u1;
+            for (int w = 0; w < W; ++w) dst[w] = child_word(pu, w, k);
             __threadfence();
-            __syncwarp();
-            if (lane == 0) atomicExch(&a.cslots[pos], ((unsigned long long)tag << 32) | idx);
+            atomicExch(&a.cslots[pos], ((unsigned long long)tag << 32) | idx);
             return INS_NEW;
         }
         if ((uint32_t)(v >> 32) == tag) {
-            v = wait_published(&a.cslots[pos], v, lane);
-            if (v == kEmpty) {
-                if (lane == 0) atomicOr(&a.ctr[C_ERR], (unsigned long long)ERR_TIMEOUT);
-                return INS_TIMEOUT;
+            int spins = 0;
+            while ((uint32_t)v == kPending) {
+                if (++spins > kSpinLimit) {
+                    atomicOr(&a.ctr[C_ERR], (unsigned long long)ERR_TIMEOUT);
+                    return INS_TIMEOUT;
+                }
+                __nanosleep(64);
+                v = load_volatile(&a.cslots[pos]);
             }
             const uint32_t idx = (uint32_t)v;
             if (idx == kOverflowIdx) return INS_ARENA_FULL;
-            __threadfence();
             const uint64_t *src = a.cand + (size_t)idx * W;
             bool eq = true;
-            if (lane < W) eq = __ldcg(src + lane) == u0;
-            if (lane + 32 < W) eq = eq && (__ldcg(src + lane + 32) == u1);
-            if (__all_sync(FULL, eq)) return INS_DUP;
+            for (int w = 0; w < W && eq; ++w) eq = __ldcg(src + w) == child_word(pu, w, k);
+            if (eq) return INS_DUP;
         }
         pos = (pos + 1) & a.cslot_mask;
     }
-    if (lane == 0) atomicOr(&a.ctr[C_ERR], (unsigned long long)ERR_TABLE_FULL);
+    atomicOr(&a.ctr[C_ERR], (unsigned long long)ERR_TABLE_FULL);
     return INS_TABLE_FULL;
 }
 
-// Insert a pathway state (support + normalised extra flux) into the level's
-// hash table; a new state is written into the child arena before its slot
-// is published.
-template <int EPL>
-__device__ int insert_state(const LevelArgs &a, int W, int Mpad, uint64_t u0, uint64_t u1, const int32_t (&t)[EPL],
-                            uint32_t meta, int lane)
+// pivot key (degree << 16 | row) -> state meta: row | degree << 10 | |U| << 23
+__device__ __forceinline__ uint32_t pack_meta(uint32_t key, int pc)
 {
-    uint64_t h = 0;
-    if (lane < W) h += mix64(u0 ^ (0x2545f4914f6cdd1dull * (uint64_t)(lane + 1)));
-    if (lane + 32 < W) h += mix64(u1 ^ (0x2545f4914f6cdd1dull * (uint64_t)(lane + 33)));
-#pragma unroll
-    for (int e = 0; e < EPL; ++e)
-        if (t[e] != 0) h += mix64(((uint64_t)(uint32_t)(lane + 32 * e) << 32) | (uint32_t)t[e]);
-    const uint32_t lo = __reduce_add_sync(FULL, (uint32_t)h);
-    const uint32_t hi = __reduce_add_sync(FULL, (uint32_t)(h >> 32));
-    uint64_t pos;
-    uint32_t tag;
-    slot_tag_pos(((uint64_t)hi << 32) | lo, a.slot_mask, pos, tag);
-    for (uint64_t probe = 0; probe <= a.slot_mask; ++probe) {
-        unsigned long long v = 0;
-        if (lane == 0) v = atomicCAS(&a.slots[pos], kEmpty, ((unsigned long long)tag << 32) | kPending);
-        v = __shfl_sync(FULL, v, 0);
-        if (v == kEmpty) {
-            unsigned long long idx = 0;
-            if (lane == 0) idx = atomicAdd(&a.ctr[C_NEXT], 1ull);
-            idx = __shfl_sync(FULL, idx, 0);
-            if ((int64_t)idx >= a.child.cap) {
-                if (lane == 0) atomicExch(&a.slots[pos], ((unsigned long long)tag << 32) | kOverflowIdx);
-                return INS_ARENA_FULL;
-            }
-            uint64_t *du = a.child.U + (size_t)idx * W;
-            if (lane < W) du[lane] = u0;
-            if (lane + 32 < W) du[lane + 32] = u1;
-            int32_t *db = a.child.B + (size_t)idx * Mpad;
-#pragma unroll
-            for (int e = 0; e < EPL; ++e) db[lane + 32 * e] = t[e];
-            if (lane == 0) a.child.meta[idx] = meta;
-            __threadfence();
-            __syncwarp();
-            if (lane == 0) atomicExch(&a.slots[pos], ((unsigned long long)tag << 32) | idx);
-            return INS_NEW;
-        }
-        if ((uint32_t)(v >> 32) == tag) {
-            v = wait_published(&a.slots[pos], v, lane);
-            if (v == kEmpty) {
-                if (lane == 0) atomicOr(&a.ctr[C_ERR], (unsigned long long)ERR_TIMEOUT);
-                return INS_TIMEOUT;
-            }
-            const uint32_t idx = (uint32_t)v;
-            if (idx == kOverflowIdx) return INS_ARENA_FULL;
-            __threadfence();
-            const uint64_t *su = a.child.U + (size_t)idx * W;
-            const int32_t *sb = a.child.B + (size_t)idx * Mpad;
-            bool eq = true;
-            if (lane < W) eq = __ldcg(su + lane) == u0;
-            if (lane + 32 < W) eq = eq && (__ldcg(su + lane + 32) == u1);
-#pragma unroll
-            for (int e = 0; e < EPL; ++e) eq = eq && (__ldcg(sb + lane + 32 * e) == t[e]);
-            if (__all_sync(FULL, eq)) return INS_DUP;
-        }
-        pos = (pos + 1) & a.slot_mask;
-    }
-    if (lane == 0) atomicOr(&a.ctr[C_ERR], (unsigned long long)ERR_TABLE_FULL);
-    return INS_TABLE_FULL;
+    return (key & 0x3FFu) | ((key >> 16) << 10) | ((uint32_t)pc << 23);
 }
 
-// ---------------------------------------------------------------------------
-// shared pieces of the AND update
-// ---------------------------------------------------------------------------
-
-// Divide the raw child balance by the gcd of its entries (warp-wide) and
-// report zero (balanced) and int32 overflow.  t64 in, t32 out.
-template <int EPL>
-__device__ __forceinline__ void normalise(int64_t (&t64)[EPL], int32_t (&t32)[EPL], bool &zero, bool &ovf)
-{
-    bool one = false, nz = false;
-#pragma unroll
-    for (int e = 0; e < EPL; ++e) {
-        one = one || (t64[e] == 1 || t64[e] == -1);
-        nz = nz || (t64[e] != 0);
-    }
-    zero = !__any_sync(FULL, nz);
-    if (zero) {
-#pragma unroll
-        for (int e = 0; e < EPL; ++e) t32[e] = 0;
-        ovf = false;
-        return;
-    }
-    if (!__any_sync(FULL, one)) {
-        uint64_t g = 0;
-#pragma unroll
-        for (int e = 0; e < EPL; ++e) g = gcd64(g, abs64(t64[e]));
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) g = gcd64(g, __shfl_xor_sync(FULL, g, off));
-        if (g > 1) {
-#pragma unroll
-            for (int e = 0; e < EPL; ++e) t64[e] /= (int64_t)g;
-        }
-    }
-    bool big = false;
-#pragma unroll
-    for (int e = 0; e < EPL; ++e) {
-        big = big || (t64[e] > 2147483647ll || t64[e] < -2147483647ll);
-        t32[e] = (int32_t)t64[e];
-    }
-    ovf = __any_sync(FULL, big);
-}
-
-// Pivot key of a state: min over unbalanced rows of (degree << 16 | row).
+// Pivot key of a state: min over unbalanced rows of (degree << 16 | row)
+// (warp-cooperative; lane l holds rows l + 32 e).
 template <int EPL>
 __device__ __forceinline__ uint32_t pivot_key(const uint32_t *bl, const NetView &nv, const int32_t (&t)[EPL], int lane)
 {
@@ -362,34 +268,27 @@ __device__ __forceinline__ uint32_t pivot_key(const uint32_t *bl, const NetView 
     return __reduce_min_sync(FULL, kmin);
 }
 
-// Does any result E in [beg, end) (through the index list if ids != null)
-// satisfy E subset of U' = U + column k?
-__device__ bool any_result_subset(const uint64_t *res, int W, const int32_t *ids, int64_t beg, int64_t end,
-                                  const uint64_t *Us, int kword, uint64_t kbit, int lane)
+// warp-cooperative normalisation of a seed column (t64 in, t32 out)
+template <int EPL>
+__device__ __forceinline__ void normalise(int64_t (&t64)[EPL], int32_t (&t32)[EPL], bool &zero)
 {
-    for (int64_t base = beg; base < end; base += 32) {
-        const int64_t i = base + lane;
-        bool hit = false;
-        if (i < end) {
-            const int64_t r = ids ? (int64_t)ids[i] : i;
-            const uint64_t *E = res + (size_t)r * W;
-            hit = true;
-            for (int w = 0; w < W; ++w) {
-                const uint64_t uw = Us[w] | (w == kword ? kbit : 0ull);
-                if (E[w] & ~uw) {
-                    hit = false;
-                    break;
-                }
-            }
-        }
-        if (__any_sync(FULL, hit)) return true;
+    bool nz = false;
+    uint64_t g = 0;
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+        nz = nz || (t64[e] != 0);
+        g = gcd64(g, abs64(t64[e]));
     }
-    return false;
+    zero = !__any_sync(FULL, nz);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) g = gcd64(g, __shfl_xor_sync(FULL, g, off));
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) t32[e] = (int32_t)(g > 1 ? t64[e] / (int64_t)g : t64[e]);
 }
 
 // ---------------------------------------------------------------------------
 // a0: seeds (INIT kernel analogue): flux 1 on every column producing the
-// target (every column for target -1).
+// target (every column for target -1).  One warp per seed.
 // ---------------------------------------------------------------------------
 
 template <int EPL>
@@ -421,13 +320,12 @@ __global__ void __launch_bounds__(kExpandWarps * 32) seed_kernel(NetView nv, Lev
                 if (row == lane + 32 * e) t64[e] = ent_coef(ent);
         }
         int32_t t[EPL];
-        bool zero, ovf;
-        normalise<EPL>(t64, t, zero, ovf);
-        const uint64_t u0 = (lane == (k >> 6)) ? (1ull << (k & 63)) : 0ull;
-        const uint64_t u1 = (lane + 32 == (k >> 6)) ? (1ull << (k & 63)) : 0ull;
+        bool zero;
+        normalise<EPL>(t64, t, zero);
         if (zero) {
             ++n_bal;
-            insert_support(a, W, u0, u1, lane);
+            if (lane == 0) insert_support(a, W, nullptr, k);
+            __syncwarp();
             continue;
         }
         const uint32_t key = pivot_key<EPL>(bl, nv, t, lane);
@@ -437,12 +335,11 @@ __global__ void __launch_bounds__(kExpandWarps * 32) seed_kernel(NetView nv, Lev
         idx = __shfl_sync(FULL, idx, 0);
         if ((int64_t)idx < a.child.cap) {
             uint64_t *du = a.child.U + (size_t)idx * W;
-            if (lane < W) du[lane] = u0;
-            if (lane + 32 < W) du[lane + 32] = u1;
+            for (int w = lane; w < W; w += 32) du[w] = child_word(nullptr, w, k);
             int32_t *db = a.child.B + (size_t)idx * nv.Mpad;
 #pragma unroll
             for (int e = 0; e < EPL; ++e) db[lane + 32 * e] = t[e];
-            if (lane == 0) a.child.meta[idx] = key;
+            if (lane == 0) a.child.meta[idx] = pack_meta(key, 1);
             deg_sum += key >> 16;
         }
     }
@@ -454,114 +351,395 @@ __global__ void __launch_bounds__(kExpandWarps * 32) seed_kernel(NetView nv, Lev
 }
 
 // ---------------------------------------------------------------------------
-// a1-a6: one level of expansion
+// a1-a6: one level of expansion, a group of G lanes per child.
+//
+// A warp takes 32 consecutive parents; their branch counts (the static
+// degree of each parent's acting metabolite, kept in the state's meta word)
+// are prefix-summed across the lanes, and the warp walks the flattened
+// (parent, branch) items 32 / G at a time.  In a group, lane l holds the
+// 16-byte chunks l, l + G, ... of the extra-flux row (CPL chunks, 4 * CPL
+// entries), so row loads and stores are coalesced and every reduction is
+// log2(G) shuffles.  The AND update reads column k of S_int from a dense
+// column-major copy of S_int (staged in shared memory with the rest of the
+// static network when it fits).  Arithmetic stays in 32 bits unless a group
+// needs the gcd or has an entry outside int32 (then a 64-bit slow path).
+// New states are claimed by CAS, written, and published with a release
+// store; probers observe published slots with an acquire CAS.
 // ---------------------------------------------------------------------------
 
-template <int EPL>
-__global__ void __launch_bounds__(kExpandWarps * 32) expand_kernel(NetView nv, LevelArgs a, int staged)
+template <int G>
+__device__ __forceinline__ uint32_t group_or(uint32_t x)
 {
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) x |= __shfl_xor_sync(FULL, x, off);
+    return x;
+}
+template <int G>
+__device__ __forceinline__ uint32_t group_min(uint32_t x)
+{
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+        const uint32_t y = __shfl_xor_sync(FULL, x, off);
+        x = y < x ? y : x;
+    }
+    return x;
+}
+template <int G>
+__device__ __forceinline__ uint32_t group_add(uint32_t x)
+{
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) x += __shfl_xor_sync(FULL, x, off);
+    return x;
+}
+
+__device__ __forceinline__ void store_release(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long cas_acquire(unsigned long long *p, unsigned long long cmp,
+                                                          unsigned long long v)
+{
+    unsigned long long old;
+    asm volatile("atom.acquire.gpu.global.cas.b64 %0, [%1], %2, %3;" : "=l"(old) : "l"(p), "l"(cmp), "l"(v) : "memory");
+    return old;
+}
+
+// 32-bit mixing of one balance entry (row m, value v) into two sums
+__device__ __forceinline__ void hash_entry(uint32_t m, uint32_t v, uint32_t &lo, uint32_t &hi)
+{
+    uint32_t x = v * 0x9E3779B1u + m * 0x85EBCA77u;
+    x ^= x >> 15;
+    x *= 0x2C1B3C6Du;
+    lo += x;
+    hi += x ^ (x >> 13) * 0x297A2D39u;
+}
+
+template <int G, int CPL>
+__global__ void __launch_bounds__(kExpandWarps * 32, (CPL <= 2 ? 3 : 2)) expand_kernel(NetView nv, LevelArgs a, int staged)
+{
+    constexpr int NG = 32 / G;    // children per warp round
+    constexpr int EPL = 4 * CPL;  // balance entries per lane
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
+    const int gi = lane / G;  // group in the warp
+    const int gl = lane % G;  // lane in the group
+    const int lead = gi * G;  // group leader lane
     const int W = nv.W;
     const int Mpad = nv.Mpad;
-    uint32_t *sblob = smem;
     const int blob_words = staged ? nv.blob_words : 0;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + blob_words);
-    uint64_t *Us = reinterpret_cast<uint64_t *>(smem + blob_words + 4) + wid * kMaxW;
-    const uint32_t *bl = stage_blob(nv, sblob, mbar, staged != 0, a.ctr);
+    const uint32_t *bl = stage_blob(nv, smem, mbar, staged != 0, a.ctr);
     if (bl == nullptr) return;
+    const int4 *dcol = reinterpret_cast<const int4 *>(bl + nv.o_dcols);
 
     unsigned long long n_exp = 0, n_ovf = 0, n_bal = 0, n_pruned = 0, deg_sum = 0;
-    const int64_t gw = (int64_t)blockIdx.x * kExpandWarps + wid;
-    const int64_t nw = (int64_t)gridDim.x * kExpandWarps;
-    bool stop = false;
-    for (int64_t p = gw; p < a.n_par && !stop; p += nw) {
-        // load the parent pathway
-        const uint64_t *pu = a.par.U + (size_t)p * W;
-        const uint64_t pu0 = lane < W ? pu[lane] : 0ull;
-        const uint64_t pu1 = lane + 32 < W ? pu[lane + 32] : 0ull;
-        Us[lane] = pu0;
-        Us[lane + 32] = pu1;
-        int32_t b[EPL];
-        const int32_t *pb = a.par.B + (size_t)p * Mpad;
+    bool fatal = false;
+    bool full = false;  // this warp saw the child arena reach its capacity
+    const uint64_t t_start = global_ns();
+    const int64_t wstride = (int64_t)gridDim.x * kExpandWarps * 32;
+    for (int64_t p0 = ((int64_t)blockIdx.x * kExpandWarps + wid) * 32; p0 < a.n_par; p0 += wstride) {
+        const int64_t pl = p0 + lane;
+        const uint32_t mj = pl < a.n_par ? a.par.meta[pl] : 0u;
+        const int dj = pl < a.n_par ? (int)((mj >> 10) & 0x1FFFu) : 0;
+        int incl = dj;
 #pragma unroll
-        for (int e = 0; e < EPL; ++e) b[e] = pb[lane + 32 * e];
-        const uint32_t meta = a.par.meta[p];
-        __syncwarp();
-        const int pc = __reduce_add_sync(FULL, (unsigned)(__popcll(pu0) + __popcll(pu1)));
-        const int sec = a.level - pc;  // secondary steps taken by the parent
-        const int piv = (int)(meta & 0xFFFFu);
-        const int32_t bi = __shfl_sync(FULL, pick<EPL>(b, piv >> 5), piv & 31);
-        const bool fwd = bi > 0;  // forward flow: consume the surplus
-        const uint32_t abi = (uint32_t)(bi < 0 ? -bi : bi);
-        const int lbeg = (int)bl[(fwd ? nv.o_consptr : nv.o_prodptr) + piv];
-        const int lend = (int)bl[(fwd ? nv.o_consptr : nv.o_prodptr) + piv + 1];
-        const int lent = fwd ? nv.o_consent : nv.o_prodent;
-        for (int q = lbeg; q < lend; ++q) {
-            const uint32_t br = bl[lent + q];
-            const int k = ent_index(br);
-            const uint32_t sik = (uint32_t)ent_coef(br);  // |S_ik|
-            const int tw = (int)bl[nv.o_twin + k];
-            if (tw >= 0 && bit_of(Us, tw)) continue;
-            const bool in_u = bit_of(Us, k);
-            if (!in_u && pc + 1 > a.max_len) continue;
-            if (in_u && sec + 1 > a.max_sec) continue;
-            ++n_exp;
-            // AND update (Eq. 3 / Eq. 4 in integers)
-            const uint32_t g = gcd32(abi, sik);
-            const int64_t A = (int64_t)(sik / g), C = (int64_t)(abi / g);
-            int64_t t64[EPL];
-#pragma unroll
-            for (int e = 0; e < EPL; ++e) t64[e] = A * (int64_t)b[e];
-            for (int r = (int)bl[nv.o_colptr + k]; r < (int)bl[nv.o_colptr + k + 1]; ++r) {
-                const uint32_t ent = bl[nv.o_colent + r];
-                const int row = ent_index(ent);
-                const int64_t add = C * (int64_t)ent_coef(ent);
-#pragma unroll
-                for (int e = 0; e < EPL; ++e)
-                    if (row == lane + 32 * e) t64[e] += add;
-            }
-            int32_t t[EPL];
-            bool zero, ovf;
-            normalise<EPL>(t64, t, zero, ovf);
-            if (ovf) {
-                ++n_ovf;
-                continue;
-            }
-            const int kword = k >> 6;
-            const uint64_t kbit = 1ull << (k & 63);
-            const uint64_t cu0 = pu0 | (lane == kword ? kbit : 0ull);
-            const uint64_t cu1 = pu1 | (lane + 32 == kword ? kbit : 0ull);
-            if (zero) {
-                ++n_bal;
-                const int rc = insert_support(a, W, cu0, cu1, lane);
-                if (rc < INS_DUP) stop = true;
-                continue;
-            }
-            // superset pruning against accepted results: results containing
-            // column k (if new) and every result of the previous level
-            bool pr = false;
-            if (!in_u) pr = any_result_subset(a.res, W, a.bidx, a.bptr[k], a.bptr[k + 1], Us, kword, kbit, lane);
-            if (!pr && a.recent_end > a.recent_begin)
-                pr = any_result_subset(a.res, W, nullptr, a.recent_begin, a.recent_end, Us, kword, kbit, lane);
-            if (pr) {
-                ++n_pruned;
-                continue;
-            }
-            const uint32_t key = pivot_key<EPL>(bl, nv, t, lane);
-            const int rc = insert_state<EPL>(a, W, Mpad, cu0, cu1, t, key, lane);
-            if (rc == INS_NEW) deg_sum += key >> 16;
-            if (rc == INS_TIMEOUT || rc == INS_TABLE_FULL) stop = true;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int x = __shfl_up_sync(FULL, incl, off);
+            if (lane >= off) incl += x;
         }
+        const int prej = incl - dj;
+        const int T = __shfl_sync(FULL, incl, 31);
+        if (T > 32 * nv.N) {
+            if (lane == 0) record_diag(a.ctr, ERR_BOUNDS, 3, T, 32 * nv.N, a.level);
+            break;
+        }
+        for (int base = 0; base < T; base += NG) {
+            if (__any_sync(FULL, fatal)) break;
+            const int c = base + gi;  // this group's item
+            int j = 0;                // largest j with pre_j <= c
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int v = __shfl_sync(FULL, prej, j + step);
+                if (v <= c) j += step;
+            }
+            const uint32_t pm = __shfl_sync(FULL, mj, j);
+            const int q = c - __shfl_sync(FULL, prej, j);
+
+            // --- branch selection (group-uniform) ---
+            bool ok = c < T;
+            int k = 0, pc = 0;
+            bool in_u = false;
+            int32_t A = 0, C = 0;
+            const int32_t *prow = nullptr;
+            const uint64_t *pu = nullptr;
+            if (ok) {
+                const int64_t p = p0 + j;
+                const int piv = (int)(pm & 0x3FFu);
+                pc = (int)((pm >> 23) & 0x7Fu);
+                prow = a.par.B + (size_t)p * Mpad;
+                pu = a.par.U + (size_t)p * W;
+                const int32_t bi = piv < nv.M ? prow[piv] : 0;
+                const bool fwd = bi > 0;  // forward flow: consume the surplus
+                const uint32_t abi = (uint32_t)(bi < 0 ? -bi : bi);
+                const int lptr = (fwd ? nv.o_consptr : nv.o_prodptr) + (piv < nv.M ? piv : 0);
+                const int lb = (int)bl[lptr];
+                const int le = (int)bl[lptr + 1];
+                if (piv >= nv.M || bi == 0 || lb + q >= le) {
+                    if (gl == 0) record_diag(a.ctr, ERR_BOUNDS, 1 + (piv >= nv.M ? 10 : 0) + (bi == 0 ? 100 : 0),
+                                             (long long)q, (long long)(le - lb), a.level);
+                    fatal = true;
+                    ok = false;
+                } else {
+                    const uint32_t br = bl[(fwd ? nv.o_consent : nv.o_prodent) + lb + q];
+                    k = ent_index(br);
+                    const uint32_t sik = (uint32_t)ent_coef(br);  // |S_ik|
+                    const int tw = (int)bl[nv.o_twin + k];
+                    in_u = bit_of(pu, k);
+                    const int sec = a.level - pc;
+                    ok = !(tw >= 0 && bit_of(pu, tw)) && (in_u ? sec + 1 <= a.max_sec : pc + 1 <= a.max_len);
+                    const uint32_t g0 = (abi == 1u || sik == 1u) ? 1u : gcd32(abi, sik);
+                    A = (int32_t)(sik / g0);
+                    C = (int32_t)(abi / g0);
+                }
+            }
+            if (ok && gl == 0) ++n_exp;
+
+            // --- AND update (Eq. 3 / Eq. 4 in integers), group-parallel ---
+            int64_t t[EPL];
+            int32_t t32[EPL];
+            uint32_t fl = 0;  // bit0 nonzero, bit1 some |t| == 1, bit2 some t outside int32
+            if (ok) {
+                const int4 *prow4 = reinterpret_cast<const int4 *>(prow);
+                const int4 *col4 = dcol + (size_t)k * (Mpad >> 2);
+#pragma unroll
+                for (int i = 0; i < CPL; ++i) {
+                    const int4 v = prow4[gl + G * i];
+                    const int4 w = col4[gl + G * i];
+                    t[4 * i + 0] = (int64_t)A * v.x + (int64_t)C * w.x;
+                    t[4 * i + 1] = (int64_t)A * v.y + (int64_t)C * w.y;
+                    t[4 * i + 2] = (int64_t)A * v.z + (int64_t)C * w.z;
+                    t[4 * i + 3] = (int64_t)A * v.w + (int64_t)C * w.w;
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < EPL; ++e) t[e] = 0;
+            }
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) {
+                const int32_t lo = (int32_t)t[e];
+                const bool fits = (uint64_t)(t[e] + 2147483647ll) <= 4294967294ull;  // |t| <= 2^31 - 1
+                t32[e] = lo;
+                fl |= (t[e] != 0 ? 1u : 0u) | ((lo == 1 || lo == -1) ? 2u : 0u) | (fits ? 0u : 4u);
+            }
+            fl = group_or<G>(fl);
+            const bool nz = fl & 1u;
+            // slow path: gcd needed (no unit entry) or an entry outside int32
+            const bool slow = ok && nz && ((fl & 6u) != 2u);
+            bool ovf = false;
+            if (__any_sync(FULL, slow)) {
+                uint64_t gg = 0, amax = 0;
+                if (slow) {
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) {
+                        const uint64_t at = abs64(t[e]);
+                        gg = gcd64(gg, at);
+                        amax = at > amax ? at : amax;
+                    }
+                }
+#pragma unroll
+                for (int off = G / 2; off > 0; off >>= 1) {
+                    gg = gcd64(gg, __shfl_xor_sync(FULL, gg, off));
+                    const uint64_t y = __shfl_xor_sync(FULL, amax, off);
+                    amax = y > amax ? y : amax;
+                }
+                if (slow) {
+                    if (gg > 1)
+#pragma unroll
+                        for (int e = 0; e < EPL; ++e) t32[e] = (int32_t)(t[e] / (int64_t)gg);
+                    ovf = amax / (gg ? gg : 1) > 2147483647ull;
+                }
+            }
+            const bool bal = ok && !nz;
+            bool norm = ok && nz && !ovf;
+            if (ovf && gl == 0) ++n_ovf;
+            if (bal && gl == 0) {
+                ++n_bal;  // all metabolites stable: to the arbiter
+                if (insert_support(a, W, pu, k) < INS_DUP) fatal = true;
+            }
+            fatal = group_or<G>(fatal ? 1u : 0u) != 0;
+
+            // --- superset pruning (group-cooperative scan) ---
+            if (__any_sync(FULL, norm)) {
+                int64_t b1 = 0, n1 = 0, b2 = 0, n2 = 0;
+                if (norm) {
+                    if (!in_u) {
+                        b1 = a.bptr[k];
+                        n1 = a.bptr[k + 1] - b1;
+                    }
+                    b2 = a.recent_begin;
+                    n2 = a.recent_end - a.recent_begin;
+                }
+                const int64_t len = n1 + n2;
+                int64_t wl = len;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    const int64_t y = __shfl_xor_sync(FULL, wl, off);
+                    wl = y > wl ? y : wl;
+                }
+                bool pr = false;
+                for (int64_t i0 = 0; i0 < wl; i0 += G) {
+                    const int64_t i = i0 + gl;
+                    bool hit = false;
+                    if (i < len && !pr) {
+                        const int64_t r = i < n1 ? (int64_t)a.bidx[b1 + i] : b2 + (i - n1);
+                        const uint64_t *E = a.res + (size_t)r * W;
+                        hit = true;
+                        for (int w = 0; w < W && hit; ++w) hit = (E[w] & ~child_word(pu, w, k)) == 0;
+                    }
+                    // every lane must take part in the shuffle: no short-circuit here
+                    const uint32_t any_hit = group_or<G>(hit ? 1u : 0u);
+                    pr = pr || any_hit != 0;
+                }
+                if (norm && pr) {
+                    norm = false;
+                    if (gl == 0) ++n_pruned;
+                }
+            }
+
+            // --- pivot key and fingerprint of the new state ---
+            uint32_t key = 0xFFFFFFFFu, hlo = 0, hhi = 0;
+            if (norm) {
+#pragma unroll
+                for (int i = 0; i < CPL; ++i)
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const int m = 4 * (gl + G * i) + jj;
+                        const int32_t v = t32[4 * i + jj];
+                        if (v != 0) {
+                            const uint32_t kk = bl[(v > 0 ? nv.o_keypos : nv.o_keyneg) + m];
+                            key = kk < key ? kk : key;
+                        }
+                        hash_entry((uint32_t)m, (uint32_t)v, hlo, hhi);
+                    }
+                for (int w = gl; w < W; w += G) {
+                    const uint64_t x = mix64(child_word(pu, w, k) ^ (0x2545f4914f6cdd1dull * (uint64_t)(w + 1)));
+                    hlo += (uint32_t)x;
+                    hhi += (uint32_t)(x >> 32);
+                }
+            }
+            key = group_min<G>(key);
+            hlo = group_add<G>(hlo);
+            hhi = group_add<G>(hhi);
+
+            // --- dedup and compaction: claim / write / publish / compare ---
+            uint64_t pos = 0;
+            uint32_t tag = 0;
+            slot_tag_pos(((uint64_t)hhi << 32) | hlo, a.slot_mask, pos, tag);
+            bool todo = norm && !full;  // group-uniform
+            uint64_t probes = 0;
+            int spins = 0;
+            const int pc1 = pc + (in_u ? 0 : 1);
+            int rounds = 0;
+            while (__any_sync(FULL, todo)) {
+                const bool expired = ++rounds > kMaxRounds || global_ns() - t_start > kWatchdogNs;
+                if (__any_sync(FULL, expired)) {  // warp-uniform decision
+                    if (lane == 0) record_diag(a.ctr, ERR_WATCHDOG, 2, rounds, kMaxRounds, a.level);
+                    fatal = true;
+                    break;
+                }
+                unsigned long long v = kEmpty;
+                if (todo && gl == 0) v = cas_acquire(&a.slots[pos], kEmpty, ((unsigned long long)tag << 32) | kPending);
+                v = __shfl_sync(FULL, v, lead);
+                const bool won = todo && v == kEmpty;
+                const bool other = todo && !won && (uint32_t)(v >> 32) != tag;
+                const bool waiting = todo && !won && !other && (uint32_t)v == kPending;
+                const bool over = todo && !won && !other && (uint32_t)v == kOverflowIdx;
+                const bool cmp = todo && !won && !other && !waiting && !over;
+                if (other) {
+                    pos = (pos + 1) & a.slot_mask;
+                    if (++probes > a.slot_mask) {
+                        if (gl == 0) atomicOr(&a.ctr[C_ERR], (unsigned long long)ERR_TABLE_FULL);
+                        todo = false;
+                        fatal = true;
+                    }
+                }
+                if (over) todo = false;
+                const unsigned wmask = __ballot_sync(FULL, won && gl == 0);
+                if (wmask) {
+                    const int leader = __ffs((int)wmask) - 1;
+                    unsigned long long base_idx = 0;
+                    if (lane == leader) base_idx = atomicAdd(&a.ctr[C_NEXT], (unsigned long long)__popc(wmask));
+                    base_idx = __shfl_sync(FULL, base_idx, leader);
+                    const uint64_t idx = base_idx + (uint64_t)__popc(wmask & ((1u << lead) - 1u));
+                    if (won) {
+                        if ((int64_t)idx >= a.child.cap) {
+                            full = true;  // level truncated: stop claiming
+                            if (gl == 0)
+                                store_release(&a.slots[pos], ((unsigned long long)tag << 32) | kOverflowIdx);
+                        } else {
+                            int4 *db = reinterpret_cast<int4 *>(a.child.B + (size_t)idx * Mpad);
+#pragma unroll
+                            for (int i = 0; i < CPL; ++i)
+                                db[gl + G * i] =
+                                    make_int4(t32[4 * i + 0], t32[4 * i + 1], t32[4 * i + 2], t32[4 * i + 3]);
+                            uint64_t *du = a.child.U + (size_t)idx * W;
+                            for (int w = gl; w < W; w += G) du[w] = child_word(pu, w, k);
+                            if (gl == 0) a.child.meta[idx] = pack_meta(key, pc1);
+                        }
+                        todo = false;
+                    }
+                    __syncwarp();  // the group's row writes precede the leader's release store
+                    if (won && gl == 0 && (int64_t)idx < a.child.cap) {
+                        store_release(&a.slots[pos], ((unsigned long long)tag << 32) | idx);
+                        deg_sum += key >> 16;
+                    }
+                    full = group_or<G>(full ? 1u : 0u) != 0;
+                }
+                if (__any_sync(FULL, cmp)) {
+                    bool eq = cmp;
+                    if (cmp) {
+                        const uint32_t ci = (uint32_t)v;
+                        const int4 *sb = reinterpret_cast<const int4 *>(a.child.B + (size_t)ci * Mpad);
+#pragma unroll
+                        for (int i = 0; i < CPL; ++i) {
+                            const int4 s = __ldcg(sb + gl + G * i);
+                            eq = eq && s.x == t32[4 * i + 0] && s.y == t32[4 * i + 1] && s.z == t32[4 * i + 2] &&
+                                 s.w == t32[4 * i + 3];
+                        }
+                        const uint64_t *su = a.child.U + (size_t)ci * W;
+                        for (int w = gl; w < W && eq; w += G) eq = __ldcg(su + w) == child_word(pu, w, k);
+                    }
+                    const bool neq = group_or<G>((cmp && !eq) ? 1u : 0u) != 0;
+                    if (cmp) {
+                        if (!neq) {
+                            todo = false;  // duplicate of a state already in the frontier
+                        } else {
+                            pos = (pos + 1) & a.slot_mask;
+                            ++probes;
+                        }
+                    }
+                }
+                if (__any_sync(FULL, waiting)) {
+                    if (waiting && ++spins > kSpinLimit) {
+                        if (gl == 0) atomicOr(&a.ctr[C_ERR], (unsigned long long)ERR_TIMEOUT);
+                        todo = false;
+                        fatal = true;
+                    }
+                    __nanosleep(32);
+                }
+                if (full) todo = false;
+            }
+            full = __any_sync(FULL, full);
+        }
+        if (__any_sync(FULL, fatal)) break;
     }
-    if (lane == 0) {
-        if (n_exp) atomicAdd(&a.ctr[C_EXP], n_exp);
-        if (n_ovf) atomicAdd(&a.ctr[C_OVF], n_ovf);
-        if (n_bal) atomicAdd(&a.ctr[C_BAL], n_bal);
-        if (n_pruned) atomicAdd(&a.ctr[C_PRUNED], n_pruned);
-        if (deg_sum) atomicAdd(&a.ctr[C_DEGSUM], deg_sum);
-    }
+    if (n_exp) atomicAdd(&a.ctr[C_EXP], n_exp);
+    if (n_ovf) atomicAdd(&a.ctr[C_OVF], n_ovf);
+    if (n_bal) atomicAdd(&a.ctr[C_BAL], n_bal);
+    if (n_pruned) atomicAdd(&a.ctr[C_PRUNED], n_pruned);
+    if (deg_sum) atomicAdd(&a.ctr[C_DEGSUM], deg_sum);
 }
 
 // ---------------------------------------------------------------------------
@@ -843,19 +1021,34 @@ cudaError_t launch_seed_t(const NetView &nv, const LevelArgs &a, int target, cud
     return cudaGetLastError();
 }
 
-template <int EPL>
+template <int G, int CPL>
 cudaError_t launch_expand_t(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s)
 {
     const bool staged = nv.blob_words * 4 <= kStageLimitBytes;
-    const size_t sm = (size_t)(staged ? nv.blob_words : 0) * 4 + 16 + (size_t)kExpandWarps * kMaxW * 8;
+    const size_t sm = (size_t)(staged ? nv.blob_words : 0) * 4 + 16;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(expand_kernel<EPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kStageLimitBytes + 16 + kExpandWarps * kMaxW * 8);
+        cudaFuncSetAttribute(expand_kernel<G, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageLimitBytes + 16);
         attr_set = true;
     }
-    expand_kernel<EPL><<<grid, kExpandWarps * 32, sm, s>>>(nv, a, staged ? 1 : 0);
+    expand_kernel<G, CPL><<<grid, kExpandWarps * 32, sm, s>>>(nv, a, staged ? 1 : 0);
     return cudaGetLastError();
+}
+
+template <int G, int CPL>
+int expand_grid_t(const NetView &nv, int sm_count)
+{
+    const bool staged = nv.blob_words * 4 <= kStageLimitBytes;
+    const size_t sm = (size_t)(staged ? nv.blob_words : 0) * 4 + 16;
+    cudaFuncSetAttribute(expand_kernel<G, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageLimitBytes + 16);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expand_kernel<G, CPL>, kExpandWarps * 32, sm) !=
+            cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return sm_count * per_sm;
 }
 
 }  // namespace
@@ -879,19 +1072,34 @@ cudaError_t launch_seed(const NetView &nv, const LevelArgs &a, int target, cudaS
 #undef CALL_SEED
 }
 
+// (lanes per child, 16-byte chunks per lane) for each row width Mpad = 32 EPL
+#define EFM_GROUP_DISPATCH(EPLV, CALL) \
+    switch (EPLV) {                    \
+    case 1: return CALL(4, 2);         \
+    case 2: return CALL(8, 2);         \
+    case 4: return CALL(16, 2);        \
+    case 8: return CALL(32, 2);        \
+    case 16: return CALL(32, 4);       \
+    case 28: return CALL(32, 7);       \
+    case 32: return CALL(32, 8);       \
+    default: break;                    \
+    }
+
 cudaError_t launch_expand(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s)
 {
-#define CALL_EXP(E) launch_expand_t<E>(nv, a, grid, s)
-    EFM_EPL_DISPATCH(nv.EPL, CALL_EXP)
+#define CALL_EXP(G, C) launch_expand_t<G, C>(nv, a, grid, s)
+    EFM_GROUP_DISPATCH(nv.EPL, CALL_EXP)
 #undef CALL_EXP
+    return cudaErrorInvalidValue;
 }
 
 int expand_grid(const NetView &nv, int sm_count)
 {
-    // resident CTAs per SM are bounded by registers at 256 threads; take a
-    // fixed multiple of the SM count (persistent grid-stride loop inside)
-    (void)nv;
-    return sm_count * 4;
+    // persistent grid: as many CTAs as can be resident (grid-stride inside)
+#define CALL_GRID(G, C) expand_grid_t<G, C>(nv, sm_count)
+    EFM_GROUP_DISPATCH(nv.EPL, CALL_GRID)
+#undef CALL_GRID
+    return sm_count;
 }
 
 cudaError_t launch_accept(const NetView &nv, const AcceptArgs &a, cudaStream_t s)
