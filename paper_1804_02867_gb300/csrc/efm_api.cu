@@ -325,8 +325,8 @@ namespace {
 // Device buffers of one traversal, reused across the targets of a job.
 struct Work {
     DevBuf U[2], B[2], meta[2];
-    DevBuf slots, cslots, cand, res, bcnt, bfill, bptr, bidx, ctr, sortidx;
-    int64_t F_cap = 0, cand_cap = 0, res_cap = 0, bidx_cap = 0;
+    DevBuf slots, cslots, cand, res, bcnt, bfill, bptr, bres, ctr, sortidx;
+    int64_t F_cap = 0, cand_cap = 0, res_cap = 0, bres_cap = 0;  // bres_cap in bucket entries
     uint64_t slot_cap = 0, cslot_cap = 0, sort_cap = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
@@ -338,7 +338,7 @@ void free_work(Work &w, cudaStream_t s)
         dev_free(w.B[i], s);
         dev_free(w.meta[i], s);
     }
-    DevBuf *bufs[] = {&w.slots, &w.cslots, &w.cand, &w.res, &w.bcnt, &w.bfill, &w.bptr, &w.bidx, &w.ctr, &w.sortidx};
+    DevBuf *bufs[] = {&w.slots, &w.cslots, &w.cand, &w.res, &w.bcnt, &w.bfill, &w.bptr, &w.bres, &w.ctr, &w.sortidx};
     for (DevBuf *b : bufs) dev_free(*b, s);
     for (auto &e : w.ev)
         if (e) cudaEventDestroy(e);
@@ -351,7 +351,6 @@ int alloc_work(Work &w, const efm_net *net, const efm_limits &lim, int total_war
     w.F_cap = lim.max_frontier > 0 ? lim.max_frontier + 1 : default_cap;
     w.cand_cap = (int64_t)1 << 20;
     w.res_cap = w.cand_cap;
-    w.bidx_cap = w.res_cap * (int64_t)lim.max_len;
     w.slot_cap = next_pow2(2 * (uint64_t)w.F_cap + 64 * (uint64_t)total_warps);
     w.cslot_cap = next_pow2(2 * (uint64_t)w.cand_cap);
     const size_t W = (size_t)nv.W, Mpad = (size_t)nv.Mpad, F = (size_t)w.F_cap;
@@ -368,7 +367,6 @@ int alloc_work(Work &w, const efm_net *net, const efm_limits &lim, int total_war
     ok = ok && dev_alloc(w.bcnt, (size_t)nv.N * 4, s);
     ok = ok && dev_alloc(w.bfill, (size_t)nv.N * 4, s);
     ok = ok && dev_alloc(w.bptr, (size_t)(nv.N + 1) * 4, s);
-    ok = ok && dev_alloc(w.bidx, (size_t)w.bidx_cap * 4, s);
     ok = ok && dev_alloc(w.ctr, C_COUNT * 8, s);
     for (auto &e : w.ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
     if (!ok) {
@@ -415,7 +413,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
     a.cand_cap = w.cand_cap;
     a.res = (const uint64_t *)w.res.p;
     a.bptr = (const int32_t *)w.bptr.p;
-    a.bidx = (const int32_t *)w.bidx.p;
+    a.bres = nullptr;
     a.max_len = lim.max_len;
     a.max_sec = lim.max_secondary;
     a.ctr = ctr;
@@ -493,8 +491,17 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
         if (level > lim.max_len + lim.max_secondary + 1) return EFM_ETIMEOUT;
         // buckets over every accepted result so far (all of them come from levels < `level`)
         if (res_n != buckets_built_for) {
+            // bucket entries needed: sum of |E| <= res_n * max_len (grown on demand)
+            const int64_t need = std::max<int64_t>(res_n * (int64_t)lim.max_len, 1);
+            if (need > w.bres_cap) {
+                dev_free(w.bres, s);
+                const int64_t cap = std::max<int64_t>(need, 2 * w.bres_cap);
+                if (!dev_alloc(w.bres, (size_t)cap * nv.W * 8, s)) return EFM_ENOMEM;
+                w.bres_cap = cap;
+            }
+            a.bres = (const uint64_t *)w.bres.p;
             CK(launch_buckets(nv, (const uint64_t *)w.res.p, res_n, (int32_t *)w.bcnt.p, (int32_t *)w.bptr.p,
-                              (int32_t *)w.bfill.p, (int32_t *)w.bidx.p, s));
+                              (int32_t *)w.bfill.p, (uint64_t *)w.bres.p, s));
             out.kernel_launches += res_n > 0 ? 3 : 1;
             buckets_built_for = res_n;
         }
@@ -504,6 +511,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
         CK(cudaMemsetAsync(ctr + C_NEXT, 0, 2 * 8, s));
         a.par = arena(cur);
         a.n_par = n_front;
+        a.cpw = (int)std::min<int64_t>(32, std::max<int64_t>(1, (n_front + total_warps - 1) / total_warps));
         a.child = arena(cur ^ 1);
         a.slot_mask = nslots - 1;
         a.level = level;

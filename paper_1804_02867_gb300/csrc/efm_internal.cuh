@@ -77,9 +77,10 @@ struct LevelArgs {
     int64_t cand_cap;
     const uint64_t *res;        // [res_cap][W]
     const int32_t *bptr;        // [N + 1] result buckets by column
-    const int32_t *bidx;
+    const uint64_t *bres;       // bucket entries: the result's W support words
     int64_t recent_begin, recent_end;  // results of the previous level
     int level, max_len, max_sec;
+    int cpw;                    // parents per warp chunk (1..32)
     unsigned long long *ctr;
 };
 
@@ -96,7 +97,7 @@ cudaError_t launch_seed(const NetView &nv, const LevelArgs &a, int target, cudaS
 cudaError_t launch_expand(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_accept(const NetView &nv, const AcceptArgs &a, cudaStream_t s);
 cudaError_t launch_buckets(const NetView &nv, const uint64_t *res, int64_t n_res, int32_t *bcnt, int32_t *bptr,
-                           int32_t *bfill, int32_t *bidx, cudaStream_t s);
+                           int32_t *bfill, uint64_t *bres, cudaStream_t s);
 cudaError_t launch_sort_results(const uint64_t *res, int64_t n, int W, uint32_t *idx, int64_t n_pow2,
                                 uint64_t *out, int64_t n_keep, cudaStream_t s);
 int expand_grid(const NetView &nv, int sm_count);

@@ -200,7 +200,7 @@ __device__ __forceinline__ uint64_t child_word(const uint64_t *pu, int w, int k)
 
 // Insert the support U' = U + {k} of a balanced pathway into the set of
 // supports judged in this traversal (one thread).
-__device__ int insert_support(const LevelArgs &a, int W, const uint64_t *pu, int k)
+__device__ __noinline__ int insert_support(const LevelArgs &a, int W, const uint64_t *pu, int k)
 {
     uint64_t h = 0;
     for (int w = 0; w < W; ++w) h += mix64(child_word(pu, w, k) ^ (0x51ed27f3a5b1c3d9ull * (uint64_t)(w + 1)));
@@ -243,6 +243,44 @@ __device__ int insert_support(const LevelArgs &a, int W, const uint64_t *pu, int
     }
     atomicOr(&a.ctr[C_ERR], (unsigned long long)ERR_TABLE_FULL);
     return INS_TABLE_FULL;
+}
+
+// 64-bit recomputation of a child's raw entries (rare: some entry left the
+// int32 range): gcd and largest magnitude over the lane's entries.
+struct GcdMax {
+    uint64_t g, m;
+};
+__device__ __noinline__ GcdMax raw_gcd_max(const int4 *prow4, const int4 *col4, int gl, int G, int CPL, int32_t A,
+                                           int32_t C)
+{
+    GcdMax r{0, 0};
+    for (int i = 0; i < CPL; ++i) {
+        const int4 v = prow4[gl + G * i];
+        const int4 w = col4[gl + G * i];
+        const int32_t pv[4] = {v.x, v.y, v.z, v.w}, cv[4] = {w.x, w.y, w.z, w.w};
+        for (int jj = 0; jj < 4; ++jj) {
+            const uint64_t at = abs64((int64_t)A * pv[jj] + (int64_t)C * cv[jj]);
+            if (at != 0) {
+                r.g = r.g == 0 ? at : gcd64(r.g, at);
+                r.m = at > r.m ? at : r.m;
+            }
+        }
+    }
+    return r;
+}
+
+// Supports of more than two words: is some result with bucket/recent
+// position in [i0, i1) a subset of U + {k}?
+__device__ __noinline__ bool subset_scan_wide(const LevelArgs &a, int W, const uint64_t *pu, int k, int64_t b1,
+                                              int64_t n1, int64_t i0, int64_t i1)
+{
+    for (int64_t i = i0; i < i1; ++i) {
+        const uint64_t *E = i < n1 ? a.bres + (size_t)(b1 + i) * W : a.res + (size_t)(a.recent_begin + i - n1) * W;
+        bool sub = true;
+        for (int w = 0; w < W && sub; ++w) sub = (__ldg(E + w) & ~child_word(pu, w, k)) == 0;
+        if (sub) return true;
+    }
+    return false;
 }
 
 // pivot key (degree << 16 | row) -> state meta: row | degree << 10 | |U| << 23
@@ -351,20 +389,23 @@ __global__ void __launch_bounds__(kExpandWarps * 32) seed_kernel(NetView nv, Lev
 }
 
 // ---------------------------------------------------------------------------
-// a1-a6: one level of expansion, a group of G lanes per child.
+// a1-a6: one level of expansion.
 //
-// A warp takes 32 consecutive parents; their branch counts (the static
-// degree of each parent's acting metabolite, kept in the state's meta word)
-// are prefix-summed across the lanes, and the warp walks the flattened
-// (parent, branch) items 32 / G at a time.  In a group, lane l holds the
-// 16-byte chunks l, l + G, ... of the extra-flux row (CPL chunks, 4 * CPL
-// entries), so row loads and stores are coalesced and every reduction is
-// log2(G) shuffles.  The AND update reads column k of S_int from a dense
-// column-major copy of S_int (staged in shared memory with the rest of the
-// static network when it fits).  Arithmetic stays in 32 bits unless a group
-// needs the gcd or has an entry outside int32 (then a 64-bit slow path).
-// New states are claimed by CAS, written, and published with a release
-// store; probers observe published slots with an acquire CAS.
+// Phase 1 (a group of G lanes per child): a warp takes 32 consecutive
+// parents; their branch counts (the static degree of each parent's acting
+// metabolite, kept in the state's meta word) are prefix-summed across the
+// lanes, and the warp walks the flattened (parent, branch) items 32 / G at a
+// time.  In a group, lane l holds the 16-byte chunks l, l + G, ... of the
+// extra-flux row (CPL chunks, 4 * CPL entries), so row loads are coalesced
+// and every reduction is log2(G) shuffles.  The AND update reads column k of
+// S_int from a dense column-major copy of S_int (staged in shared memory
+// with the rest of the static network when it fits) and stays in 32 bits
+// unless a group needs the gcd or has an entry outside int32.  Unbalanced
+// children are appended to a per-warp batch in shared memory.
+//
+// Phase 2 (one lane per batched child, NB children at once): superset
+// pruning, then claim / write / publish / compare in the state hash table,
+// so the latency of the atomics is paid once per batch, not per child.
 // ---------------------------------------------------------------------------
 
 template <int G>
@@ -391,6 +432,13 @@ __device__ __forceinline__ uint32_t group_add(uint32_t x)
     for (int off = G / 2; off > 0; off >>= 1) x += __shfl_xor_sync(FULL, x, off);
     return x;
 }
+template <int G>
+__device__ __forceinline__ uint32_t group_xor(uint32_t x)
+{
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) x ^= __shfl_xor_sync(FULL, x, off);
+    return x;
+}
 
 __device__ __forceinline__ void store_release(unsigned long long *p, unsigned long long v)
 {
@@ -408,18 +456,28 @@ __device__ __forceinline__ unsigned long long cas_acquire(unsigned long long *p,
 // 32-bit mixing of one balance entry (row m, value v) into two sums
 __device__ __forceinline__ void hash_entry(uint32_t m, uint32_t v, uint32_t &lo, uint32_t &hi)
 {
-    uint32_t x = v * 0x9E3779B1u + m * 0x85EBCA77u;
-    x ^= x >> 15;
-    x *= 0x2C1B3C6Du;
-    lo += x;
-    hi += x ^ (x >> 13) * 0x297A2D39u;
+    const uint32_t x = (v ^ (m * 0x9E3779B9u)) * 0x85EBCA6Bu;
+    lo += x ^ (x >> 16);
+    hi ^= x + m;
 }
+
+// children per warp batch for a row of 16-byte chunks nch (shared memory
+// per warp: NB padded rows plus 32 bytes of bookkeeping per child)
+template <int G, int CPL>
+struct BatchShape {
+    static constexpr int NCH = G * CPL;          // 16-byte chunks per row
+    static constexpr int NB = NCH <= 16 ? 16 : (NCH <= 32 ? 8 : 4);
+    static constexpr int ROW = NCH + 1;          // padded row (int4 units): conflict-free per-lane access
+    static constexpr int BYTES = NB * ROW * 16 + NB * 32;
+};
 
 template <int G, int CPL>
 __global__ void __launch_bounds__(kExpandWarps * 32, (CPL <= 2 ? 3 : 2)) expand_kernel(NetView nv, LevelArgs a, int staged)
 {
     constexpr int NG = 32 / G;    // children per warp round
     constexpr int EPL = 4 * CPL;  // balance entries per lane
+    using BS = BatchShape<G, CPL>;
+    constexpr int NB = BS::NB;
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
@@ -430,19 +488,169 @@ __global__ void __launch_bounds__(kExpandWarps * 32, (CPL <= 2 ? 3 : 2)) expand_
     const int Mpad = nv.Mpad;
     const int blob_words = staged ? nv.blob_words : 0;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + blob_words);
+    // per-warp batch: rows, then (pos, tag, key, info, parent) per child
+    char *wbase = reinterpret_cast<char *>(smem + blob_words + 4) + (size_t)wid * BS::BYTES;
+    int4 *brow = reinterpret_cast<int4 *>(wbase);
+    uint64_t *bpos = reinterpret_cast<uint64_t *>(wbase + NB * BS::ROW * 16);
+    uint32_t *btag = reinterpret_cast<uint32_t *>(bpos + NB);
+    uint32_t *bkey = btag + NB;
+    uint32_t *binfo = bkey + NB;  // k | in_u << 12 | pc1 << 13
+    uint32_t *bpar = binfo + NB;  // parent index
     const uint32_t *bl = stage_blob(nv, smem, mbar, staged != 0, a.ctr);
     if (bl == nullptr) return;
     const int4 *dcol = reinterpret_cast<const int4 *>(bl + nv.o_dcols);
 
     unsigned long long n_exp = 0, n_ovf = 0, n_bal = 0, n_pruned = 0, deg_sum = 0;
     bool fatal = false;
-    bool full = false;  // this warp saw the child arena reach its capacity
+    bool full = false;  // the child arena reached its capacity
+    int nb = 0;         // children in the batch (warp-uniform)
     const uint64_t t_start = global_ns();
-    const int64_t wstride = (int64_t)gridDim.x * kExpandWarps * 32;
-    for (int64_t p0 = ((int64_t)blockIdx.x * kExpandWarps + wid) * 32; p0 < a.n_par; p0 += wstride) {
+
+    // Phase 2: prune and insert the batched children, one lane each.
+    auto flush = [&]() {
+        __syncwarp();
+        const bool mine = lane < nb;
+        const uint32_t info = mine ? binfo[lane] : 0u;
+        const int k = (int)(info & 0xFFFu);
+        const bool in_u = (info >> 12) & 1u;
+        const uint64_t *pu = a.par.U + (size_t)(mine ? bpar[lane] : 0u) * W;
+        bool todo = mine;
+        if (todo) {
+            // superset pruning (counted on a truncated level too): results
+            // containing column k (if new) and every result of the previous
+            // level; the loads of PU entries are issued together
+            const int64_t b1 = in_u ? 0 : a.bptr[k];
+            const int64_t n1 = in_u ? 0 : a.bptr[k + 1] - b1;
+            const int64_t n2 = a.recent_end - a.recent_begin;
+            const int64_t n = n1 + n2;
+            constexpr int PU = 8;
+            bool pr = false;
+            uint64_t u0 = 0, u1 = 0;
+            if (W <= 2) {
+                u0 = child_word(pu, 0, k);
+                u1 = W == 2 ? child_word(pu, 1, k) : 0ull;
+            }
+            for (int64_t i0 = 0; i0 < n && !pr; i0 += PU) {
+                if (W <= 2) {
+                    uint64_t e0[PU], e1[PU];
+#pragma unroll
+                    for (int u = 0; u < PU; ++u) {
+                        const int64_t i = i0 + u;
+                        const uint64_t *E = i < n1 ? a.bres + (size_t)(b1 + i) * W
+                                                   : a.res + (size_t)(a.recent_begin + i - n1) * W;
+                        e0[u] = i < n ? __ldg(E) : ~0ull;
+                        e1[u] = (i < n && W == 2) ? __ldg(E + 1) : 0ull;
+                    }
+#pragma unroll
+                    for (int u = 0; u < PU; ++u) pr = pr || (((e0[u] & ~u0) | (e1[u] & ~u1)) == 0);
+                } else {
+                    pr = subset_scan_wide(a, W, pu, k, b1, n1, i0, i0 + PU < n ? i0 + PU : n);
+                }
+            }
+            if (pr) {
+                ++n_pruned;
+                todo = false;
+            }
+        }
+        if (full) todo = false;
+        const uint64_t row_i = (uint64_t)lane * BS::ROW;
+        uint64_t pos = mine ? bpos[lane] : 0ull;
+        const uint32_t tag = mine ? btag[lane] : 0u;
+        uint64_t probes = 0;
+        int spins = 0, rounds = 0;
+        while (__any_sync(FULL, todo)) {
+            const bool expired = ++rounds > kMaxRounds || global_ns() - t_start > kWatchdogNs;
+            if (__any_sync(FULL, expired)) {  // warp-uniform decision
+                if (lane == 0) record_diag(a.ctr, ERR_WATCHDOG, 2, rounds, kMaxRounds, a.level);
+                fatal = true;
+                break;
+            }
+            unsigned long long v = kEmpty;
+            if (todo) v = cas_acquire(&a.slots[pos], kEmpty, ((unsigned long long)tag << 32) | kPending);
+            const bool won = todo && v == kEmpty;
+            const bool other = todo && !won && (uint32_t)(v >> 32) != tag;
+            const bool waiting = todo && !won && !other && (uint32_t)v == kPending;
+            const bool over = todo && !won && !other && (uint32_t)v == kOverflowIdx;
+            const bool cmp = todo && !won && !other && !waiting && !over;
+            if (other) {
+                pos = (pos + 1) & a.slot_mask;
+                if (++probes > a.slot_mask) {
+                    atomicOr(&a.ctr[C_ERR], (unsigned long long)ERR_TABLE_FULL);
+                    todo = false;
+                    fatal = true;
+                }
+            }
+            if (over) todo = false;
+            const unsigned wmask = __ballot_sync(FULL, won);
+            if (wmask) {
+                const int leader = __ffs((int)wmask) - 1;
+                unsigned long long base_idx = 0;
+                if (lane == leader) base_idx = atomicAdd(&a.ctr[C_NEXT], (unsigned long long)__popc(wmask));
+                base_idx = __shfl_sync(FULL, base_idx, leader);
+                const uint64_t idx = base_idx + (uint64_t)__popc(wmask & ((1u << lane) - 1u));
+                bool wrote = false;
+                if (won) {
+                    if ((int64_t)idx >= a.child.cap) {
+                        full = true;  // level truncated: stop claiming
+                        store_release(&a.slots[pos], ((unsigned long long)tag << 32) | kOverflowIdx);
+                    } else {
+                        int4 *db = reinterpret_cast<int4 *>(a.child.B + (size_t)idx * Mpad);
+                        for (int c = 0; c < BS::NCH; ++c) db[c] = brow[row_i + c];
+                        uint64_t *du = a.child.U + (size_t)idx * W;
+                        for (int w = 0; w < W; ++w) du[w] = child_word(pu, w, k);
+                        a.child.meta[idx] = pack_meta(bkey[lane], (int)(info >> 13));
+                        wrote = true;
+                    }
+                    todo = false;
+                }
+                __threadfence_block();  // order each lane's row writes before its release store
+                if (wrote) {
+                    store_release(&a.slots[pos], ((unsigned long long)tag << 32) | idx);
+                    deg_sum += bkey[lane] >> 16;
+                }
+            }
+            if (cmp) {
+                const uint32_t ci = (uint32_t)v;
+                const int4 *sb = reinterpret_cast<const int4 *>(a.child.B + (size_t)ci * Mpad);
+                bool eq = true;
+                for (int c = 0; c < BS::NCH && eq; ++c) {
+                    const int4 s = __ldcg(sb + c);
+                    const int4 o = brow[row_i + c];
+                    eq = s.x == o.x && s.y == o.y && s.z == o.z && s.w == o.w;
+                }
+                const uint64_t *su = a.child.U + (size_t)ci * W;
+                for (int w = 0; w < W && eq; ++w) eq = __ldcg(su + w) == child_word(pu, w, k);
+                if (eq) {
+                    todo = false;  // duplicate of a state already in the frontier
+                } else {
+                    pos = (pos + 1) & a.slot_mask;
+                    ++probes;
+                }
+            }
+            if (__any_sync(FULL, waiting)) {
+                if (waiting && ++spins > kSpinLimit) {
+                    atomicOr(&a.ctr[C_ERR], (unsigned long long)ERR_TIMEOUT);
+                    todo = false;
+                    fatal = true;
+                }
+                __nanosleep(32);
+            }
+            full = __any_sync(FULL, full);
+            if (full) todo = false;
+        }
+        nb = 0;
+        __syncwarp();
+    };
+
+    // chunks of cpw parents per warp (fewer for small levels, so that the
+    // items of a small level spread over all warps)
+    const int cpw = a.cpw;
+    const int64_t wstride = (int64_t)gridDim.x * kExpandWarps * cpw;
+    for (int64_t p0 = ((int64_t)blockIdx.x * kExpandWarps + wid) * cpw; p0 < a.n_par; p0 += wstride) {
         const int64_t pl = p0 + lane;
-        const uint32_t mj = pl < a.n_par ? a.par.meta[pl] : 0u;
-        const int dj = pl < a.n_par ? (int)((mj >> 10) & 0x1FFFu) : 0;
+        const bool pin = lane < cpw && pl < a.n_par;
+        const uint32_t mj = pin ? a.par.meta[pl] : 0u;
+        const int dj = pin ? (int)((mj >> 10) & 0x1FFFu) : 0;
         int incl = dj;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -453,7 +661,7 @@ __global__ void __launch_bounds__(kExpandWarps * 32, (CPL <= 2 ? 3 : 2)) expand_
         const int T = __shfl_sync(FULL, incl, 31);
         if (T > 32 * nv.N) {
             if (lane == 0) record_diag(a.ctr, ERR_BOUNDS, 3, T, 32 * nv.N, a.level);
-            break;
+            fatal = true;
         }
         for (int base = 0; base < T; base += NG) {
             if (__any_sync(FULL, fatal)) break;
@@ -472,14 +680,12 @@ __global__ void __launch_bounds__(kExpandWarps * 32, (CPL <= 2 ? 3 : 2)) expand_
             int k = 0, pc = 0;
             bool in_u = false;
             int32_t A = 0, C = 0;
-            const int32_t *prow = nullptr;
-            const uint64_t *pu = nullptr;
+            const int64_t p = p0 + j;
+            const int32_t *prow = a.par.B + (size_t)p * Mpad;
+            const uint64_t *pu = a.par.U + (size_t)p * W;
             if (ok) {
-                const int64_t p = p0 + j;
                 const int piv = (int)(pm & 0x3FFu);
                 pc = (int)((pm >> 23) & 0x7Fu);
-                prow = a.par.B + (size_t)p * Mpad;
-                pu = a.par.U + (size_t)p * W;
                 const int32_t bi = piv < nv.M ? prow[piv] : 0;
                 const bool fwd = bi > 0;  // forward flow: consume the surplus
                 const uint32_t abi = (uint32_t)(bi < 0 ? -bi : bi);
@@ -507,62 +713,83 @@ __global__ void __launch_bounds__(kExpandWarps * 32, (CPL <= 2 ? 3 : 2)) expand_
             if (ok && gl == 0) ++n_exp;
 
             // --- AND update (Eq. 3 / Eq. 4 in integers), group-parallel ---
-            int64_t t[EPL];
             int32_t t32[EPL];
             uint32_t fl = 0;  // bit0 nonzero, bit1 some |t| == 1, bit2 some t outside int32
+            const int4 *prow4 = reinterpret_cast<const int4 *>(prow);
+            const int4 *col4 = dcol + (size_t)k * (Mpad >> 2);
             if (ok) {
-                const int4 *prow4 = reinterpret_cast<const int4 *>(prow);
-                const int4 *col4 = dcol + (size_t)k * (Mpad >> 2);
 #pragma unroll
                 for (int i = 0; i < CPL; ++i) {
                     const int4 v = prow4[gl + G * i];
                     const int4 w = col4[gl + G * i];
-                    t[4 * i + 0] = (int64_t)A * v.x + (int64_t)C * w.x;
-                    t[4 * i + 1] = (int64_t)A * v.y + (int64_t)C * w.y;
-                    t[4 * i + 2] = (int64_t)A * v.z + (int64_t)C * w.z;
-                    t[4 * i + 3] = (int64_t)A * v.w + (int64_t)C * w.w;
+                    const int32_t pv[4] = {v.x, v.y, v.z, v.w}, cv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const int64_t tt = (int64_t)A * pv[jj] + (int64_t)C * cv[jj];
+                        const int32_t lo = (int32_t)tt;
+                        const bool fits = tt == (int64_t)lo && lo != INT32_MIN;
+                        t32[4 * i + jj] = lo;
+                        fl |= (tt != 0 ? 1u : 0u) | ((lo == 1 || lo == -1) ? 2u : 0u) | (fits ? 0u : 4u);
+                    }
                 }
             } else {
 #pragma unroll
-                for (int e = 0; e < EPL; ++e) t[e] = 0;
-            }
-#pragma unroll
-            for (int e = 0; e < EPL; ++e) {
-                const int32_t lo = (int32_t)t[e];
-                const bool fits = (uint64_t)(t[e] + 2147483647ll) <= 4294967294ull;  // |t| <= 2^31 - 1
-                t32[e] = lo;
-                fl |= (t[e] != 0 ? 1u : 0u) | ((lo == 1 || lo == -1) ? 2u : 0u) | (fits ? 0u : 4u);
+                for (int e = 0; e < EPL; ++e) t32[e] = 0;
             }
             fl = group_or<G>(fl);
             const bool nz = fl & 1u;
-            // slow path: gcd needed (no unit entry) or an entry outside int32
+            // slow path: the gcd is needed (no unit entry), or an entry is
+            // outside int32 (then the raw entries are recomputed in 64 bits)
             const bool slow = ok && nz && ((fl & 6u) != 2u);
+            const bool big = (fl & 4u) != 0u;
             bool ovf = false;
             if (__any_sync(FULL, slow)) {
                 uint64_t gg = 0, amax = 0;
-                if (slow) {
+                if (slow && !big) {
 #pragma unroll
                     for (int e = 0; e < EPL; ++e) {
-                        const uint64_t at = abs64(t[e]);
-                        gg = gcd64(gg, at);
-                        amax = at > amax ? at : amax;
+                        const uint32_t at = (uint32_t)(t32[e] < 0 ? -t32[e] : t32[e]);
+                        if (at != 0) gg = gg == 0 ? at : gcd32((uint32_t)gg, at);
                     }
+                } else if (slow) {
+                    const GcdMax gm = raw_gcd_max(prow4, col4, gl, G, CPL, A, C);
+                    gg = gm.g;
+                    amax = gm.m;
                 }
 #pragma unroll
                 for (int off = G / 2; off > 0; off >>= 1) {
-                    gg = gcd64(gg, __shfl_xor_sync(FULL, gg, off));
+                    const uint64_t og = __shfl_xor_sync(FULL, gg, off);
+                    gg = og == 0 ? gg : (gg == 0 ? og : gcd64(gg, og));
                     const uint64_t y = __shfl_xor_sync(FULL, amax, off);
                     amax = y > amax ? y : amax;
                 }
                 if (slow) {
-                    if (gg > 1)
+                    ovf = big && amax / gg > 2147483647ull;
+                    if (!ovf && gg > 1) {
+                        const bool pow2 = (gg & (gg - 1)) == 0;
+                        const int sh = __ffsll((long long)gg) - 1;
+                        if (!big) {
 #pragma unroll
-                        for (int e = 0; e < EPL; ++e) t32[e] = (int32_t)(t[e] / (int64_t)gg);
-                    ovf = amax / (gg ? gg : 1) > 2147483647ull;
+                            for (int e = 0; e < EPL; ++e)
+                                t32[e] = t32[e] == 0 ? 0 : (pow2 ? (t32[e] >> sh) : t32[e] / (int32_t)gg);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < CPL; ++i) {
+                                const int4 v = prow4[gl + G * i];
+                                const int4 w = col4[gl + G * i];
+                                const int32_t pv[4] = {v.x, v.y, v.z, v.w}, cv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                                for (int jj = 0; jj < 4; ++jj) {
+                                    const int64_t tt = (int64_t)A * pv[jj] + (int64_t)C * cv[jj];
+                                    t32[4 * i + jj] = (int32_t)(tt / (int64_t)gg);
+                                }
+                            }
+                        }
+                    }
                 }
             }
             const bool bal = ok && !nz;
-            bool norm = ok && nz && !ovf;
+            const bool norm = ok && nz && !ovf;
             if (ovf && gl == 0) ++n_ovf;
             if (bal && gl == 0) {
                 ++n_bal;  // all metabolites stable: to the arbiter
@@ -570,45 +797,7 @@ __global__ void __launch_bounds__(kExpandWarps * 32, (CPL <= 2 ? 3 : 2)) expand_
             }
             fatal = group_or<G>(fatal ? 1u : 0u) != 0;
 
-            // --- superset pruning (group-cooperative scan) ---
-            if (__any_sync(FULL, norm)) {
-                int64_t b1 = 0, n1 = 0, b2 = 0, n2 = 0;
-                if (norm) {
-                    if (!in_u) {
-                        b1 = a.bptr[k];
-                        n1 = a.bptr[k + 1] - b1;
-                    }
-                    b2 = a.recent_begin;
-                    n2 = a.recent_end - a.recent_begin;
-                }
-                const int64_t len = n1 + n2;
-                int64_t wl = len;
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    const int64_t y = __shfl_xor_sync(FULL, wl, off);
-                    wl = y > wl ? y : wl;
-                }
-                bool pr = false;
-                for (int64_t i0 = 0; i0 < wl; i0 += G) {
-                    const int64_t i = i0 + gl;
-                    bool hit = false;
-                    if (i < len && !pr) {
-                        const int64_t r = i < n1 ? (int64_t)a.bidx[b1 + i] : b2 + (i - n1);
-                        const uint64_t *E = a.res + (size_t)r * W;
-                        hit = true;
-                        for (int w = 0; w < W && hit; ++w) hit = (E[w] & ~child_word(pu, w, k)) == 0;
-                    }
-                    // every lane must take part in the shuffle: no short-circuit here
-                    const uint32_t any_hit = group_or<G>(hit ? 1u : 0u);
-                    pr = pr || any_hit != 0;
-                }
-                if (norm && pr) {
-                    norm = false;
-                    if (gl == 0) ++n_pruned;
-                }
-            }
-
-            // --- pivot key and fingerprint of the new state ---
+            // --- pivot key and fingerprint, then append to the batch ---
             uint32_t key = 0xFFFFFFFFu, hlo = 0, hhi = 0;
             if (norm) {
 #pragma unroll
@@ -626,115 +815,36 @@ __global__ void __launch_bounds__(kExpandWarps * 32, (CPL <= 2 ? 3 : 2)) expand_
                 for (int w = gl; w < W; w += G) {
                     const uint64_t x = mix64(child_word(pu, w, k) ^ (0x2545f4914f6cdd1dull * (uint64_t)(w + 1)));
                     hlo += (uint32_t)x;
-                    hhi += (uint32_t)(x >> 32);
+                    hhi ^= (uint32_t)(x >> 32);
                 }
             }
             key = group_min<G>(key);
             hlo = group_add<G>(hlo);
-            hhi = group_add<G>(hhi);
-
-            // --- dedup and compaction: claim / write / publish / compare ---
-            uint64_t pos = 0;
-            uint32_t tag = 0;
-            slot_tag_pos(((uint64_t)hhi << 32) | hlo, a.slot_mask, pos, tag);
-            bool todo = norm && !full;  // group-uniform
-            uint64_t probes = 0;
-            int spins = 0;
-            const int pc1 = pc + (in_u ? 0 : 1);
-            int rounds = 0;
-            while (__any_sync(FULL, todo)) {
-                const bool expired = ++rounds > kMaxRounds || global_ns() - t_start > kWatchdogNs;
-                if (__any_sync(FULL, expired)) {  // warp-uniform decision
-                    if (lane == 0) record_diag(a.ctr, ERR_WATCHDOG, 2, rounds, kMaxRounds, a.level);
-                    fatal = true;
-                    break;
-                }
-                unsigned long long v = kEmpty;
-                if (todo && gl == 0) v = cas_acquire(&a.slots[pos], kEmpty, ((unsigned long long)tag << 32) | kPending);
-                v = __shfl_sync(FULL, v, lead);
-                const bool won = todo && v == kEmpty;
-                const bool other = todo && !won && (uint32_t)(v >> 32) != tag;
-                const bool waiting = todo && !won && !other && (uint32_t)v == kPending;
-                const bool over = todo && !won && !other && (uint32_t)v == kOverflowIdx;
-                const bool cmp = todo && !won && !other && !waiting && !over;
-                if (other) {
-                    pos = (pos + 1) & a.slot_mask;
-                    if (++probes > a.slot_mask) {
-                        if (gl == 0) atomicOr(&a.ctr[C_ERR], (unsigned long long)ERR_TABLE_FULL);
-                        todo = false;
-                        fatal = true;
-                    }
-                }
-                if (over) todo = false;
-                const unsigned wmask = __ballot_sync(FULL, won && gl == 0);
-                if (wmask) {
-                    const int leader = __ffs((int)wmask) - 1;
-                    unsigned long long base_idx = 0;
-                    if (lane == leader) base_idx = atomicAdd(&a.ctr[C_NEXT], (unsigned long long)__popc(wmask));
-                    base_idx = __shfl_sync(FULL, base_idx, leader);
-                    const uint64_t idx = base_idx + (uint64_t)__popc(wmask & ((1u << lead) - 1u));
-                    if (won) {
-                        if ((int64_t)idx >= a.child.cap) {
-                            full = true;  // level truncated: stop claiming
-                            if (gl == 0)
-                                store_release(&a.slots[pos], ((unsigned long long)tag << 32) | kOverflowIdx);
-                        } else {
-                            int4 *db = reinterpret_cast<int4 *>(a.child.B + (size_t)idx * Mpad);
+            hhi = group_xor<G>(hhi);
+            const unsigned nm = __ballot_sync(FULL, norm && gl == 0);
+            if (norm) {
+                const int slot = nb + __popc(nm & ((1u << lead) - 1u));
+                int4 *r = brow + (size_t)slot * BS::ROW;
 #pragma unroll
-                            for (int i = 0; i < CPL; ++i)
-                                db[gl + G * i] =
-                                    make_int4(t32[4 * i + 0], t32[4 * i + 1], t32[4 * i + 2], t32[4 * i + 3]);
-                            uint64_t *du = a.child.U + (size_t)idx * W;
-                            for (int w = gl; w < W; w += G) du[w] = child_word(pu, w, k);
-                            if (gl == 0) a.child.meta[idx] = pack_meta(key, pc1);
-                        }
-                        todo = false;
-                    }
-                    __syncwarp();  // the group's row writes precede the leader's release store
-                    if (won && gl == 0 && (int64_t)idx < a.child.cap) {
-                        store_release(&a.slots[pos], ((unsigned long long)tag << 32) | idx);
-                        deg_sum += key >> 16;
-                    }
-                    full = group_or<G>(full ? 1u : 0u) != 0;
+                for (int i = 0; i < CPL; ++i)
+                    r[gl + G * i] = make_int4(t32[4 * i + 0], t32[4 * i + 1], t32[4 * i + 2], t32[4 * i + 3]);
+                if (gl == 0) {
+                    uint64_t pos;
+                    uint32_t tag;
+                    slot_tag_pos(((uint64_t)hhi << 32) | hlo, a.slot_mask, pos, tag);
+                    bpos[slot] = pos;
+                    btag[slot] = tag;
+                    bkey[slot] = key;
+                    binfo[slot] = (uint32_t)k | (in_u ? 1u << 12 : 0u) | ((uint32_t)(pc + (in_u ? 0 : 1)) << 13);
+                    bpar[slot] = (uint32_t)p;
                 }
-                if (__any_sync(FULL, cmp)) {
-                    bool eq = cmp;
-                    if (cmp) {
-                        const uint32_t ci = (uint32_t)v;
-                        const int4 *sb = reinterpret_cast<const int4 *>(a.child.B + (size_t)ci * Mpad);
-#pragma unroll
-                        for (int i = 0; i < CPL; ++i) {
-                            const int4 s = __ldcg(sb + gl + G * i);
-                            eq = eq && s.x == t32[4 * i + 0] && s.y == t32[4 * i + 1] && s.z == t32[4 * i + 2] &&
-                                 s.w == t32[4 * i + 3];
-                        }
-                        const uint64_t *su = a.child.U + (size_t)ci * W;
-                        for (int w = gl; w < W && eq; w += G) eq = __ldcg(su + w) == child_word(pu, w, k);
-                    }
-                    const bool neq = group_or<G>((cmp && !eq) ? 1u : 0u) != 0;
-                    if (cmp) {
-                        if (!neq) {
-                            todo = false;  // duplicate of a state already in the frontier
-                        } else {
-                            pos = (pos + 1) & a.slot_mask;
-                            ++probes;
-                        }
-                    }
-                }
-                if (__any_sync(FULL, waiting)) {
-                    if (waiting && ++spins > kSpinLimit) {
-                        if (gl == 0) atomicOr(&a.ctr[C_ERR], (unsigned long long)ERR_TIMEOUT);
-                        todo = false;
-                        fatal = true;
-                    }
-                    __nanosleep(32);
-                }
-                if (full) todo = false;
             }
-            full = __any_sync(FULL, full);
+            nb += __popc(nm);
+            if (nb > NB - NG) flush();
         }
         if (__any_sync(FULL, fatal)) break;
     }
+    if (nb > 0 && !__any_sync(FULL, fatal)) flush();
     if (n_exp) atomicAdd(&a.ctr[C_EXP], n_exp);
     if (n_ovf) atomicAdd(&a.ctr[C_OVF], n_ovf);
     if (n_bal) atomicAdd(&a.ctr[C_BAL], n_bal);
@@ -945,15 +1055,16 @@ __global__ void bucket_scan_kernel(const int32_t *bcnt, int N, int32_t *bptr)
 }
 
 __global__ void bucket_fill_kernel(const uint64_t *res, int64_t n, int W, const int32_t *bptr, int32_t *bfill,
-                                   int32_t *bidx)
+                                   uint64_t *bres)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n * W) return;
     const int w = (int)(i % W);
-    const int32_t r = (int32_t)(i / W);
+    const int64_t r = i / W;
     for (uint64_t x = res[i]; x; x &= x - 1) {
         const int k = w * 64 + __ffsll((long long)x) - 1;
-        bidx[bptr[k] + atomicAdd(&bfill[k], 1)] = r;
+        const int64_t pos = (int64_t)bptr[k] + atomicAdd(&bfill[k], 1);
+        for (int v = 0; v < W; ++v) bres[pos * W + v] = res[r * W + v];
     }
 }
 
@@ -1025,10 +1136,11 @@ template <int G, int CPL>
 cudaError_t launch_expand_t(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s)
 {
     const bool staged = nv.blob_words * 4 <= kStageLimitBytes;
-    const size_t sm = (size_t)(staged ? nv.blob_words : 0) * 4 + 16;
+    const size_t sm = (size_t)(staged ? nv.blob_words : 0) * 4 + 16 + (size_t)kExpandWarps * BatchShape<G, CPL>::BYTES;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(expand_kernel<G, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageLimitBytes + 16);
+        cudaFuncSetAttribute(expand_kernel<G, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kStageLimitBytes + 16 + kExpandWarps * BatchShape<G, CPL>::BYTES);
         attr_set = true;
     }
     expand_kernel<G, CPL><<<grid, kExpandWarps * 32, sm, s>>>(nv, a, staged ? 1 : 0);
@@ -1039,8 +1151,9 @@ template <int G, int CPL>
 int expand_grid_t(const NetView &nv, int sm_count)
 {
     const bool staged = nv.blob_words * 4 <= kStageLimitBytes;
-    const size_t sm = (size_t)(staged ? nv.blob_words : 0) * 4 + 16;
-    cudaFuncSetAttribute(expand_kernel<G, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageLimitBytes + 16);
+    const size_t sm = (size_t)(staged ? nv.blob_words : 0) * 4 + 16 + (size_t)kExpandWarps * BatchShape<G, CPL>::BYTES;
+    cudaFuncSetAttribute(expand_kernel<G, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kStageLimitBytes + 16 + kExpandWarps * BatchShape<G, CPL>::BYTES);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expand_kernel<G, CPL>, kExpandWarps * 32, sm) !=
             cudaSuccess ||
@@ -1119,7 +1232,7 @@ cudaError_t launch_accept(const NetView &nv, const AcceptArgs &a, cudaStream_t s
 }
 
 cudaError_t launch_buckets(const NetView &nv, const uint64_t *res, int64_t n_res, int32_t *bcnt, int32_t *bptr,
-                           int32_t *bfill, int32_t *bidx, cudaStream_t s)
+                           int32_t *bfill, uint64_t *bres, cudaStream_t s)
 {
     cudaError_t e;
     if ((e = cudaMemsetAsync(bcnt, 0, sizeof(int32_t) * (size_t)nv.N, s)) != cudaSuccess) return e;
@@ -1128,7 +1241,7 @@ cudaError_t launch_buckets(const NetView &nv, const uint64_t *res, int64_t n_res
     const int tb = 256;
     if (items > 0) bucket_count_kernel<<<(int)((items + tb - 1) / tb), tb, 0, s>>>(res, n_res, nv.W, bcnt);
     bucket_scan_kernel<<<1, 1024, 0, s>>>(bcnt, nv.N, bptr);
-    if (items > 0) bucket_fill_kernel<<<(int)((items + tb - 1) / tb), tb, 0, s>>>(res, n_res, nv.W, bptr, bfill, bidx);
+    if (items > 0) bucket_fill_kernel<<<(int)((items + tb - 1) / tb), tb, 0, s>>>(res, n_res, nv.W, bptr, bfill, bres);
     return cudaGetLastError();
 }
 
