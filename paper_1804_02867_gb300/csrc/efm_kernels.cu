@@ -440,6 +440,11 @@ __device__ __forceinline__ uint32_t group_xor(uint32_t x)
     return x;
 }
 
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ void store_release(unsigned long long *p, unsigned long long v)
 {
     asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -559,7 +564,7 @@ __global__ void __launch_bounds__(kExpandWarps * 32, (CPL <= 2 ? 3 : 2)) expand_
         uint64_t probes = 0;
         int spins = 0, rounds = 0;
         while (__any_sync(FULL, todo)) {
-            const bool expired = ++rounds > kMaxRounds || global_ns() - t_start > kWatchdogNs;
+            const bool expired = ++rounds > kMaxRounds || ((rounds & 63) == 0 && global_ns() - t_start > kWatchdogNs);
             if (__any_sync(FULL, expired)) {  // warp-uniform decision
                 if (lane == 0) record_diag(a.ctr, ERR_WATCHDOG, 2, rounds, kMaxRounds, a.level);
                 fatal = true;
@@ -649,6 +654,19 @@ __global__ void __launch_bounds__(kExpandWarps * 32, (CPL <= 2 ? 3 : 2)) expand_
     for (int64_t p0 = ((int64_t)blockIdx.x * kExpandWarps + wid) * cpw; p0 < a.n_par; p0 += wstride) {
         const int64_t pl = p0 + lane;
         const bool pin = lane < cpw && pl < a.n_par;
+        // pull this chunk's and the next chunk's parents toward L2
+        if (pin) {
+            const char *rp = reinterpret_cast<const char *>(a.par.B + (size_t)pl * Mpad);
+            for (int off = 0; off < Mpad * 4; off += 128) prefetch_l2(rp + off);
+            prefetch_l2(a.par.U + (size_t)pl * W);
+        }
+        const int64_t pn = pl + wstride;
+        if (lane < cpw && pn < a.n_par) {
+            const char *rp = reinterpret_cast<const char *>(a.par.B + (size_t)pn * Mpad);
+            for (int off = 0; off < Mpad * 4; off += 128) prefetch_l2(rp + off);
+            prefetch_l2(a.par.U + (size_t)pn * W);
+            prefetch_l2(a.par.meta + pn);
+        }
         const uint32_t mj = pin ? a.par.meta[pl] : 0u;
         const int dj = pin ? (int)((mj >> 10) & 0x1FFFu) : 0;
         int incl = dj;
@@ -832,6 +850,7 @@ __global__ void __launch_bounds__(kExpandWarps * 32, (CPL <= 2 ? 3 : 2)) expand_
                     uint64_t pos;
                     uint32_t tag;
                     slot_tag_pos(((uint64_t)hhi << 32) | hlo, a.slot_mask, pos, tag);
+                    prefetch_l2(&a.slots[pos]);
                     bpos[slot] = pos;
                     btag[slot] = tag;
                     bkey[slot] = key;
