@@ -123,6 +123,31 @@ int efm_column_map(const efm_net *net, int32_t *orig_rxn, int8_t *dir);
 int efm_find_pathways(efm_net *net, const int32_t *targets, int32_t n_targets, const efm_limits *limits,
                       const void *model, efm_job **out);
 
+/* Batched traversal: job i enumerates the pathways of targets[i] in
+ * nets[i] (Prop. 1 seeds, the same method and counters as
+ * efm_find_pathways), for thousands of uneven networks in ONE persistent
+ * kernel launch captured in a CUDA graph.  Each CTA of the launch takes jobs
+ * from a device queue and runs a job's whole level loop in its own scratch
+ * slice.  An autotuner picks the CTAs per SM and the queue order (input
+ * order or largest network first) by timing a sample of the jobs, and caches
+ * the choice per (job count, row class, SM count).
+ *  nets[n_jobs]     loaded networks (any mix; all on nets[0]'s stream and
+ *                   device; at most 256 internal metabolites each)
+ *  targets[n_jobs]  target metabolite per job (or -1)
+ *  limits           as efm_find_pathways; max_frontier must be > 0 (it sizes
+ *                   each CTA's frontier arena); each job uses
+ *                   min(max_len, its column count)
+ *  out              one job handle with n_jobs entries for efm_fetch_results
+ * Per-job device errors (capacity, bounded waits) are reported by
+ * efm_fetch_results for that entry.  Per job at most 2^15 distinct balanced
+ * supports and 2^13 results. */
+int efm_find_pathways_batch(efm_net *const *nets, const int32_t *targets, int32_t n_jobs, const efm_limits *limits,
+                            const void *model, efm_job **out);
+
+/* The autotuner's last choice: CTAs per SM and whether the queue runs the
+ * largest networks first.  EFM_EINVAL before any batch ran. */
+int efm_batch_tuning(int32_t *ctas_per_sm, int32_t *largest_first);
+
 /* Copy the results of target number `job_target_idx` (0-based position in
  * the targets array) into `supports` (host memory, capacity rows of W
  * words), sorted by (|U|, ascending column list).  supports == NULL is a

@@ -3,7 +3,10 @@
 // kernels of efm_kernels.cu; this file only prepares static data, sizes
 // buffers, launches and reads back one counter block per level.
 #include <algorithm>
+#include <chrono>
 #include <cstdio>
+#include <map>
+#include <mutex>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -80,6 +83,8 @@ struct efm_net {
 
 struct TargetOut {
     DevBuf sup;
+    const uint64_t *borrowed = nullptr;  // batched jobs: rows inside the job's shared buffer
+    int err = 0;                         // batched jobs: this job's error code (0 = none)
     int64_t n = 0;
     efm_counters ctr{};
     int status = 0;
@@ -90,6 +95,8 @@ struct TargetOut {
 struct efm_job {
     efm_net *net = nullptr;
     std::vector<TargetOut> out;
+    std::vector<int> words;  // batched jobs: support width of each entry
+    DevBuf shared_out;       // batched jobs: output rows of every job
 };
 
 extern "C" int efm_set_allocator(efm_alloc_fn alloc, efm_free_fn free_fn, void *ctx)
@@ -628,19 +635,293 @@ extern "C" int efm_find_pathways(efm_net *net, const int32_t *targets, int32_t n
     return flags;
 }
 
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Scratch slice of one CTA of the batched traversal, sized for the largest
+// network of the batch.
+BatchLayout batch_layout(int64_t cap, int Wmax, int Mpad_max, int Nmax, int max_len_max)
+{
+    BatchLayout L{};
+    L.cap = cap;
+    L.cand_cap = (int64_t)1 << 15;
+    L.res_cap = (int64_t)1 << 13;
+    L.slot_cap = next_pow2(2 * (uint64_t)cap + 64 * (uint64_t)(kBatchThreads / 32));
+    L.cslot_cap = next_pow2(2 * (uint64_t)L.cand_cap);
+    size_t o = 0;
+    for (int i = 0; i < 2; ++i) {
+        L.o_U[i] = o;
+        o = align256(o + (size_t)cap * Wmax * 8);
+        L.o_B[i] = o;
+        o = align256(o + (size_t)cap * Mpad_max * 4);
+        L.o_meta[i] = o;
+        o = align256(o + (size_t)cap * 4);
+    }
+    L.o_slots = o;
+    o = align256(o + L.slot_cap * 8);
+    L.o_cslots = o;
+    o = align256(o + L.cslot_cap * 8);
+    L.o_cand = o;
+    o = align256(o + (size_t)L.cand_cap * Wmax * 8);
+    L.o_res = o;
+    o = align256(o + (size_t)L.res_cap * Wmax * 8);
+    L.o_bcnt = o;
+    o = align256(o + (size_t)Nmax * 4);
+    L.o_bfill = o;
+    o = align256(o + (size_t)Nmax * 4);
+    L.o_bptr = o;
+    o = align256(o + (size_t)(Nmax + 1) * 4);
+    L.o_bres = o;
+    o = align256(o + (size_t)L.res_cap * max_len_max * Wmax * 8);
+    L.o_sort = o;
+    o = align256(o + next_pow2((uint64_t)L.res_cap) * 4);
+    L.slice_bytes = o;
+    return L;
+}
+
+// Autotuner cache: (log2 jobs, largest row class, SMs) -> (CTAs per SM, largest-first order)
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune;
+
+}  // namespace
+
+extern "C" int efm_find_pathways_batch(efm_net *const *nets, const int32_t *targets, int32_t n_jobs,
+                                       const efm_limits *limits, const void *model, efm_job **out)
+{
+    if (!out) return EFM_EINVAL;
+    *out = nullptr;
+    if (!nets || !targets || n_jobs <= 0 || !limits || model) return EFM_EINVAL;
+    const efm_limits lim = *limits;
+    if (lim.max_len < 1 || lim.max_len > EFM_MAX_LEN || lim.max_secondary < 0 || lim.first_k != 0 ||
+        lim.proposal != 0 || lim.max_frontier <= 0)
+        return EFM_EINVAL;
+    int Wmax = 1, Mpad_max = 32, Nmax = 1, Lmax = 1, max_epl = 1;
+    for (int i = 0; i < n_jobs; ++i) {
+        const efm_net *n = nets[i];
+        if (!n || targets[i] < -1 || targets[i] >= n->n_met) return EFM_EINVAL;
+        if (n->nv.EPL > 8) return EFM_EUNSUPPORTED;
+        Wmax = std::max(Wmax, n->nv.W);
+        Mpad_max = std::max(Mpad_max, n->nv.Mpad);
+        Nmax = std::max(Nmax, n->nv.N);
+        Lmax = std::max(Lmax, std::min(lim.max_len, n->nv.N));
+        max_epl = std::max(max_epl, n->nv.EPL);
+    }
+    efm_net *net0 = nets[0];
+    cudaStream_t s = net0->stream;
+    const BatchLayout L = batch_layout(lim.max_frontier + 1, Wmax, Mpad_max, Nmax, Lmax);
+    const int occ = batch_blocks_per_sm();
+    const int sms = net0->sm_count;
+
+    auto *job = new (std::nothrow) efm_job();
+    if (!job) return EFM_ENOMEM;
+    job->net = net0;
+    job->out.resize(n_jobs);
+    job->words.resize(n_jobs);
+    DevBuf pool, djobs, dorder, dctr, dqueue;
+    const size_t out_rows = (size_t)L.res_cap;
+    int rc = EFM_OK;
+    std::vector<BatchJob> hj(n_jobs);
+    std::vector<int> order_in(n_jobs), order_big(n_jobs);
+    std::vector<unsigned long long> hctr((size_t)n_jobs * C_COUNT);
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms = 0.f;
+    int best_per_sm = 1, best_big = 1;
+    BatchArgs ba{};
+
+    if (!dev_alloc(pool, (size_t)sms * occ * L.slice_bytes, s) ||
+        !dev_alloc(djobs, sizeof(BatchJob) * (size_t)n_jobs, s) || !dev_alloc(dorder, 4 * (size_t)n_jobs, s) ||
+        !dev_alloc(dctr, 8 * (size_t)C_COUNT * n_jobs, s) || !dev_alloc(dqueue, 16, s) ||
+        !dev_alloc(job->shared_out, out_rows * Wmax * 8 * (size_t)n_jobs, s)) {
+        rc = EFM_ENOMEM;
+        goto done;
+    }
+    for (int i = 0; i < n_jobs; ++i) {
+        hj[i].nv = nets[i]->nv;
+        hj[i].target = targets[i];
+        hj[i].max_len = std::min(lim.max_len, nets[i]->nv.N);
+        hj[i].out = (uint64_t *)job->shared_out.p + (size_t)i * out_rows * Wmax;
+        hj[i].ctr = (unsigned long long *)dctr.p + (size_t)i * C_COUNT;
+        order_in[i] = i;
+        order_big[i] = i;
+        job->words[i] = nets[i]->nv.W;
+    }
+    // queue schedule "largest first": by the number of split columns times
+    // internal metabolites (a proxy of the traversal's size)
+    std::stable_sort(order_big.begin(), order_big.end(), [&](int x, int y) {
+        return (int64_t)nets[x]->nv.N * nets[x]->nv.M > (int64_t)nets[y]->nv.N * nets[y]->nv.M;
+    });
+    if (cudaMemcpyAsync(djobs.p, hj.data(), sizeof(BatchJob) * n_jobs, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        rc = EFM_ECUDA;
+        goto done;
+    }
+    ba.jobs = (const BatchJob *)djobs.p;
+    ba.order = (const int *)dorder.p;
+    ba.queue = (unsigned int *)dqueue.p;
+    ba.pool = (char *)pool.p;
+    ba.layout = L;
+    ba.max_sec = lim.max_secondary;
+    ba.max_frontier = lim.max_frontier;
+    ba.max_results = lim.max_results;
+    {
+        // autotune (CTAs per SM, queue order) on a sample of the jobs, cached per shape
+        int lg = 0;
+        while ((1 << lg) < n_jobs) ++lg;
+        const auto key = std::make_tuple(lg, max_epl, sms);
+        bool have = false;
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            auto it = g_tune.find(key);
+            if (it != g_tune.end()) {
+                best_per_sm = it->second.first;
+                best_big = it->second.second;
+                have = true;
+            }
+        }
+        if (!have && n_jobs >= 64) {
+            const int sample = std::min(n_jobs, 256);
+            float best = 1e30f;
+            for (int big = 0; big < 2 && rc == EFM_OK; ++big) {
+                const std::vector<int> &ord = big ? order_big : order_in;
+                // a strided sample keeps the size mix of the whole batch
+                std::vector<int> samp(sample);
+                for (int i = 0; i < sample; ++i) samp[i] = ord[(size_t)i * n_jobs / sample];
+                for (int per_sm = 1; per_sm <= occ && rc == EFM_OK; ++per_sm) {
+                    ba.n_jobs = sample;
+                    if (cudaMemcpyAsync(dorder.p, samp.data(), 4 * sample, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                        cudaMemsetAsync(dctr.p, 0, 8 * (size_t)C_COUNT * n_jobs, s) != cudaSuccess ||
+                        cudaMemsetAsync(dqueue.p, 0, 16, s) != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess ||
+                        launch_batch(ba, sms * per_sm, s) != cudaSuccess || cudaEventRecord(e1, s) != cudaSuccess ||
+                        cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                        if (getenv("EFM_DEBUG"))
+                            fprintf(stderr, "efm: batch tuning run failed: %s\n", cudaGetErrorString(cudaGetLastError()));
+                        rc = EFM_ECUDA;
+                        break;
+                    }
+                    if (ms < best) {
+                        best = ms;
+                        best_per_sm = per_sm;
+                        best_big = big;
+                    }
+                }
+            }
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            g_tune[key] = std::make_pair(best_per_sm, best_big);
+        }
+    }
+    if (rc != EFM_OK) goto done;
+    // the batch: one persistent launch, captured in a CUDA graph with its resets
+    ba.n_jobs = n_jobs;
+    if (cudaMemcpyAsync(dorder.p, (best_big ? order_big : order_in).data(), 4 * (size_t)n_jobs,
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        rc = EFM_ECUDA;
+        goto done;
+    }
+    {
+        // capture on a private stream (the caller's may be the legacy default
+        // stream, which cannot be captured); the graph then runs on the caller's
+        cudaStream_t cs = nullptr;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+            rc = EFM_ECUDA;
+            goto done;
+        }
+        bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            ok = cudaMemsetAsync(dctr.p, 0, 8 * (size_t)C_COUNT * n_jobs, cs) == cudaSuccess &&
+                 cudaMemsetAsync(dqueue.p, 0, 16, cs) == cudaSuccess &&
+                 launch_batch(ba, sms * best_per_sm, cs) == cudaSuccess;
+            ok = (cudaStreamEndCapture(cs, &graph) == cudaSuccess) && ok;
+        }
+        ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+        cudaStreamDestroy(cs);
+        if (!ok) {
+            if (getenv("EFM_DEBUG")) fprintf(stderr, "efm: batch graph capture failed: %s\n", cudaGetErrorString(cudaGetLastError()));
+            rc = EFM_ECUDA;
+            goto done;
+        }
+    }
+    if (cudaEventRecord(e0, s) != cudaSuccess || cudaGraphLaunch(exec, s) != cudaSuccess ||
+        cudaEventRecord(e1, s) != cudaSuccess ||
+        cudaMemcpyAsync(hctr.data(), dctr.p, 8 * hctr.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        if (getenv("EFM_DEBUG")) fprintf(stderr, "efm: batch launch failed: %s\n", cudaGetErrorString(cudaGetLastError()));
+        rc = EFM_ECUDA;
+        goto done;
+    }
+    for (int i = 0; i < n_jobs; ++i) {
+        const unsigned long long *h = &hctr[(size_t)i * C_COUNT];
+        TargetOut &o = job->out[i];
+        o.borrowed = hj[i].out;
+        o.err = err_from_bits(h[C_ERR]);
+        if (!o.err && !h[C_DONE]) o.err = EFM_ECUDA;
+        o.n = (int64_t)h[C_OUT_N];
+        efm_counters &c = o.ctr;
+        c.levels = (int64_t)h[C_LEVELS];
+        c.seeds = (int64_t)h[C_SEEDS];
+        c.expansions = (int64_t)h[C_EXP];
+        c.overflow = (int64_t)h[C_OVF];
+        c.balanced = (int64_t)h[C_BAL];
+        c.candidates = (int64_t)h[C_CAND_N];
+        c.results = (int64_t)h[C_RES];
+        c.pruned = (int64_t)h[C_PRUNED];
+        c.frontier = (int64_t)h[C_FRONTIER];
+        c.frontier_max = (int64_t)h[C_FRONTIER_MAX];
+        c.status = (int64_t)h[C_STATUS];
+        o.status = (int)h[C_STATUS];
+        o.total_ms = ms;
+        o.kernel_launches = i == 0 ? 1 : 0;
+    }
+done:
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dev_free(pool, s);
+    dev_free(djobs, s);
+    dev_free(dorder, s);
+    dev_free(dctr, s);
+    dev_free(dqueue, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess && rc == EFM_OK) rc = EFM_ECUDA;
+    if (rc != EFM_OK) {
+        cudaGetLastError();
+        efm_free_job(job);
+        return rc;
+    }
+    int flags = 0;
+    for (auto &o : job->out) flags |= o.status;
+    *out = job;
+    return flags;
+}
+
+extern "C" int efm_batch_tuning(int32_t *ctas_per_sm, int32_t *largest_first)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    if (g_tune.empty()) return EFM_EINVAL;
+    const auto &v = g_tune.rbegin()->second;
+    if (ctas_per_sm) *ctas_per_sm = v.first;
+    if (largest_first) *largest_first = v.second;
+    return EFM_OK;
+}
+
 extern "C" int efm_fetch_results(efm_job *job, int32_t idx, uint64_t *supports, int64_t capacity, int64_t *n_out,
                                  int32_t *words_per_set, efm_counters *ctr)
 {
     if (!job || idx < 0 || idx >= (int32_t)job->out.size()) return EFM_EINVAL;
     TargetOut &o = job->out[idx];
-    const int W = job->net->nv.W;
+    const int W = job->words.empty() ? job->net->nv.W : job->words[idx];
     if (n_out) *n_out = o.n;
     if (words_per_set) *words_per_set = W;
     if (ctr) *ctr = o.ctr;
+    if (o.err) return o.err;
     if (!supports) return o.status;
     if (capacity < o.n) return EFM_ECAPACITY;
     if (o.n > 0) {
-        if (cudaMemcpyAsync(supports, o.sup.p, (size_t)o.n * W * 8, cudaMemcpyDeviceToHost, job->net->stream) !=
+        const void *src = o.borrowed ? (const void *)o.borrowed : o.sup.p;
+        if (cudaMemcpyAsync(supports, src, (size_t)o.n * W * 8, cudaMemcpyDeviceToHost, job->net->stream) !=
                 cudaSuccess ||
             cudaStreamSynchronize(job->net->stream) != cudaSuccess) {
             cudaGetLastError();
@@ -668,6 +949,7 @@ extern "C" void efm_free_job(efm_job *job)
     if (!job) return;
     cudaStream_t s = job->net ? job->net->stream : nullptr;
     for (auto &o : job->out) dev_free(o.sup, s);
+    dev_free(job->shared_out, s);
     cudaStreamSynchronize(s);
     delete job;
 }

@@ -28,6 +28,8 @@ enum {
     C_CAND_N,     // candidate list length (cumulative)
     C_RES_N,      // result list length (cumulative)
     C_ERR,        // ERR_* bits
+    C_OUT_N = 20, // batched traversal: rows written to the job's output
+    C_DONE,       // batched traversal: job finished
     C_DIAG = 24,  // first bounds/watchdog record: code, value, limit, level
     C_COUNT = 32
 };
@@ -92,6 +94,34 @@ struct AcceptArgs {
     unsigned long long *ctr;
 };
 
+// Batched traversal: per-CTA scratch slice layout (byte offsets)
+constexpr int kBatchThreads = 256;
+struct BatchLayout {
+    size_t slice_bytes;
+    size_t o_U[2], o_B[2], o_meta[2];
+    size_t o_slots, o_cslots, o_cand, o_res, o_bcnt, o_bfill, o_bptr, o_bres, o_sort;
+    int64_t cap, cand_cap, res_cap;
+    uint64_t slot_cap, cslot_cap;
+};
+
+struct BatchJob {
+    NetView nv;
+    int target, max_len;
+    uint64_t *out;            // [res_cap][W] sorted supports
+    unsigned long long *ctr;  // [C_COUNT] counters of this job (zeroed by the host)
+};
+
+struct BatchArgs {
+    const BatchJob *jobs;
+    const int *order;         // queue schedule: job index per queue position
+    int n_jobs;
+    unsigned int *queue;      // next queue position (zeroed by the host)
+    char *pool;               // gridDim.x slices of layout.slice_bytes
+    BatchLayout layout;
+    int max_sec;
+    int64_t max_frontier, max_results;
+};
+
 // kernels (efm_kernels.cu)
 cudaError_t launch_seed(const NetView &nv, const LevelArgs &a, int target, cudaStream_t s);
 cudaError_t launch_expand(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s);
@@ -101,5 +131,8 @@ cudaError_t launch_buckets(const NetView &nv, const uint64_t *res, int64_t n_res
 cudaError_t launch_sort_results(const uint64_t *res, int64_t n, int W, uint32_t *idx, int64_t n_pow2,
                                 uint64_t *out, int64_t n_keep, cudaStream_t s);
 int expand_grid(const NetView &nv, int sm_count);
+cudaError_t launch_batch(const BatchArgs &ba, int grid, cudaStream_t s);
+int batch_blocks_per_sm();
+size_t batch_smem_bytes();
 
 }  // namespace efm

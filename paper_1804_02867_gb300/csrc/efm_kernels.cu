@@ -330,11 +330,9 @@ __device__ __forceinline__ void normalise(int64_t (&t64)[EPL], int32_t (&t32)[EP
 // ---------------------------------------------------------------------------
 
 template <int EPL>
-__global__ void __launch_bounds__(kExpandWarps * 32) seed_kernel(NetView nv, LevelArgs a, int target)
+__device__ void seed_range(const NetView &nv, const LevelArgs &a, int target, int gw, int nw)
 {
     const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
     const uint32_t *bl = nv.blob;
     const int W = nv.W;
     unsigned long long n_seed = 0, n_bal = 0, deg_sum = 0;
@@ -386,6 +384,12 @@ __global__ void __launch_bounds__(kExpandWarps * 32) seed_kernel(NetView nv, Lev
         if (n_bal) atomicAdd(&a.ctr[C_BAL], n_bal);
         if (deg_sum) atomicAdd(&a.ctr[C_DEGSUM], deg_sum);
     }
+}
+
+template <int EPL>
+__global__ void __launch_bounds__(kExpandWarps * 32) seed_kernel(NetView nv, LevelArgs a, int target)
+{
+    seed_range<EPL>(nv, a, target, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5);
 }
 
 // ---------------------------------------------------------------------------
@@ -476,33 +480,30 @@ struct BatchShape {
     static constexpr int BYTES = NB * ROW * 16 + NB * 32;
 };
 
+// One level of expansion by the warps worker = 0 .. nworkers-1 (the whole
+// grid, or the warps of one CTA in the batched kernel).  bl: the static
+// network (shared or global); wbase: this warp's batch region.
 template <int G, int CPL>
-__global__ void __launch_bounds__(kExpandWarps * 32, (CPL <= 2 ? 3 : 2)) expand_kernel(NetView nv, LevelArgs a, int staged)
+__device__ void expand_range(const NetView &nv, const LevelArgs &a, const uint32_t *bl, char *wbase, int64_t worker,
+                             int64_t nworkers)
 {
     constexpr int NG = 32 / G;    // children per warp round
     constexpr int EPL = 4 * CPL;  // balance entries per lane
     using BS = BatchShape<G, CPL>;
     constexpr int NB = BS::NB;
-    extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5;
     const int gi = lane / G;  // group in the warp
     const int gl = lane % G;  // lane in the group
     const int lead = gi * G;  // group leader lane
     const int W = nv.W;
     const int Mpad = nv.Mpad;
-    const int blob_words = staged ? nv.blob_words : 0;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + blob_words);
     // per-warp batch: rows, then (pos, tag, key, info, parent) per child
-    char *wbase = reinterpret_cast<char *>(smem + blob_words + 4) + (size_t)wid * BS::BYTES;
     int4 *brow = reinterpret_cast<int4 *>(wbase);
     uint64_t *bpos = reinterpret_cast<uint64_t *>(wbase + NB * BS::ROW * 16);
     uint32_t *btag = reinterpret_cast<uint32_t *>(bpos + NB);
     uint32_t *bkey = btag + NB;
     uint32_t *binfo = bkey + NB;  // k | in_u << 12 | pc1 << 13
     uint32_t *bpar = binfo + NB;  // parent index
-    const uint32_t *bl = stage_blob(nv, smem, mbar, staged != 0, a.ctr);
-    if (bl == nullptr) return;
     const int4 *dcol = reinterpret_cast<const int4 *>(bl + nv.o_dcols);
 
     unsigned long long n_exp = 0, n_ovf = 0, n_bal = 0, n_pruned = 0, deg_sum = 0;
@@ -650,8 +651,8 @@ __global__ void __launch_bounds__(kExpandWarps * 32, (CPL <= 2 ? 3 : 2)) expand_
     // chunks of cpw parents per warp (fewer for small levels, so that the
     // items of a small level spread over all warps)
     const int cpw = a.cpw;
-    const int64_t wstride = (int64_t)gridDim.x * kExpandWarps * cpw;
-    for (int64_t p0 = ((int64_t)blockIdx.x * kExpandWarps + wid) * cpw; p0 < a.n_par; p0 += wstride) {
+    const int64_t wstride = nworkers * cpw;
+    for (int64_t p0 = worker * cpw; p0 < a.n_par; p0 += wstride) {
         const int64_t pl = p0 + lane;
         const bool pin = lane < cpw && pl < a.n_par;
         // pull this chunk's and the next chunk's parents toward L2
@@ -871,6 +872,19 @@ __global__ void __launch_bounds__(kExpandWarps * 32, (CPL <= 2 ? 3 : 2)) expand_
     if (deg_sum) atomicAdd(&a.ctr[C_DEGSUM], deg_sum);
 }
 
+template <int G, int CPL>
+__global__ void __launch_bounds__(kExpandWarps * 32, (CPL <= 2 ? 3 : 2)) expand_kernel(NetView nv, LevelArgs a, int staged)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int wid = threadIdx.x >> 5;
+    const int blob_words = staged ? nv.blob_words : 0;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + blob_words);
+    char *wbase = reinterpret_cast<char *>(smem + blob_words + 4) + (size_t)wid * BatchShape<G, CPL>::BYTES;
+    const uint32_t *bl = stage_blob(nv, smem, mbar, staged != 0, a.ctr);
+    if (bl == nullptr) return;
+    expand_range<G, CPL>(nv, a, bl, wbase, (int64_t)blockIdx.x * kExpandWarps + wid, (int64_t)gridDim.x * kExpandWarps);
+}
+
 // ---------------------------------------------------------------------------
 // a7/a8: exact minimality test by elimination modulo primes, then append.
 // ---------------------------------------------------------------------------
@@ -962,20 +976,21 @@ __device__ bool full_rank_mod_p(const uint32_t *bl, const NetView &nv, const int
     return false;
 }
 
-__global__ void __launch_bounds__(kAcceptWarps * 32) accept_kernel(NetView nv, AcceptArgs a)
+// shared memory of one minimality warp: basis 64x64, columns 64, pivots 64, row map 32
+constexpr int kAcceptWarpWords = 64 * 64 + 64 + 64 + 32;
+
+// Minimality test of the candidates [cand_begin, cand_end) by the warps
+// gw = 0 .. nw-1; ws: this warp's shared-memory scratch (kAcceptWarpWords).
+__device__ void accept_range(const NetView &nv, const AcceptArgs &a, uint32_t *ws, int64_t gw, int64_t nw)
 {
-    extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5;
     const int W = nv.W;
-    uint32_t *basis = smem + wid * (64 * 64);
-    int *cols = reinterpret_cast<int *>(smem + kAcceptWarps * 64 * 64) + wid * 64;
-    int *pivcol = reinterpret_cast<int *>(smem + kAcceptWarps * 64 * 64 + kAcceptWarps * 64) + wid * 64;
-    uint32_t *rowmap = smem + kAcceptWarps * 64 * 64 + 2 * kAcceptWarps * 64 + wid * 32;
+    uint32_t *basis = ws;
+    int *cols = reinterpret_cast<int *>(ws + 64 * 64);
+    int *pivcol = cols + 64;
+    uint32_t *rowmap = reinterpret_cast<uint32_t *>(pivcol + 64);
     const uint32_t *bl = nv.blob;
     unsigned long long n_acc = 0;
-    const int64_t gw = (int64_t)blockIdx.x * kAcceptWarps + wid;
-    const int64_t nw = (int64_t)gridDim.x * kAcceptWarps;
     for (int64_t ci = a.cand_begin + gw; ci < a.cand_end; ci += nw) {
         const uint64_t *U = a.cand + (size_t)ci * W;
         const uint64_t u0 = lane < W ? U[lane] : 0ull;
@@ -1035,6 +1050,14 @@ __global__ void __launch_bounds__(kAcceptWarps * 32) accept_kernel(NetView nv, A
         __syncwarp();
     }
     if (lane == 0 && n_acc) atomicAdd(&a.ctr[C_RES], n_acc);
+}
+
+__global__ void __launch_bounds__(kAcceptWarps * 32) accept_kernel(NetView nv, AcceptArgs a)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int wid = threadIdx.x >> 5;
+    accept_range(nv, a, smem + wid * kAcceptWarpWords, (int64_t)blockIdx.x * kAcceptWarps + wid,
+                 (int64_t)gridDim.x * kAcceptWarps);
 }
 
 // ---------------------------------------------------------------------------
@@ -1141,6 +1164,257 @@ __global__ void gather_kernel(const uint64_t *res, int W, const uint32_t *idx, i
     out[i] = res[(size_t)idx[r] * W + w];
 }
 
+// ---------------------------------------------------------------------------
+// Batched traversal: one persistent launch over many (network, target) jobs.
+// Each CTA pulls jobs from a device queue and runs the whole level loop of a
+// job (seed, expand, minimality test, buckets, sorted output) with CTA
+// barriers between the steps, in its own slice of a scratch pool.  The level
+// decisions (truncation, cap, counters) are those of the single-job host loop.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint64_t next_pow2_dev(uint64_t x)
+{
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// CTA-level bucket rebuild over results [0, n_res)
+__device__ void cta_buckets(const NetView &nv, const uint64_t *res, int64_t n_res, int32_t *bcnt, int32_t *bptr,
+                            int32_t *bfill, uint64_t *bres)
+{
+    const int W = nv.W;
+    for (int i = threadIdx.x; i < nv.N; i += blockDim.x) {
+        bcnt[i] = 0;
+        bfill[i] = 0;
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n_res * W; i += blockDim.x) {
+        const int w = (int)(i % W);
+        for (uint64_t x = res[i]; x; x &= x - 1) atomicAdd(&bcnt[w * 64 + __ffsll((long long)x) - 1], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t run = 0;
+        for (int k = 0; k < nv.N; ++k) {
+            bptr[k] = run;
+            run += bcnt[k];
+        }
+        bptr[nv.N] = run;
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n_res * W; i += blockDim.x) {
+        const int w = (int)(i % W);
+        const int64_t r = i / W;
+        for (uint64_t x = res[i]; x; x &= x - 1) {
+            const int k = w * 64 + __ffsll((long long)x) - 1;
+            const int64_t pos = (int64_t)bptr[k] + atomicAdd(&bfill[k], 1);
+            for (int v = 0; v < W; ++v) bres[pos * W + v] = res[r * W + v];
+        }
+    }
+    __syncthreads();
+}
+
+// CTA-level sort of results [0, n) into out (first n_keep rows)
+__device__ void cta_sort(const uint64_t *res, int64_t n, int W, uint32_t *idx, uint64_t *out, int64_t n_keep)
+{
+    if (n <= 0 || n_keep <= 0) return;
+    const int64_t n2 = (int64_t)next_pow2_dev((uint64_t)n);
+    for (int64_t i = threadIdx.x; i < n2; i += blockDim.x) idx[i] = i < n ? (uint32_t)i : 0xFFFFFFFFu;
+    __syncthreads();
+    for (int64_t k = 2; k <= n2; k <<= 1)
+        for (int64_t j = k >> 1; j > 0; j >>= 1) {
+            for (int64_t i = threadIdx.x; i < n2; i += blockDim.x) {
+                const int64_t l = i ^ j;
+                if (l <= i) continue;
+                const uint32_t x = idx[i], y = idx[l];
+                const bool up = (i & k) == 0;
+                if (support_greater(res, W, x, y) == up) {
+                    idx[i] = y;
+                    idx[l] = x;
+                }
+            }
+            __syncthreads();
+        }
+    for (int64_t i = threadIdx.x; i < n_keep * W; i += blockDim.x) out[i] = res[(size_t)idx[i / W] * W + i % W];
+    __syncthreads();
+}
+
+template <int G, int CPL>
+__device__ void run_job(const BatchArgs &ba, const BatchJob &job, char *slice, uint32_t *sm)
+{
+    constexpr int EPL = G * CPL / 8;  // seed layout: Mpad = 32 EPL = 4 G CPL
+    const NetView &nv = job.nv;
+    unsigned long long *ctr = job.ctr;
+    const int nwarps = blockDim.x >> 5;
+    const int wid = threadIdx.x >> 5;
+    const BatchLayout &L = ba.layout;
+    __shared__ unsigned long long sh[C_COUNT];
+
+    LevelArgs a{};
+    a.slots = reinterpret_cast<unsigned long long *>(slice + L.o_slots);
+    a.cslots = reinterpret_cast<unsigned long long *>(slice + L.o_cslots);
+    a.cslot_mask = L.cslot_cap - 1;
+    a.cand = reinterpret_cast<uint64_t *>(slice + L.o_cand);
+    a.cand_cap = L.cand_cap;
+    a.res = reinterpret_cast<const uint64_t *>(slice + L.o_res);
+    a.bptr = reinterpret_cast<const int32_t *>(slice + L.o_bptr);
+    a.bres = reinterpret_cast<const uint64_t *>(slice + L.o_bres);
+    a.max_len = job.max_len;
+    a.max_sec = ba.max_sec;
+    a.ctr = ctr;
+    auto arena = [&](int i) {
+        Arena r;
+        r.U = reinterpret_cast<uint64_t *>(slice + L.o_U[i]);
+        r.B = reinterpret_cast<int32_t *>(slice + L.o_B[i]);
+        r.meta = reinterpret_cast<uint32_t *>(slice + L.o_meta[i]);
+        r.cap = L.cap;
+        return r;
+    };
+    AcceptArgs acc{};
+    acc.cand = a.cand;
+    acc.res = reinterpret_cast<uint64_t *>(slice + L.o_res);
+    acc.res_cap = L.res_cap;
+    acc.ctr = ctr;
+    int32_t *bcnt = reinterpret_cast<int32_t *>(slice + L.o_bcnt);
+    int32_t *bfill = reinterpret_cast<int32_t *>(slice + L.o_bfill);
+    int32_t *bptr = reinterpret_cast<int32_t *>(slice + L.o_bptr);
+    uint64_t *bres = reinterpret_cast<uint64_t *>(slice + L.o_bres);
+
+    for (uint64_t i = threadIdx.x; i < L.cslot_cap; i += blockDim.x) a.cslots[i] = kEmpty;
+    for (int i = threadIdx.x; i <= nv.N; i += blockDim.x) bptr[i] = 0;
+    __syncthreads();
+    auto read_ctr = [&]() {
+        __syncthreads();
+        for (int i = threadIdx.x; i < C_COUNT; i += blockDim.x) sh[i] = __ldcg(&ctr[i]);
+        __syncthreads();
+    };
+    auto set_ctr = [&](int i, unsigned long long v) {
+        if (threadIdx.x == 0) ctr[i] = v;
+    };
+    const int ERRMASK = ERR_TIMEOUT | ERR_CAND_CAP | ERR_RES_CAP | ERR_TABLE_FULL | ERR_PRIMES | ERR_LEN |
+                        ERR_WATCHDOG | ERR_BOUNDS;
+
+    // level 0: seeds, then the minimality test of balanced seeds
+    int cur = 0;
+    a.level = 0;
+    a.child = arena(cur);
+    seed_range<EPL>(nv, a, job.target, wid, nwarps);
+    read_ctr();
+    if (sh[C_ERR] & ERRMASK) return;
+    acc.cand_begin = 0;
+    acc.cand_end = (int64_t)sh[C_CAND_N];
+    if (wid < kAcceptWarps) accept_range(nv, acc, sm + wid * kAcceptWarpWords, wid, kAcceptWarps);
+    read_ctr();
+    if (sh[C_ERR] & ERRMASK) return;
+    int64_t cand_done = (int64_t)sh[C_CAND_N];
+    int64_t res_n = (int64_t)min(sh[C_RES_N], (unsigned long long)L.res_cap);
+    int64_t n_front = (int64_t)sh[C_NEXT];
+    uint64_t deg_sum = sh[C_DEGSUM];
+    unsigned long long status = 0, frontier = 0, frontier_max = 0, levels = 1;
+    bool stop = false;
+    if (ba.max_frontier > 0 && n_front > ba.max_frontier) {
+        status |= EFM_TRUNCATED;
+        stop = true;
+    } else {
+        frontier += n_front;
+        frontier_max = max(frontier_max, (unsigned long long)n_front);
+        if (ba.max_results > 0 && (int64_t)sh[C_RES] >= ba.max_results) {
+            status |= EFM_CAPPED;
+            stop = true;
+        }
+    }
+    int64_t res_prev_level_begin = 0, built_for = 0;
+    for (int level = 1; !stop && n_front > 0; ++level) {
+        if (level > a.max_len + a.max_sec + 1) {
+            if (threadIdx.x == 0) atomicOr(&ctr[C_ERR], (unsigned long long)ERR_WATCHDOG);
+            return;
+        }
+        if (res_n != built_for) {
+            cta_buckets(nv, acc.res, res_n, bcnt, bptr, bfill, bres);
+            built_for = res_n;
+        }
+        const uint64_t bound = min(deg_sum, (uint64_t)L.cap);
+        const uint64_t nslots = min(L.slot_cap, next_pow2_dev(2 * bound + 64 * (uint64_t)nwarps));
+        for (uint64_t i = threadIdx.x; i < nslots; i += blockDim.x) a.slots[i] = kEmpty;
+        set_ctr(C_NEXT, 0);
+        set_ctr(C_DEGSUM, 0);
+        __syncthreads();
+        a.par = arena(cur);
+        a.n_par = n_front;
+        a.child = arena(cur ^ 1);
+        a.slot_mask = nslots - 1;
+        a.level = level;
+        a.recent_begin = res_prev_level_begin;
+        a.recent_end = res_n;
+        a.cpw = (int)min((int64_t)32, max((int64_t)1, (n_front + nwarps - 1) / nwarps));
+        expand_range<G, CPL>(nv, a, nv.blob, reinterpret_cast<char *>(sm) + (size_t)wid * BatchShape<G, CPL>::BYTES,
+                             wid, nwarps);
+        read_ctr();
+        if (sh[C_ERR] & ERRMASK) return;
+        acc.cand_begin = cand_done;
+        acc.cand_end = (int64_t)sh[C_CAND_N];
+        if (wid < kAcceptWarps) accept_range(nv, acc, sm + wid * kAcceptWarpWords, wid, kAcceptWarps);
+        read_ctr();
+        if (sh[C_ERR] & ERRMASK) return;
+        cand_done = (int64_t)sh[C_CAND_N];
+        res_prev_level_begin = res_n;
+        res_n = (int64_t)min(sh[C_RES_N], (unsigned long long)L.res_cap);
+        n_front = (int64_t)sh[C_NEXT];
+        deg_sum = sh[C_DEGSUM];
+        levels = level + 1;
+        cur ^= 1;
+        if (ba.max_frontier > 0 && n_front > ba.max_frontier) {
+            status |= EFM_TRUNCATED;
+            break;
+        }
+        frontier += n_front;
+        frontier_max = max(frontier_max, (unsigned long long)n_front);
+        if (ba.max_results > 0 && (int64_t)sh[C_RES] >= ba.max_results) {
+            status |= EFM_CAPPED;
+            break;
+        }
+    }
+    if ((int64_t)sh[C_RES_N] > L.res_cap) {
+        if (threadIdx.x == 0) atomicOr(&ctr[C_ERR], (unsigned long long)ERR_RES_CAP);
+        return;
+    }
+    const int64_t n_keep = ba.max_results > 0 ? min(res_n, ba.max_results) : res_n;
+    cta_sort(acc.res, res_n, nv.W, reinterpret_cast<uint32_t *>(slice + L.o_sort), job.out, n_keep);
+    if (sh[C_OVF]) status |= EFM_OVERFLOW_DROPPED;
+    set_ctr(C_LEVELS, levels);
+    set_ctr(C_FRONTIER, frontier);
+    set_ctr(C_FRONTIER_MAX, frontier_max);
+    set_ctr(C_STATUS, status);
+    set_ctr(C_OUT_N, (unsigned long long)n_keep);
+    set_ctr(C_DONE, 1ull);
+}
+
+__global__ void __launch_bounds__(kBatchThreads) batch_kernel(BatchArgs ba)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ int s_job;
+    char *slice = ba.pool + (size_t)blockIdx.x * ba.layout.slice_bytes;
+    for (;;) {
+        if (threadIdx.x == 0) s_job = (int)atomicAdd(ba.queue, 1u);
+        __syncthreads();
+        const int qi = s_job;
+        __syncthreads();
+        if (qi >= ba.n_jobs) break;
+        const BatchJob &job = ba.jobs[ba.order[qi]];
+        switch (job.nv.EPL) {
+        case 1: run_job<4, 2>(ba, job, slice, smem); break;
+        case 2: run_job<8, 2>(ba, job, slice, smem); break;
+        case 4: run_job<16, 2>(ba, job, slice, smem); break;
+        case 8: run_job<32, 2>(ba, job, slice, smem); break;
+        default:
+            if (threadIdx.x == 0) atomicOr(&job.ctr[C_ERR], (unsigned long long)ERR_LEN);
+            break;
+        }
+        __syncthreads();
+    }
+}
+
 template <int EPL>
 cudaError_t launch_seed_t(const NetView &nv, const LevelArgs &a, int target, cudaStream_t s)
 {
@@ -1238,7 +1512,7 @@ cudaError_t launch_accept(const NetView &nv, const AcceptArgs &a, cudaStream_t s
 {
     const int64_t n = a.cand_end - a.cand_begin;
     if (n <= 0) return cudaSuccess;
-    const size_t sm = (size_t)kAcceptWarps * (64 * 64 + 64 + 64 + 32) * 4;
+    const size_t sm = (size_t)kAcceptWarps * kAcceptWarpWords * 4;
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(accept_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -1275,6 +1549,40 @@ cudaError_t launch_sort_results(const uint64_t *res, int64_t n, int W, uint32_t 
         for (int64_t j = k >> 1; j > 0; j >>= 1) bitonic_step_kernel<<<blocks, tb, 0, s>>>(res, W, idx, n2, k, j);
     const int64_t items = n_keep * W;
     gather_kernel<<<(int)((items + tb - 1) / tb), tb, 0, s>>>(res, W, idx, n_keep, out);
+    return cudaGetLastError();
+}
+
+int batch_blocks_per_sm()
+{
+    int per_sm = 0;
+    const size_t sm = batch_smem_bytes();
+    cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBatchThreads, sm) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return per_sm;
+}
+
+size_t batch_smem_bytes()
+{
+    // union of the expansion batches of all warps (largest row class) and the
+    // minimality scratch of kAcceptWarps warps
+    size_t ex = (size_t)BatchShape<4, 2>::BYTES;
+    ex = ex > (size_t)BatchShape<8, 2>::BYTES ? ex : (size_t)BatchShape<8, 2>::BYTES;
+    ex = ex > (size_t)BatchShape<16, 2>::BYTES ? ex : (size_t)BatchShape<16, 2>::BYTES;
+    ex = ex > (size_t)BatchShape<32, 2>::BYTES ? ex : (size_t)BatchShape<32, 2>::BYTES;
+    ex *= (size_t)(kBatchThreads / 32);
+    const size_t ac = (size_t)kAcceptWarps * kAcceptWarpWords * 4;
+    return ex > ac ? ex : ac;
+}
+
+cudaError_t launch_batch(const BatchArgs &ba, int grid, cudaStream_t s)
+{
+    const size_t sm = batch_smem_bytes();
+    cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    batch_kernel<<<grid, kBatchThreads, sm, s>>>(ba);
     return cudaGetLastError();
 }
 

@@ -21,7 +21,7 @@ COUNTER_FIELDS = ("levels", "seeds", "expansions", "overflow", "balanced", "cand
                   "frontier", "frontier_max", "status")
 EXPORTS = ("efm_load_network", "efm_network_shape", "efm_column_map", "efm_find_pathways", "efm_fetch_results",
            "efm_job_timing", "efm_free_job", "efm_free_net", "efm_status_str", "efm_set_allocator",
-           "efm_sort_supports_noalloc")
+           "efm_sort_supports_noalloc", "efm_find_pathways_batch", "efm_batch_tuning")
 EFM_NOALLOC_MAX_ROWS = 1 << 20
 
 
@@ -86,6 +86,11 @@ def load_library(path: str | None = None):
     lib.efm_sort_supports_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
                                               ctypes.c_size_t]
     lib.efm_sort_supports_noalloc.restype = ctypes.c_int
+    lib.efm_find_pathways_batch.argtypes = [_P(ctypes.c_void_p), _P(ctypes.c_int32), ctypes.c_int32, _P(efm_limits),
+                                            ctypes.c_void_p, _P(ctypes.c_void_p)]
+    lib.efm_find_pathways_batch.restype = ctypes.c_int
+    lib.efm_batch_tuning.argtypes = [_P(ctypes.c_int32), _P(ctypes.c_int32)]
+    lib.efm_batch_tuning.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -153,6 +158,25 @@ def efm_find_pathways(net, targets, max_len, max_secondary, max_results=0, max_f
     if rc < 0:
         raise EfmError(rc, "efm_find_pathways")
     return job.value, rc
+
+
+def efm_find_pathways_batch(nets, targets, max_len, max_secondary, max_results=0, max_frontier=1 << 12):
+    """One job per (net handle, target) in one persistent launch.
+    Returns (job handle, OR of warning flags)."""
+    hs = (ctypes.c_void_p * len(nets))(*[ctypes.c_void_p(h) for h in nets])
+    tg, ptg = _arr(targets, np.int32, ctypes.c_int32)
+    lim = efm_limits(int(max_len), int(max_secondary), int(max_results), int(max_frontier), 0, 0)
+    job = ctypes.c_void_p()
+    rc = load_library().efm_find_pathways_batch(hs, ptg, len(tg), ctypes.byref(lim), None, ctypes.byref(job))
+    if rc < 0:
+        raise EfmError(rc, "efm_find_pathways_batch")
+    return job.value, rc
+
+
+def efm_batch_tuning():
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    rc = load_library().efm_batch_tuning(ctypes.byref(a), ctypes.byref(b))
+    return (a.value, b.value) if rc == 0 else None
 
 
 def efm_fetch_results(job, idx, copy=True, out=None):

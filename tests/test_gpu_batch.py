@@ -1,0 +1,66 @@
+"""Batched traversal (one persistent, graph-captured launch over many uneven
+networks): every job's supports and counters equal the CPU oracle's and the
+single-job path's."""
+import numpy as np
+import pytest
+
+from paper_1804_02867_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def efm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1804_02867_gb300 import build, efmgraph
+
+    build.build()
+    efmgraph.load_library()
+    return efmgraph
+
+
+def _batch(efm, nets, L, S, budget, max_results=0):
+    handles = [efm.Network(n) for n in nets]
+    try:
+        targets = [n.targets[0] for n in nets]
+        job, _ = efm.efm_find_pathways_batch([h.handle for h in handles], targets, L, S, max_results, budget)
+        out = []
+        for i in range(len(nets)):
+            sup, ctr, _ = efm.efm_fetch_results(job, i)
+            out.append((sup, ctr))
+        efm.efm_free_job(job)
+        return out
+    finally:
+        for h in handles:
+            h.close()
+
+
+@pytest.mark.parametrize("budget", [2**10, 2**12])
+def test_batch_matches_oracle(oracle_lib, efm, budget):
+    nets = [synth.batched_member(i) for i in range(96)]
+    got = _batch(efm, nets, 30, 4, budget)
+    for net, (sup, ctr) in zip(nets, got):
+        L = min(30, net.split_columns())
+        osup, octr = oracle_lib.enumerate_pathways(net, net.targets[0], oracle_lib.Limits(L, 4, 0, budget))
+        assert np.array_equal(sup, osup), net.name
+        assert ctr == octr, (net.name, ctr, octr)
+
+
+def test_batch_matches_single_job_path(efm):
+    nets = [synth.batched_member(1000 + i) for i in range(40)] + [synth.tiny(i) for i in range(8)]
+    got = _batch(efm, nets, 12, 2, 2**11)
+    for net, (sup, ctr) in zip(nets, got):
+        L = min(12, net.split_columns())
+        with efm.Network(net) as nw:
+            (ssup, sctr), = efm.enumerate_targets(nw, [net.targets[0]], L, 2, 0, 2**11)
+        assert np.array_equal(sup, ssup) and ctr == sctr, net.name
+
+
+def test_batch_autotuner_reports_choice(efm):
+    nets = [synth.batched_member(2000 + i) for i in range(80)]
+    _batch(efm, nets, 20, 2, 2**9)
+    tune = efm.efm_batch_tuning()
+    assert tune is not None and tune[0] >= 1 and tune[1] in (0, 1)
