@@ -46,9 +46,10 @@
  *  Search (breadth first by level; level 0 = seeds; level l expands the
  *  frontier F_{l-1}):
  *    - a balanced support is judged once per job (a set of seen supports);
- *    - a non-balanced child whose support contains a result accepted at a
- *      level < l is pruned (any balanced descendant would contain that
- *      result, so it could not be minimal);
+ *    - a non-balanced child whose new column k completes the support of a
+ *      result accepted at a level < l (k in E, E contained in U + {k}) is
+ *      pruned: any balanced descendant would contain that result, so it could
+ *      not be minimal (secondary steps, k already in U, are never pruned);
  *    - F_l = distinct (U, EF) among the remaining children (equal keys at
  *      one level have equal sec);
  *    - if |F_l| > max_frontier (> 0): status TRUNCATED, stop; results of
@@ -728,13 +729,15 @@ static int judge(or_run *R, const uint64_t *U, int64_t level)
     return OR_OK;
 }
 
-/* superset rule against results accepted before `level` */
-static int contains_result(const or_run *R, const uint64_t *U, int64_t level)
+/* superset rule: the step that adds column k completes the support of a
+ * result accepted before `level` (k in E and E contained in U + {k}) */
+static int completes_result(const or_run *R, const uint64_t *U, int k, int64_t level)
 {
     int W = R->g->W;
     for (size_t r = 0; r < R->results.n; ++r) {
         const uint64_t *E = (const uint64_t *)vec_at(&R->results, r);
         if ((int64_t)E[W] >= level) continue;
+        if (!bit_test(E, k)) continue;
         int sub = 1;
         for (int w = 0; w < W; ++w)
             if (E[w] & ~U[w]) { sub = 0; break; }
@@ -880,7 +883,7 @@ int oracle_enumerate(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, const
                     if ((rc = judge(&R, U2, level)) != OR_OK) goto done;
                     continue;
                 }
-                if (contains_result(&R, U2, level)) {
+                if (!in_u && completes_result(&R, U2, k, level)) {
                     ctr->pruned++;
                     continue;
                 }

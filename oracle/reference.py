@@ -187,7 +187,8 @@ def enumerate_reference(net, target, max_len=64, max_secondary=4, max_results=0,
                     ctr["balanced"] += 1
                     judge(U2, level)
                     continue
-                if any((E & ~U2) == 0 for E, lv in results if lv < level):
+                # the new column completes a result accepted at an earlier level
+                if not in_u and any((E >> k) & 1 and (E & ~U2) == 0 for E, lv in results if lv < level):
                     ctr["pruned"] += 1
                     continue
                 key = (U2, nef)

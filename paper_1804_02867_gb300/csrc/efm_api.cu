@@ -332,7 +332,7 @@ namespace {
 // Device buffers of one traversal, reused across the targets of a job.
 struct Work {
     DevBuf U[2], B[2], meta[2];
-    DevBuf slots, cslots, cand, res, bcnt, bfill, bptr, bres, ctr, sortidx;
+    DevBuf slots, cslots, cand, res, bcnt, bfill, bptr, bres, ctr, sortidx, rcols;
     int64_t F_cap = 0, cand_cap = 0, res_cap = 0, bres_cap = 0;  // bres_cap in bucket entries
     uint64_t slot_cap = 0, cslot_cap = 0, sort_cap = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -345,7 +345,7 @@ void free_work(Work &w, cudaStream_t s)
         dev_free(w.B[i], s);
         dev_free(w.meta[i], s);
     }
-    DevBuf *bufs[] = {&w.slots, &w.cslots, &w.cand, &w.res, &w.bcnt, &w.bfill, &w.bptr, &w.bres, &w.ctr, &w.sortidx};
+    DevBuf *bufs[] = {&w.slots, &w.cslots, &w.cand, &w.res, &w.bcnt, &w.bfill, &w.bptr, &w.bres, &w.ctr, &w.sortidx, &w.rcols};
     for (DevBuf *b : bufs) dev_free(*b, s);
     for (auto &e : w.ev)
         if (e) cudaEventDestroy(e);
@@ -375,6 +375,7 @@ int alloc_work(Work &w, const efm_net *net, const efm_limits &lim, int total_war
     ok = ok && dev_alloc(w.bfill, (size_t)nv.N * 4, s);
     ok = ok && dev_alloc(w.bptr, (size_t)(nv.N + 1) * 4, s);
     ok = ok && dev_alloc(w.ctr, C_COUNT * 8, s);
+    if (nv.W > 2) ok = ok && dev_alloc(w.rcols, (size_t)w.res_cap * kRcolStride * 2, s);
     for (auto &e : w.ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -421,6 +422,8 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
     a.res = (const uint64_t *)w.res.p;
     a.bptr = (const int32_t *)w.bptr.p;
     a.bres = nullptr;
+    a.bids = nullptr;
+    a.rcols = nv.W > 2 ? (const uint16_t *)w.rcols.p : nullptr;
     a.max_len = lim.max_len;
     a.max_sec = lim.max_secondary;
     a.ctr = ctr;
@@ -448,6 +451,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
     acc.cand = (const uint64_t *)w.cand.p;
     acc.res = (uint64_t *)w.res.p;
     acc.res_cap = w.res_cap;
+    acc.rcols = nv.W > 2 ? (uint16_t *)w.rcols.p : nullptr;
     acc.ctr = ctr;
     auto read_ctr = [&]() -> int {
         if (cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -489,7 +493,6 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
             stop = true;
         }
     }
-    int64_t res_prev_level_begin = 0;  // results accepted by the previous level
     unsigned long long exp_before = 0;
     int64_t buckets_built_for = 0;
     float ms = 0.f;
@@ -507,6 +510,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
                 w.bres_cap = cap;
             }
             a.bres = (const uint64_t *)w.bres.p;
+            a.bids = (const int32_t *)w.bres.p;
             CK(launch_buckets(nv, (const uint64_t *)w.res.p, res_n, (int32_t *)w.bcnt.p, (int32_t *)w.bptr.p,
                               (int32_t *)w.bfill.p, (uint64_t *)w.bres.p, s));
             out.kernel_launches += res_n > 0 ? 3 : 1;
@@ -522,8 +526,6 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
         a.child = arena(cur ^ 1);
         a.slot_mask = nslots - 1;
         a.level = level;
-        a.recent_begin = res_prev_level_begin;
-        a.recent_end = res_n;
         CK(cudaEventRecord(w.ev[2], s));
         CK(launch_expand(nv, a, grid, s));
         CK(cudaEventRecord(w.ev[3], s));
@@ -545,7 +547,6 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
         out.kernel_launches += acc.cand_end > acc.cand_begin ? 1 : 0;
         if ((rc = read_ctr())) return rc;
         cand_done = (int64_t)h[C_CAND_N];
-        res_prev_level_begin = res_n;
         res_n = (int64_t)std::min<unsigned long long>(h[C_RES_N], (unsigned long long)w.res_cap);
         n_front = (int64_t)h[C_NEXT];
         deg_sum = h[C_DEGSUM];
@@ -676,6 +677,8 @@ BatchLayout batch_layout(int64_t cap, int Wmax, int Mpad_max, int Nmax, int max_
     o = align256(o + (size_t)L.res_cap * max_len_max * Wmax * 8);
     L.o_sort = o;
     o = align256(o + next_pow2((uint64_t)L.res_cap) * 4);
+    L.o_rcols = o;
+    o = align256(o + (Wmax > 2 ? (size_t)L.res_cap * kRcolStride * 2 : 16));
     L.slice_bytes = o;
     return L;
 }

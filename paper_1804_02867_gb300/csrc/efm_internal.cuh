@@ -79,17 +79,21 @@ struct LevelArgs {
     int64_t cand_cap;
     const uint64_t *res;        // [res_cap][W]
     const int32_t *bptr;        // [N + 1] result buckets by column
-    const uint64_t *bres;       // bucket entries: the result's W support words
-    int64_t recent_begin, recent_end;  // results of the previous level
+    const uint64_t *bres;       // bucket entries: the result's W support words (W <= 2)
+    const int32_t *bids;        // bucket entries: result ids (W > 2), same buffer as bres
+    const uint16_t *rcols;      // per result: column count, then its columns (stride kRcolStride)
     int level, max_len, max_sec;
     int cpw;                    // parents per warp chunk (1..32)
     unsigned long long *ctr;
 };
 
+constexpr int kRcolStride = 65;  // column count + up to 64 columns per result
+
 struct AcceptArgs {
     const uint64_t *cand;
     int64_t cand_begin, cand_end;
     uint64_t *res;
+    uint16_t *rcols;            // written on accept when non-null
     int64_t res_cap;
     unsigned long long *ctr;
 };
@@ -99,7 +103,7 @@ constexpr int kBatchThreads = 256;
 struct BatchLayout {
     size_t slice_bytes;
     size_t o_U[2], o_B[2], o_meta[2];
-    size_t o_slots, o_cslots, o_cand, o_res, o_bcnt, o_bfill, o_bptr, o_bres, o_sort;
+    size_t o_slots, o_cslots, o_cand, o_res, o_bcnt, o_bfill, o_bptr, o_bres, o_sort, o_rcols;
     int64_t cap, cand_cap, res_cap;
     uint64_t slot_cap, cslot_cap;
 };
@@ -127,7 +131,7 @@ cudaError_t launch_seed(const NetView &nv, const LevelArgs &a, int target, cudaS
 cudaError_t launch_expand(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_accept(const NetView &nv, const AcceptArgs &a, cudaStream_t s);
 cudaError_t launch_buckets(const NetView &nv, const uint64_t *res, int64_t n_res, int32_t *bcnt, int32_t *bptr,
-                           int32_t *bfill, uint64_t *bres, cudaStream_t s);
+                           int32_t *bfill, uint64_t *bres, cudaStream_t s);  // W > 2: bres holds int32 ids
 cudaError_t launch_sort_results(const uint64_t *res, int64_t n, int W, uint32_t *idx, int64_t n_pow2,
                                 uint64_t *out, int64_t n_keep, cudaStream_t s);
 int expand_grid(const NetView &nv, int sm_count);

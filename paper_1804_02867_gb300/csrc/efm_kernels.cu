@@ -269,18 +269,19 @@ __device__ __noinline__ GcdMax raw_gcd_max(const int4 *prow4, const int4 *col4, 
     return r;
 }
 
-// Supports of more than two words: is some result with bucket/recent
-// position in [i0, i1) a subset of U + {k}?
-__device__ __noinline__ bool subset_scan_wide(const LevelArgs &a, int W, const uint64_t *pu, int k, int64_t b1,
-                                              int64_t n1, int64_t i0, int64_t i1)
+// Supports of more than two words: does the result with bucket position i
+// (id list, column lists) lie inside U + {k}?  Its columns are probed
+// independently (no early exit), so the loads overlap.
+__device__ __forceinline__ bool result_inside_wide(const LevelArgs &a, const uint64_t *pu, int k, int64_t i)
 {
-    for (int64_t i = i0; i < i1; ++i) {
-        const uint64_t *E = i < n1 ? a.bres + (size_t)(b1 + i) * W : a.res + (size_t)(a.recent_begin + i - n1) * W;
-        bool sub = true;
-        for (int w = 0; w < W && sub; ++w) sub = (__ldg(E + w) & ~child_word(pu, w, k)) == 0;
-        if (sub) return true;
+    const uint16_t *lst = a.rcols + (size_t)a.bids[i] * kRcolStride;
+    const int n = lst[0];
+    bool sub = true;
+    for (int j = 1; j <= n; ++j) {
+        const int c = lst[j];
+        sub = sub && (c == k || bit_of(pu, c));
     }
-    return false;
+    return sub;
 }
 
 // pivot key (degree << 16 | row) -> state meta: row | degree << 10 | |U| << 23
@@ -512,8 +513,115 @@ __device__ void expand_range(const NetView &nv, const LevelArgs &a, const uint32
     int nb = 0;         // children in the batch (warp-uniform)
     const uint64_t t_start = global_ns();
 
+    // Phase 2 for wide rows (more than 32 chunks): the whole warp prunes,
+    // claims and copies or compares one batched child at a time.
+    auto flush_wide = [&]() {
+        __syncwarp();
+        for (int b = 0; b < nb; ++b) {
+            const uint32_t info = binfo[b];
+            const int k = (int)(info & 0xFFFu);
+            const bool in_u = (info >> 12) & 1u;
+            const uint64_t *pu = a.par.U + (size_t)bpar[b] * W;
+            // superset pruning: lanes take the results containing k in parallel
+            const int64_t b1 = in_u ? 0 : a.bptr[k];
+            const int64_t n = in_u ? 0 : a.bptr[k + 1] - b1;
+            bool pr = false;
+            for (int64_t i0 = 0; i0 < n && !pr; i0 += 32) {
+                const int64_t i = i0 + lane;
+                bool sub = false;
+                if (i < n) {
+                    if (W > 2) {
+                        sub = result_inside_wide(a, pu, k, b1 + i);
+                    } else {
+                        const uint64_t *E = a.bres + (size_t)(b1 + i) * W;
+                        sub = true;
+                        for (int w = 0; w < W && sub; ++w) sub = (__ldg(E + w) & ~child_word(pu, w, k)) == 0;
+                    }
+                }
+                pr = __any_sync(FULL, sub);
+            }
+            if (pr) {
+                if (lane == 0) ++n_pruned;
+                continue;
+            }
+            if (full) continue;
+            uint64_t pos = bpos[b];
+            const uint32_t tag = btag[b];
+            const int4 *row = brow + (size_t)b * BS::ROW;
+            for (uint64_t probe = 0;; ++probe) {
+                if (probe > a.slot_mask) {
+                    if (lane == 0) atomicOr(&a.ctr[C_ERR], (unsigned long long)ERR_TABLE_FULL);
+                    fatal = true;
+                    break;
+                }
+                unsigned long long v = kEmpty;
+                if (lane == 0) v = cas_acquire(&a.slots[pos], kEmpty, ((unsigned long long)tag << 32) | kPending);
+                v = __shfl_sync(FULL, v, 0);
+                if (v == kEmpty) {
+                    unsigned long long idx = 0;
+                    if (lane == 0) idx = atomicAdd(&a.ctr[C_NEXT], 1ull);
+                    idx = __shfl_sync(FULL, idx, 0);
+                    if ((int64_t)idx >= a.child.cap) {
+                        full = true;
+                        if (lane == 0) store_release(&a.slots[pos], ((unsigned long long)tag << 32) | kOverflowIdx);
+                        break;
+                    }
+                    int4 *db = reinterpret_cast<int4 *>(a.child.B + (size_t)idx * Mpad);
+                    for (int c = lane; c < BS::NCH; c += 32) db[c] = row[c];
+                    uint64_t *du = a.child.U + (size_t)idx * W;
+                    for (int w = lane; w < W; w += 32) du[w] = child_word(pu, w, k);
+                    if (lane == 0) a.child.meta[idx] = pack_meta(bkey[b], (int)(info >> 13));
+                    __threadfence();
+                    __syncwarp();
+                    if (lane == 0) {
+                        store_release(&a.slots[pos], ((unsigned long long)tag << 32) | idx);
+                        deg_sum += bkey[b] >> 16;
+                    }
+                    break;
+                }
+                if ((uint32_t)(v >> 32) != tag) {
+                    pos = (pos + 1) & a.slot_mask;
+                    continue;
+                }
+                int spins = 0;
+                while ((uint32_t)v == kPending && spins < kSpinLimit) {
+                    __nanosleep(64);
+                    ++spins;
+                    if (lane == 0) v = cas_acquire(&a.slots[pos], kEmpty, kEmpty);
+                    v = __shfl_sync(FULL, v, 0);
+                }
+                if ((uint32_t)v == kPending) {
+                    if (lane == 0) atomicOr(&a.ctr[C_ERR], (unsigned long long)ERR_TIMEOUT);
+                    fatal = true;
+                    break;
+                }
+                if ((uint32_t)v == kOverflowIdx) break;
+                const uint32_t ci = (uint32_t)v;
+                const int4 *sb = reinterpret_cast<const int4 *>(a.child.B + (size_t)ci * Mpad);
+                bool eq = true;
+                for (int c = lane; c < BS::NCH && eq; c += 32) {
+                    const int4 x = __ldcg(sb + c), o = row[c];
+                    eq = x.x == o.x && x.y == o.y && x.z == o.z && x.w == o.w;
+                }
+                const uint64_t *su = a.child.U + (size_t)ci * W;
+                for (int w = lane; w < W && eq; w += 32) eq = __ldcg(su + w) == child_word(pu, w, k);
+                if (__all_sync(FULL, eq)) break;  // duplicate of a state already in the frontier
+                pos = (pos + 1) & a.slot_mask;
+            }
+            if (__any_sync(FULL, fatal)) break;
+        }
+        fatal = __any_sync(FULL, fatal);
+        full = __any_sync(FULL, full);
+        nb = 0;
+        __syncwarp();
+    };
+
     // Phase 2: prune and insert the batched children, one lane each.
     auto flush = [&]() {
+        if (BS::NCH > 32) {
+            flush_wide();
+            return;
+        }
         __syncwarp();
         const bool mine = lane < nb;
         const uint32_t info = mine ? binfo[lane] : 0u;
@@ -522,13 +630,11 @@ __device__ void expand_range(const NetView &nv, const LevelArgs &a, const uint32
         const uint64_t *pu = a.par.U + (size_t)(mine ? bpar[lane] : 0u) * W;
         bool todo = mine;
         if (todo) {
-            // superset pruning (counted on a truncated level too): results
-            // containing column k (if new) and every result of the previous
-            // level; the loads of PU entries are issued together
+            // superset pruning (counted on a truncated level too): the new
+            // column k completes a result accepted at an earlier level (the
+            // results containing k, bucket loads issued eight at a time)
             const int64_t b1 = in_u ? 0 : a.bptr[k];
-            const int64_t n1 = in_u ? 0 : a.bptr[k + 1] - b1;
-            const int64_t n2 = a.recent_end - a.recent_begin;
-            const int64_t n = n1 + n2;
+            const int64_t n = in_u ? 0 : a.bptr[k + 1] - b1;
             constexpr int PU = 8;
             bool pr = false;
             uint64_t u0 = 0, u1 = 0;
@@ -542,15 +648,14 @@ __device__ void expand_range(const NetView &nv, const LevelArgs &a, const uint32
 #pragma unroll
                     for (int u = 0; u < PU; ++u) {
                         const int64_t i = i0 + u;
-                        const uint64_t *E = i < n1 ? a.bres + (size_t)(b1 + i) * W
-                                                   : a.res + (size_t)(a.recent_begin + i - n1) * W;
+                        const uint64_t *E = a.bres + (size_t)(b1 + i) * W;
                         e0[u] = i < n ? __ldg(E) : ~0ull;
                         e1[u] = (i < n && W == 2) ? __ldg(E + 1) : 0ull;
                     }
 #pragma unroll
                     for (int u = 0; u < PU; ++u) pr = pr || (((e0[u] & ~u0) | (e1[u] & ~u1)) == 0);
                 } else {
-                    pr = subset_scan_wide(a, W, pu, k, b1, n1, i0, i0 + PU < n ? i0 + PU : n);
+                    for (int64_t i = i0; i < i0 + PU && i < n && !pr; ++i) pr = result_inside_wide(a, pu, k, b1 + i);
                 }
             }
             if (pr) {
@@ -1042,6 +1147,11 @@ __device__ void accept_range(const NetView &nv, const AcceptArgs &a, uint32_t *w
                 uint64_t *dst = a.res + (size_t)idx * W;
                 if (lane < W) dst[lane] = u0;
                 if (lane + 32 < W) dst[lane + 32] = u1;
+                if (a.rcols) {
+                    uint16_t *lst = a.rcols + (size_t)idx * kRcolStride;
+                    for (int j = lane; j < n; j += 32) lst[1 + j] = (uint16_t)cols[j];
+                    if (lane == 0) lst[0] = (uint16_t)n;
+                }
             } else if (lane == 0) {
                 atomicOr(&a.ctr[C_ERR], (unsigned long long)ERR_RES_CAP);
             }
@@ -1106,7 +1216,10 @@ __global__ void bucket_fill_kernel(const uint64_t *res, int64_t n, int W, const 
     for (uint64_t x = res[i]; x; x &= x - 1) {
         const int k = w * 64 + __ffsll((long long)x) - 1;
         const int64_t pos = (int64_t)bptr[k] + atomicAdd(&bfill[k], 1);
-        for (int v = 0; v < W; ++v) bres[pos * W + v] = res[r * W + v];
+        if (W > 2)
+            reinterpret_cast<int32_t *>(bres)[pos] = (int32_t)r;
+        else
+            for (int v = 0; v < W; ++v) bres[pos * W + v] = res[r * W + v];
     }
 }
 
@@ -1209,7 +1322,10 @@ __device__ void cta_buckets(const NetView &nv, const uint64_t *res, int64_t n_re
         for (uint64_t x = res[i]; x; x &= x - 1) {
             const int k = w * 64 + __ffsll((long long)x) - 1;
             const int64_t pos = (int64_t)bptr[k] + atomicAdd(&bfill[k], 1);
-            for (int v = 0; v < W; ++v) bres[pos * W + v] = res[r * W + v];
+            if (W > 2)
+                reinterpret_cast<int32_t *>(bres)[pos] = (int32_t)r;
+            else
+                for (int v = 0; v < W; ++v) bres[pos * W + v] = res[r * W + v];
         }
     }
     __syncthreads();
@@ -1260,6 +1376,8 @@ __device__ void run_job(const BatchArgs &ba, const BatchJob &job, char *slice, u
     a.res = reinterpret_cast<const uint64_t *>(slice + L.o_res);
     a.bptr = reinterpret_cast<const int32_t *>(slice + L.o_bptr);
     a.bres = reinterpret_cast<const uint64_t *>(slice + L.o_bres);
+    a.bids = reinterpret_cast<const int32_t *>(slice + L.o_bres);
+    a.rcols = nv.W > 2 ? reinterpret_cast<const uint16_t *>(slice + L.o_rcols) : nullptr;
     a.max_len = job.max_len;
     a.max_sec = ba.max_sec;
     a.ctr = ctr;
@@ -1275,6 +1393,7 @@ __device__ void run_job(const BatchArgs &ba, const BatchJob &job, char *slice, u
     acc.cand = a.cand;
     acc.res = reinterpret_cast<uint64_t *>(slice + L.o_res);
     acc.res_cap = L.res_cap;
+    acc.rcols = nv.W > 2 ? reinterpret_cast<uint16_t *>(slice + L.o_rcols) : nullptr;
     acc.ctr = ctr;
     int32_t *bcnt = reinterpret_cast<int32_t *>(slice + L.o_bcnt);
     int32_t *bfill = reinterpret_cast<int32_t *>(slice + L.o_bfill);
@@ -1324,7 +1443,7 @@ __device__ void run_job(const BatchArgs &ba, const BatchJob &job, char *slice, u
             stop = true;
         }
     }
-    int64_t res_prev_level_begin = 0, built_for = 0;
+    int64_t built_for = 0;
     for (int level = 1; !stop && n_front > 0; ++level) {
         if (level > a.max_len + a.max_sec + 1) {
             if (threadIdx.x == 0) atomicOr(&ctr[C_ERR], (unsigned long long)ERR_WATCHDOG);
@@ -1345,8 +1464,6 @@ __device__ void run_job(const BatchArgs &ba, const BatchJob &job, char *slice, u
         a.child = arena(cur ^ 1);
         a.slot_mask = nslots - 1;
         a.level = level;
-        a.recent_begin = res_prev_level_begin;
-        a.recent_end = res_n;
         a.cpw = (int)min((int64_t)32, max((int64_t)1, (n_front + nwarps - 1) / nwarps));
         expand_range<G, CPL>(nv, a, nv.blob, reinterpret_cast<char *>(sm) + (size_t)wid * BatchShape<G, CPL>::BYTES,
                              wid, nwarps);
@@ -1358,7 +1475,6 @@ __device__ void run_job(const BatchArgs &ba, const BatchJob &job, char *slice, u
         read_ctr();
         if (sh[C_ERR] & ERRMASK) return;
         cand_done = (int64_t)sh[C_CAND_N];
-        res_prev_level_begin = res_n;
         res_n = (int64_t)min(sh[C_RES_N], (unsigned long long)L.res_cap);
         n_front = (int64_t)sh[C_NEXT];
         deg_sum = sh[C_DEGSUM];
