@@ -53,8 +53,9 @@ extern "C" {
 #define EFM_MAX_LEN 64         /* max_len (pathway length in columns) */
 #define EFM_MAX_COEF 524287    /* |stoichiometric coefficient| */
 
-typedef struct efm_net efm_net; /* opaque, library-owned */
-typedef struct efm_job efm_job; /* opaque, library-owned */
+typedef struct efm_net efm_net;     /* opaque, library-owned */
+typedef struct efm_job efm_job;     /* opaque, library-owned */
+typedef struct efm_model efm_model; /* opaque, library-owned */
 
 /* Limits of one traversal (the MAX_LOOP bound of Sec. 3.2 and the length
  * bound L of Alg. 1, plus level-granular budgets). */
@@ -63,9 +64,17 @@ typedef struct {
     int32_t max_secondary; /* max secondary steps per pathway (Def. 10, Eq. 4), >= 0 */
     int64_t max_results;   /* <= 0: no cap; else stop after the level reaching it (EFM_CAPPED) */
     int64_t max_frontier;  /* <= 0: no budget; else stop when a level exceeds it (EFM_TRUNCATED) */
-    int32_t first_k;       /* reserved, must be 0 */
-    int32_t proposal;      /* reserved, must be 0 */
+    int32_t first_k;       /* 0: every result; K > 0: exactly the K smallest results in the
+                              output order (|U|, then the ascending column list), found by
+                              the same traversal with an exact branch and bound; max_results
+                              must then be 0 (not with the batched call) */
+    int32_t proposal;      /* order of a first-K search: EFM_PLAIN (arena order) or
+                              EFM_LEARNED (scores of the model passed with the call); the
+                              result set is the same either way */
 } efm_limits;
+
+#define EFM_PLAIN 0
+#define EFM_LEARNED 1
 
 /* Counters of one (network, target) traversal; the same definitions as the
  * CPU oracle's.  frontier / frontier_max exclude a truncated level. */
@@ -115,13 +124,14 @@ int efm_column_map(const efm_net *net, int32_t *orig_rxn, int8_t *dir);
  * and compaction, superset pruning) -> exact mod-p minimality test on the
  * network's stream and returns when all targets are done.
  *  targets[n_targets]    : metabolite indices in [0, n_met) or -1
- *  limits                : see efm_limits (first_k and proposal must be 0)
- *  model                 : reserved, must be NULL
+ *  limits                : see efm_limits
+ *  model                 : NULL, or a proposal model (efm_model_create) when
+ *                          limits->proposal is EFM_LEARNED
  *  out                   : receives the job handle (results stay on device
  *                          until fetched or freed)
  * Returns the OR of the warning flags over all targets, or an error. */
 int efm_find_pathways(efm_net *net, const int32_t *targets, int32_t n_targets, const efm_limits *limits,
-                      const void *model, efm_job **out);
+                      const efm_model *model, efm_job **out);
 
 /* Batched traversal: job i enumerates the pathways of targets[i] in
  * nets[i] (Prop. 1 seeds, the same method and counters as
@@ -142,7 +152,7 @@ int efm_find_pathways(efm_net *net, const int32_t *targets, int32_t n_targets, c
  * efm_fetch_results for that entry.  Per job at most 2^15 distinct balanced
  * supports and 2^13 results. */
 int efm_find_pathways_batch(efm_net *const *nets, const int32_t *targets, int32_t n_jobs, const efm_limits *limits,
-                            const void *model, efm_job **out);
+                            const efm_model *model, efm_job **out);
 
 /* The autotuner's last choice: CTAs per SM and whether the queue runs the
  * largest networks first.  EFM_EINVAL before any batch ran. */
@@ -193,6 +203,72 @@ void efm_free_net(efm_net *net);
 #define EFM_NOALLOC_MAX_ROWS (1 << 20)
 int efm_sort_supports_noalloc(const uint64_t *supports_in, int64_t n_rows, int32_t words_per_set,
                               uint64_t *supports_out, uintptr_t cuda_stream);
+
+/* ---- learned proposal of first-K searches -------------------------------
+ * A two-layer MLP scores the parents of each level of a first-K search
+ * (efm_limits.first_k > 0, proposal = EFM_LEARNED); parents are expanded in
+ * descending score.  The search's branch and bound is exact, so the model
+ * changes the order and the time to the answer, never the answer.
+ *   x (128 features, BF16) -> h = relu(W1 x) (256 units, FP32 accumulate on
+ *   the tensor cores) -> s = w2 . h + b2 (FP32); the hidden layer's bias is
+ *   the weight of feature 10, which is constant 1.
+ * Features of a state: see the feature list in the library's kernel source
+ * (counts of unbalanced metabolites, pivot degree, |U|, secondary steps,
+ * lowest columns, a 64-bucket hashed embedding of the support).
+ * Training: binary cross-entropy of s against labels of traced states
+ * (1 = the state's support lies inside a support of the search's answer),
+ * positives weighted by pos_weight, Adam (0.9, 0.999, 1e-8).
+ * Parameters are one FP32 array of EFM_MLP_PARAMS values:
+ *   W1[256][128] (row = hidden unit), then w2[256], then b2.
+ * Not thread-safe; every call runs on the model's stream and returns when
+ * its work is done.  Errors: EFM_EINVAL (bad arguments), EFM_ENOMEM,
+ * EFM_ECUDA, EFM_ETIMEOUT (a bounded device wait gave up). */
+#define EFM_MLP_FEATURES 128
+#define EFM_MLP_HIDDEN 256
+#define EFM_MLP_PARAMS (256 * 128 + 256 + 1)
+
+/* New model with seeded uniform fan-in initialisation (splitmix64 stream;
+ * W1 in +-sqrt(6/128), w2 in +-sqrt(3/256), b2 = 0) and no training rows. */
+int efm_model_create(uint64_t seed, uintptr_t cuda_stream, efm_model **out);
+
+/* Read (write = 0) or replace (write = 1; resets the Adam state) the FP32
+ * parameters; params is a host array of EFM_MLP_PARAMS floats. */
+int efm_model_params(efm_model *model, float *params, int32_t write);
+
+/* Append n training rows: x host [n][128] FP32 (stored as BF16), y host [n]
+ * labels, each 0 or 1. */
+int efm_model_add_rows(efm_model *model, const float *x, const float *y, int64_t n);
+
+/* Training rows held, and how many are labelled 1 (either may be NULL). */
+int efm_model_rows(efm_model *model, int64_t *n_rows, int64_t *n_positive);
+int efm_model_clear_rows(efm_model *model);
+
+/* Scores of n host rows x [n][128] (rounded to BF16) into host scores[n],
+ * through the tensor-core forward kernel. */
+int efm_model_forward(efm_model *model, const float *x, int64_t n, float *scores);
+
+/* Gradient of the mean training loss over all held rows (host grad of
+ * EFM_MLP_PARAMS floats, same layout as the parameters) and the loss;
+ * the parameters are not changed.  dL/dh is rounded to BF16 for the
+ * tensor-core product dW1 = dH^T X. */
+int efm_model_gradient(efm_model *model, float pos_weight, float *grad, float *loss);
+
+/* Adam training over the held rows: `epochs` passes in seeded random order
+ * of 128-row tiles, batch_tiles tiles per step.  last_loss: mean batch loss
+ * of the last epoch (may be NULL). */
+int efm_model_train(efm_model *model, int32_t epochs, int32_t batch_tiles, float lr, float pos_weight, uint64_t seed,
+                    float *last_loss);
+
+/* Training rows from traces: for each target, run the first-K search of
+ * `limits` (first_k > 0, max_results = 0) in plain order, then run it
+ * again and record the features of up to rows_per_level states of every
+ * level's frontier (an evenly strided sample), labelled 1 when the state's
+ * support lies inside a support of the answer.  Targets whose search is
+ * truncated or finds nothing add no rows. */
+int efm_model_trace(efm_model *model, efm_net *net, const int32_t *targets, int32_t n_targets,
+                    const efm_limits *limits, int64_t rows_per_level);
+
+void efm_model_free(efm_model *model);
 
 /* Human-readable name of a status code. */
 const char *efm_status_str(int code);

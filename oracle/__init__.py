@@ -6,7 +6,8 @@ with the CUDA library (``paper_1804_02867_gb300``) and never imports it.
 
 * ``efm_oracle.c``  -- the plain C enumerator (built into ``liboracle.so``);
 * ``reference.py``  -- a pure-Python restatement for tiny inputs;
-* ``bruteforce.py`` -- brute-force EFM enumeration over every support.
+* ``bruteforce.py`` -- brute-force EFM enumeration over every support;
+* ``mlp.py``        -- fp64 forward / gradient of the proposal model.
 """
 from __future__ import annotations
 
@@ -150,3 +151,19 @@ def supports_to_lists(supports) -> list:
                 word ^= low
         out.append(tuple(cols))
     return out
+
+
+def first_k(net, target: int, k: int, max_len: int, max_secondary: int):
+    """The k smallest results (by |U|, then ascending column list) of the
+    traversal with no frontier budget and no cap.
+
+    Results of popcount <= P are exactly the results of the traversal run
+    with max_len = P (every state on a path to such a result has popcount
+    <= P), so the definition is evaluated by deepening P until at least k
+    results of popcount <= P exist (or P = max_len), then keeping the k
+    smallest.  Returns (supports uint64[min(k, n), W], the P used)."""
+    for P in range(1, max_len + 1):
+        sup, _ = enumerate_pathways(net, target, Limits(P, max_secondary, 0, 0))
+        if len(sup) >= k or P == max_len:
+            return sup[:k], P
+    raise AssertionError("unreachable")

@@ -3,6 +3,7 @@
 // kernels of efm_kernels.cu; this file only prepares static data, sizes
 // buffers, launches and reads back one counter block per level.
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <cstdio>
 #include <map>
@@ -97,6 +98,16 @@ struct efm_job {
     std::vector<TargetOut> out;
     std::vector<int> words;  // batched jobs: support width of each entry
     DevBuf shared_out;       // batched jobs: output rows of every job
+};
+
+// Proposal model: FP32 parameters, their gradients and Adam moments, the
+// BF16 operand copy of W1, and the training rows (BF16 feature tiles and
+// labels) collected from traversal traces.
+struct efm_model {
+    cudaStream_t stream = nullptr;
+    DevBuf params, grad, mom, wb, loss, err, X, y, tiles;
+    int64_t n_rows = 0, cap_rows = 0;
+    int step = 0;
 };
 
 extern "C" int efm_set_allocator(efm_alloc_fn alloc, efm_free_fn free_fn, void *ctx)
@@ -333,6 +344,9 @@ namespace {
 struct Work {
     DevBuf U[2], B[2], meta[2];
     DevBuf slots, cslots, cand, res, bcnt, bfill, bptr, bres, ctr, sortidx, rcols;
+    DevBuf perm, fkb;  // first-K search: parent order of a level, bound support
+    DevBuf lx, lscore, lhist, lerr;  // learned order: features, scores, buckets, error flag
+    int64_t lx_rows = 0;
     int64_t F_cap = 0, cand_cap = 0, res_cap = 0, bres_cap = 0;  // bres_cap in bucket entries
     uint64_t slot_cap = 0, cslot_cap = 0, sort_cap = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -345,7 +359,9 @@ void free_work(Work &w, cudaStream_t s)
         dev_free(w.B[i], s);
         dev_free(w.meta[i], s);
     }
-    DevBuf *bufs[] = {&w.slots, &w.cslots, &w.cand, &w.res, &w.bcnt, &w.bfill, &w.bptr, &w.bres, &w.ctr, &w.sortidx, &w.rcols};
+    DevBuf *bufs[] = {&w.slots, &w.cslots, &w.cand, &w.res, &w.bcnt,    &w.bfill, &w.bptr,
+                      &w.bres,  &w.ctr,    &w.sortidx, &w.rcols, &w.perm, &w.fkb,
+                      &w.lx,    &w.lscore, &w.lhist,   &w.lerr};
     for (DevBuf *b : bufs) dev_free(*b, s);
     for (auto &e : w.ev)
         if (e) cudaEventDestroy(e);
@@ -376,6 +392,10 @@ int alloc_work(Work &w, const efm_net *net, const efm_limits &lim, int total_war
     ok = ok && dev_alloc(w.bptr, (size_t)(nv.N + 1) * 4, s);
     ok = ok && dev_alloc(w.ctr, C_COUNT * 8, s);
     if (nv.W > 2) ok = ok && dev_alloc(w.rcols, (size_t)w.res_cap * kRcolStride * 2, s);
+    if (lim.first_k > 0) {
+        ok = ok && dev_alloc(w.perm, F * 4, s);
+        ok = ok && dev_alloc(w.fkb, W * 8, s);
+    }
     for (auto &e : w.ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -401,8 +421,70 @@ int err_from_bits(unsigned long long e)
         }                             \
     } while (0)
 
+// The K smallest results found so far by a first-K search (output order:
+// |U|, then the ascending column list), kept on the host; the K-th is the
+// branch-and-bound of the next expansion launches.
+struct TopK {
+    int K = 0, W = 0;
+    std::vector<uint64_t> rows;  // at most K rows once K were found
+    int pc = 0;                  // |U| of the K-th (0 while fewer than K)
+    std::vector<uint64_t> kth;
+
+    static int popc(const uint64_t *r, int W)
+    {
+        int c = 0;
+        for (int w = 0; w < W; ++w) c += __builtin_popcountll(r[w]);
+        return c;
+    }
+    static bool less(const uint64_t *x, const uint64_t *y, int W)
+    {
+        const int cx = popc(x, W), cy = popc(y, W);
+        if (cx != cy) return cx < cy;
+        for (int w = 0; w < W; ++w) {
+            const uint64_t d = x[w] ^ y[w];
+            if (d) return (x[w] & (d & (~d + 1))) != 0;
+        }
+        return false;
+    }
+    void add(const uint64_t *r, int64_t n)
+    {
+        rows.insert(rows.end(), r, r + (size_t)n * W);
+        const int64_t have = (int64_t)(rows.size() / W);
+        if (have < K) return;
+        std::vector<int64_t> idx((size_t)have);
+        for (int64_t i = 0; i < have; ++i) idx[i] = i;
+        const uint64_t *base = rows.data();
+        const int Wl = W;
+        std::nth_element(idx.begin(), idx.begin() + (K - 1), idx.end(), [&](int64_t i, int64_t j) {
+            return less(base + i * Wl, base + j * Wl, Wl);
+        });
+        std::vector<uint64_t> keep((size_t)K * W);
+        for (int i = 0; i < K; ++i) std::copy(base + idx[i] * W, base + idx[i] * W + W, keep.begin() + (size_t)i * W);
+        kth.assign(base + idx[K - 1] * W, base + idx[K - 1] * W + W);
+        rows.swap(keep);
+        pc = popc(kth.data(), W);
+    }
+};
+
 // One (network, target) traversal.  Level 0 = seeds; level l expands F_{l-1}.
-int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetOut &out)
+// With limits.first_k = K > 0 the traversal is the same, with each level's
+// frontier expanded in chunks (in the order the proposal gives) and an exact
+// branch and bound between chunks: once K results are known, a child that
+// would follow the K-th of them in the output order is not generated, since
+// every descendant keeps or grows its support.
+// Training trace of a first-K search: features of a strided sample of each
+// level's frontier, labelled against the search's answer.
+struct Trace {
+    efm_model *m = nullptr;
+    const uint64_t *ans = nullptr;  // device, n_ans x W
+    int64_t n_ans = 0;
+    int64_t rows_per_level = 0;
+};
+
+bool model_reserve_rows(efm_model *m, int64_t rows);
+
+int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetOut &out,
+               const efm_model *model = nullptr, Trace *trace = nullptr)
 {
     const NetView &nv = net->nv;
     cudaStream_t s = net->stream;
@@ -466,6 +548,10 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
                     (long long)h[C_DIAG + 3]);
         return e;
     };
+    const bool fk = lim.first_k > 0;
+    TopK top;
+    top.K = lim.first_k;
+    top.W = nv.W;
     int rc = read_ctr();
     if (rc) return rc;
     acc.cand_begin = 0;
@@ -475,6 +561,13 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
     if ((rc = read_ctr())) return rc;
     int64_t cand_done = (int64_t)h[C_CAND_N];
     int64_t res_n = (int64_t)std::min<unsigned long long>(h[C_RES_N], (unsigned long long)w.res_cap);
+    if (fk && res_n > 0) {
+        std::vector<uint64_t> fresh((size_t)res_n * nv.W);
+        CK(cudaMemcpyAsync(fresh.data(), w.res.p, fresh.size() * 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        top.add(fresh.data(), res_n);
+        if (top.pc > 0) CK(cudaMemcpyAsync(w.fkb.p, top.kth.data(), (size_t)nv.W * 8, cudaMemcpyHostToDevice, s));
+    }
     int64_t n_front = (int64_t)h[C_NEXT];
     uint64_t deg_sum = h[C_DEGSUM];
     int status = 0;
@@ -521,33 +614,101 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
         CK(cudaMemsetAsync(w.slots.p, 0xFF, nslots * 8, s));
         CK(cudaMemsetAsync(ctr + C_NEXT, 0, 2 * 8, s));
         a.par = arena(cur);
-        a.n_par = n_front;
-        a.cpw = (int)std::min<int64_t>(32, std::max<int64_t>(1, (n_front + total_warps - 1) / total_warps));
         a.child = arena(cur ^ 1);
         a.slot_mask = nslots - 1;
         a.level = level;
-        CK(cudaEventRecord(w.ev[2], s));
-        CK(launch_expand(nv, a, grid, s));
-        CK(cudaEventRecord(w.ev[3], s));
-        if ((rc = read_ctr())) return rc;
-        CK(cudaEventElapsedTime(&ms, w.ev[2], w.ev[3]));
-        out.expand_ms += ms;
-        out.expand_launches += 1;
-        out.kernel_launches += 1;
-        {
-            const double state_bytes = 8.0 * nv.W + 4.0 * nv.M + 4.0;
-            const double n_new = (double)std::min<unsigned long long>(h[C_NEXT], (unsigned long long)w.F_cap);
-            const double n_child = (double)(h[C_EXP] - exp_before);
-            out.expand_bytes += state_bytes * ((double)n_front + n_new) + 16.0 * n_child;
-            exp_before = h[C_EXP];
+        // first-K: the level's parents in proposal order, in chunks with the
+        // bound refreshed between them
+        if (trace && n_front > 0) {
+            // training rows: a strided sample of this frontier (level - 1)
+            const int64_t stride = std::max<int64_t>(1, (n_front + trace->rows_per_level - 1) / trace->rows_per_level);
+            const int64_t cnt = (n_front + stride - 1) / stride;
+            efm_model *m = trace->m;
+            if (!model_reserve_rows(m, m->n_rows + cnt)) return EFM_ENOMEM;
+            CK(launch_features(nv, arena(cur), 0, stride, cnt, level - 1, lim.max_len, lim.max_secondary, m->X.p,
+                               m->n_rows, s));
+            CK(launch_labels((const uint64_t *)w.U[cur].p, nv.W, 0, stride, cnt, trace->ans, trace->n_ans,
+                             (float *)m->y.p, m->n_rows, s));
+            m->n_rows += cnt;
         }
-        acc.cand_begin = cand_done;
-        acc.cand_end = (int64_t)h[C_CAND_N];
-        CK(launch_accept(nv, acc, s));
-        out.kernel_launches += acc.cand_end > acc.cand_begin ? 1 : 0;
-        if ((rc = read_ctr())) return rc;
-        cand_done = (int64_t)h[C_CAND_N];
-        res_n = (int64_t)std::min<unsigned long long>(h[C_RES_N], (unsigned long long)w.res_cap);
+        int64_t chunk = n_front;
+        if (fk) {
+            chunk = std::max<int64_t>(kFirstKChunkMin, (n_front + kFirstKChunks - 1) / kFirstKChunks);
+            if (model && lim.proposal == EFM_LEARNED && n_front > chunk) {
+                // the model's order: features of every parent, scores, and a
+                // counting sort by score (highest first)
+                const int64_t rows = (n_front + kMlpTileRows - 1) / kMlpTileRows * kMlpTileRows;
+                if (rows > w.lx_rows) {
+                    dev_free(w.lx, s);
+                    dev_free(w.lscore, s);
+                    const int64_t cap = std::max<int64_t>(rows, 2 * w.lx_rows);
+                    if (!dev_alloc(w.lx, (size_t)cap * kMlpFeatures * 2, s) || !dev_alloc(w.lscore, (size_t)cap * 4, s))
+                        return EFM_ENOMEM;
+                    w.lx_rows = cap;
+                }
+                if (!w.lhist.p) {
+                    if (!dev_alloc(w.lhist, 4096 * 4, s) || !dev_alloc(w.lerr, 4, s)) return EFM_ENOMEM;
+                    CK(cudaMemsetAsync(w.lerr.p, 0, 4, s));
+                }
+                CK(launch_features(nv, arena(cur), 0, 1, n_front, level - 1, lim.max_len, lim.max_secondary, w.lx.p, 0,
+                                   s));
+                CK(launch_mlp_score(w.lx.p, n_front, model->wb.p, (const float *)model->params.p,
+                                    (float *)w.lscore.p, (unsigned *)w.lerr.p, s));
+                CK(launch_score_order((const float *)w.lscore.p, n_front, (unsigned *)w.lhist.p,
+                                      (uint32_t *)w.perm.p, s));
+                out.kernel_launches += 6;
+            } else {
+                CK(launch_iota((uint32_t *)w.perm.p, n_front, s));
+                out.kernel_launches += 1;
+            }
+        }
+        uint64_t next_before = 0;
+        for (int64_t c0 = 0; c0 < n_front; c0 += chunk) {
+            const int64_t cn = std::min<int64_t>(chunk, n_front - c0);
+            a.n_par = cn;
+            a.perm = fk ? (const uint32_t *)w.perm.p + c0 : nullptr;
+            a.cpw = (int)std::min<int64_t>(32, std::max<int64_t>(1, (cn + total_warps - 1) / total_warps));
+            a.fk_pc = fk ? top.pc : 0;
+            a.fk_sup = (const uint64_t *)w.fkb.p;
+            a.max_len = (fk && top.pc > 0) ? std::min(lim.max_len, top.pc) : lim.max_len;
+            CK(cudaEventRecord(w.ev[2], s));
+            CK(launch_expand(nv, a, grid, s));
+            CK(cudaEventRecord(w.ev[3], s));
+            if ((rc = read_ctr())) return rc;
+            CK(cudaEventElapsedTime(&ms, w.ev[2], w.ev[3]));
+            out.expand_ms += ms;
+            out.expand_launches += 1;
+            out.kernel_launches += 1;
+            {
+                const double state_bytes = 8.0 * nv.W + 4.0 * nv.M + 4.0;
+                const uint64_t next_now = std::min<unsigned long long>(h[C_NEXT], (unsigned long long)w.F_cap);
+                const double n_new = (double)(next_now - next_before);
+                const double n_child = (double)(h[C_EXP] - exp_before);
+                out.expand_bytes += state_bytes * ((double)cn + n_new) + 16.0 * n_child;
+                exp_before = h[C_EXP];
+                next_before = next_now;
+            }
+            acc.cand_begin = cand_done;
+            acc.cand_end = (int64_t)h[C_CAND_N];
+            CK(launch_accept(nv, acc, s));
+            out.kernel_launches += acc.cand_end > acc.cand_begin ? 1 : 0;
+            if ((rc = read_ctr())) return rc;
+            cand_done = (int64_t)h[C_CAND_N];
+            const int64_t res_now = (int64_t)std::min<unsigned long long>(h[C_RES_N], (unsigned long long)w.res_cap);
+            if (fk && res_now > res_n) {
+                // fetch the new results and tighten the bound
+                std::vector<uint64_t> fresh((size_t)(res_now - res_n) * nv.W);
+                CK(cudaMemcpyAsync(fresh.data(), (const uint64_t *)w.res.p + (size_t)res_n * nv.W,
+                                   fresh.size() * 8, cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                const int pc_before = top.pc;
+                const std::vector<uint64_t> kth_before = top.kth;
+                top.add(fresh.data(), res_now - res_n);
+                if (top.pc > 0 && (top.pc != pc_before || top.kth != kth_before))
+                    CK(cudaMemcpyAsync(w.fkb.p, top.kth.data(), (size_t)nv.W * 8, cudaMemcpyHostToDevice, s));
+            }
+            res_n = res_now;
+        }
         n_front = (int64_t)h[C_NEXT];
         deg_sum = h[C_DEGSUM];
         c.levels = level + 1;
@@ -565,8 +726,15 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
         }
     }
     if ((int64_t)h[C_RES_N] > w.res_cap) return EFM_ECAPACITY;
+    if (w.lerr.p) {
+        unsigned e = 0;
+        CK(cudaMemcpyAsync(&e, w.lerr.p, 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (e) return EFM_ETIMEOUT;
+    }
     // output: sorted by (|U|, column list), capped
-    const int64_t n_keep = lim.max_results > 0 ? std::min<int64_t>(res_n, lim.max_results) : res_n;
+    int64_t n_keep = lim.max_results > 0 ? std::min<int64_t>(res_n, lim.max_results) : res_n;
+    if (fk) n_keep = std::min<int64_t>(res_n, lim.first_k);
     const uint64_t n2 = next_pow2((uint64_t)std::max<int64_t>(res_n, 1));
     if (n2 > w.sort_cap) {
         dev_free(w.sortidx, s);
@@ -602,15 +770,19 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
 }  // namespace
 
 extern "C" int efm_find_pathways(efm_net *net, const int32_t *targets, int32_t n_targets, const efm_limits *limits,
-                                 const void *model, efm_job **out)
+                                 const efm_model *model, efm_job **out)
 {
     if (!out) return EFM_EINVAL;
     *out = nullptr;
-    if (!net || !targets || n_targets <= 0 || !limits || model) return EFM_EINVAL;
+    if (!net || !targets || n_targets <= 0 || !limits) return EFM_EINVAL;
     const efm_limits lim = *limits;
-    if (lim.max_len < 1 || lim.max_len > EFM_MAX_LEN || lim.max_secondary < 0 || lim.first_k != 0 ||
-        lim.proposal != 0)
+    if (lim.max_len < 1 || lim.max_len > EFM_MAX_LEN || lim.max_secondary < 0 || lim.first_k < 0 ||
+        (lim.proposal != EFM_PLAIN && lim.proposal != EFM_LEARNED))
         return EFM_EINVAL;
+    if (lim.first_k > 0 && lim.max_results != 0) return EFM_EINVAL;
+    // a model orders a first-K search and nothing else
+    if ((lim.proposal == EFM_LEARNED) != (model != nullptr) || (model && lim.first_k <= 0)) return EFM_EINVAL;
+    const efm_model *mdl = model;
     for (int i = 0; i < n_targets; ++i)
         if (targets[i] < -1 || targets[i] >= net->n_met) return EFM_EINVAL;
     auto *job = new (std::nothrow) efm_job();
@@ -622,7 +794,7 @@ extern "C" int efm_find_pathways(efm_net *net, const int32_t *targets, int32_t n
     int rc = alloc_work(w, net, lim, total_warps, net->stream);
     int flags = 0;
     for (int i = 0; rc == EFM_OK && i < n_targets; ++i) {
-        rc = run_target(net, w, lim, targets[i], job->out[i]);
+        rc = run_target(net, w, lim, targets[i], job->out[i], mdl);
         flags |= job->out[i].status;
     }
     free_work(w, net->stream);
@@ -690,7 +862,7 @@ std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune;
 }  // namespace
 
 extern "C" int efm_find_pathways_batch(efm_net *const *nets, const int32_t *targets, int32_t n_jobs,
-                                       const efm_limits *limits, const void *model, efm_job **out)
+                                       const efm_limits *limits, const efm_model *model, efm_job **out)
 {
     if (!out) return EFM_EINVAL;
     *out = nullptr;
@@ -955,4 +1127,340 @@ extern "C" void efm_free_job(efm_job *job)
     dev_free(job->shared_out, s);
     cudaStreamSynchronize(s);
     delete job;
+}
+
+// ---------------------------------------------------------------------------
+// Proposal model (the learned order of first-K searches).
+// ---------------------------------------------------------------------------
+
+namespace {
+
+uint64_t splitmix64(uint64_t &x)
+{
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+float uniform_pm1(uint64_t &x) { return (float)((double)(splitmix64(x) >> 11) * (2.0 / 9007199254740992.0) - 1.0); }
+
+int model_check_err(efm_model *m)
+{
+    unsigned e = 0;
+    if (cudaMemcpyAsync(&e, m->err.p, 4, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+        cudaStreamSynchronize(m->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return EFM_ECUDA;
+    }
+    return e ? EFM_ETIMEOUT : EFM_OK;
+}
+
+// valid rows in training tile t
+int64_t tile_rows(const efm_model *m, int64_t t) { return std::min<int64_t>(kMlpTileRows, m->n_rows - t * kMlpTileRows); }
+
+bool model_reserve_rows(efm_model *m, int64_t rows)
+{
+    const int64_t need = (rows + kMlpTileRows - 1) / kMlpTileRows * kMlpTileRows;
+    if (need <= m->cap_rows) return true;
+    const int64_t cap = std::max<int64_t>(need, 2 * m->cap_rows);
+    DevBuf X, y, tiles;
+    if (!dev_alloc(X, (size_t)cap * kMlpFeatures * 2, m->stream) || !dev_alloc(y, (size_t)cap * 4, m->stream) ||
+        !dev_alloc(tiles, (size_t)(cap / kMlpTileRows) * 4, m->stream)) {
+        dev_free(X, m->stream);
+        dev_free(y, m->stream);
+        dev_free(tiles, m->stream);
+        return false;
+    }
+    // rows past n_rows stay zero (padding of the last tile)
+    cudaMemsetAsync(X.p, 0, (size_t)cap * kMlpFeatures * 2, m->stream);
+    if (m->n_rows > 0) {
+        const int64_t used = (m->n_rows + kMlpTileRows - 1) / kMlpTileRows * kMlpTileRows;
+        cudaMemcpyAsync(X.p, m->X.p, (size_t)used * kMlpFeatures * 2, cudaMemcpyDeviceToDevice, m->stream);
+        cudaMemcpyAsync(y.p, m->y.p, (size_t)m->n_rows * 4, cudaMemcpyDeviceToDevice, m->stream);
+    }
+    dev_free(m->X, m->stream);
+    dev_free(m->y, m->stream);
+    dev_free(m->tiles, m->stream);
+    // the rows may be written from another stream (a network's, when tracing)
+    cudaStreamSynchronize(m->stream);
+    m->X = X;
+    m->y = y;
+    m->tiles = tiles;
+    m->cap_rows = cap;
+    return true;
+}
+
+}  // namespace
+
+extern "C" int efm_model_create(uint64_t seed, uintptr_t cuda_stream, efm_model **out)
+{
+    if (!out) return EFM_EINVAL;
+    *out = nullptr;
+    auto *m = new (std::nothrow) efm_model();
+    if (!m) return EFM_ENOMEM;
+    m->stream = (cudaStream_t)cuda_stream;
+    cudaStream_t s = m->stream;
+    const size_t pb = (size_t)kMlpParams * 4;
+    if (!dev_alloc(m->params, pb, s) || !dev_alloc(m->grad, pb, s) || !dev_alloc(m->mom, 2 * pb, s) ||
+        !dev_alloc(m->wb, (size_t)kMlpHidden * kMlpFeatures * 2, s) || !dev_alloc(m->loss, 4, s) ||
+        !dev_alloc(m->err, 4, s)) {
+        efm_model_free(m);
+        return EFM_ENOMEM;
+    }
+    // uniform initialisation scaled by fan-in (He), from a seeded splitmix64 stream
+    std::vector<float> p((size_t)kMlpParams, 0.f);
+    uint64_t st = seed;
+    const float a1 = std::sqrt(6.0f / kMlpFeatures), a2 = std::sqrt(3.0f / kMlpHidden);
+    for (int i = 0; i < kMlpW2; ++i) p[kMlpW1 + i] = a1 * uniform_pm1(st);
+    for (int j = 0; j < kMlpHidden; ++j) p[kMlpW2 + j] = a2 * uniform_pm1(st);
+    p[kMlpB2] = 0.f;
+    if (cudaMemcpyAsync(m->params.p, p.data(), pb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(m->grad.p, 0, pb, s) != cudaSuccess || cudaMemsetAsync(m->mom.p, 0, 2 * pb, s) != cudaSuccess ||
+        cudaMemsetAsync(m->err.p, 0, 4, s) != cudaSuccess ||
+        launch_pack_w((const float *)m->params.p, m->wb.p, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        efm_model_free(m);
+        return EFM_ECUDA;
+    }
+    *out = m;
+    return EFM_OK;
+}
+
+extern "C" int efm_model_params(efm_model *m, float *params, int32_t write)
+{
+    if (!m || !params) return EFM_EINVAL;
+    cudaStream_t s = m->stream;
+    const size_t pb = (size_t)kMlpParams * 4;
+    if (write) {
+        if (cudaMemcpyAsync(m->params.p, params, pb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemsetAsync(m->mom.p, 0, 2 * pb, s) != cudaSuccess ||
+            launch_pack_w((const float *)m->params.p, m->wb.p, s) != cudaSuccess) {
+            cudaGetLastError();
+            return EFM_ECUDA;
+        }
+        m->step = 0;
+    } else if (cudaMemcpyAsync(params, m->params.p, pb, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+        cudaGetLastError();
+        return EFM_ECUDA;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return EFM_ECUDA;
+    }
+    return EFM_OK;
+}
+
+extern "C" int efm_model_add_rows(efm_model *m, const float *x, const float *y, int64_t n)
+{
+    if (!m || n < 0 || (n > 0 && (!x || !y))) return EFM_EINVAL;
+    if (n == 0) return EFM_OK;
+    for (int64_t i = 0; i < n; ++i)
+        if (!(y[i] == 0.f || y[i] == 1.f)) return EFM_EINVAL;
+    cudaStream_t s = m->stream;
+    if (!model_reserve_rows(m, m->n_rows + n)) return EFM_ENOMEM;
+    DevBuf tmp;
+    if (!dev_alloc(tmp, (size_t)n * kMlpFeatures * 4, s)) return EFM_ENOMEM;
+    int rc = EFM_OK;
+    if (cudaMemcpyAsync(tmp.p, x, (size_t)n * kMlpFeatures * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        launch_pack_rows((const float *)tmp.p, n, m->X.p, m->n_rows, s) != cudaSuccess ||
+        cudaMemcpyAsync((float *)m->y.p + m->n_rows, y, (size_t)n * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        rc = EFM_ECUDA;
+    }
+    dev_free(tmp, s);
+    if (rc == EFM_OK) m->n_rows += n;
+    return rc;
+}
+
+extern "C" int efm_model_rows(efm_model *m, int64_t *n_rows, int64_t *n_positive)
+{
+    if (!m) return EFM_EINVAL;
+    if (n_rows) *n_rows = m->n_rows;
+    if (n_positive) {
+        std::vector<float> y((size_t)m->n_rows);
+        if (m->n_rows > 0 &&
+            (cudaMemcpyAsync(y.data(), m->y.p, y.size() * 4, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+             cudaStreamSynchronize(m->stream) != cudaSuccess)) {
+            cudaGetLastError();
+            return EFM_ECUDA;
+        }
+        int64_t c = 0;
+        for (float v : y) c += v > 0.5f;
+        *n_positive = c;
+    }
+    return EFM_OK;
+}
+
+extern "C" int efm_model_clear_rows(efm_model *m)
+{
+    if (!m) return EFM_EINVAL;
+    m->n_rows = 0;
+    if (m->X.p && cudaMemsetAsync(m->X.p, 0, m->X.bytes, m->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return EFM_ECUDA;
+    }
+    return EFM_OK;
+}
+
+extern "C" int efm_model_forward(efm_model *m, const float *x, int64_t n, float *scores)
+{
+    if (!m || n < 0 || (n > 0 && (!x || !scores))) return EFM_EINVAL;
+    if (n == 0) return EFM_OK;
+    cudaStream_t s = m->stream;
+    const int64_t rows = (n + kMlpTileRows - 1) / kMlpTileRows * kMlpTileRows;
+    DevBuf tx, tX, ts;
+    int rc = EFM_OK;
+    if (!dev_alloc(tx, (size_t)n * kMlpFeatures * 4, s) || !dev_alloc(tX, (size_t)rows * kMlpFeatures * 2, s) ||
+        !dev_alloc(ts, (size_t)n * 4, s)) {
+        rc = EFM_ENOMEM;
+    } else if (cudaMemcpyAsync(tx.p, x, (size_t)n * kMlpFeatures * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+               cudaMemsetAsync(tX.p, 0, (size_t)rows * kMlpFeatures * 2, s) != cudaSuccess ||
+               launch_pack_rows((const float *)tx.p, n, tX.p, 0, s) != cudaSuccess ||
+               launch_mlp_score(tX.p, n, m->wb.p, (const float *)m->params.p, (float *)ts.p, (unsigned *)m->err.p,
+                                s) != cudaSuccess ||
+               cudaMemcpyAsync(scores, ts.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+               cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        rc = EFM_ECUDA;
+    }
+    dev_free(tx, s);
+    dev_free(tX, s);
+    dev_free(ts, s);
+    if (rc == EFM_OK) rc = model_check_err(m);
+    return rc;
+}
+
+namespace {
+
+// one training pass over tiles[0..n_tiles) (device list); adds the gradient
+// into m->grad and the loss into m->loss
+int model_pass(efm_model *m, const int32_t *tiles_dev, int n_tiles, int64_t rows, float pos_weight)
+{
+    if (launch_mlp_train(m->X.p, (const float *)m->y.p, m->n_rows, tiles_dev, n_tiles, m->wb.p,
+                         (const float *)m->params.p, pos_weight, 1.0f / (float)std::max<int64_t>(rows, 1),
+                         (float *)m->grad.p, (float *)m->loss.p, (unsigned *)m->err.p, m->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return EFM_ECUDA;
+    }
+    return EFM_OK;
+}
+
+}  // namespace
+
+extern "C" int efm_model_gradient(efm_model *m, float pos_weight, float *grad, float *loss)
+{
+    if (!m || !grad || m->n_rows <= 0) return EFM_EINVAL;
+    cudaStream_t s = m->stream;
+    const int n_tiles = (int)((m->n_rows + kMlpTileRows - 1) / kMlpTileRows);
+    std::vector<int32_t> t((size_t)n_tiles);
+    for (int i = 0; i < n_tiles; ++i) t[i] = i;
+    const size_t pb = (size_t)kMlpParams * 4;
+    if (cudaMemcpyAsync(m->tiles.p, t.data(), t.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(m->grad.p, 0, pb, s) != cudaSuccess || cudaMemsetAsync(m->loss.p, 0, 4, s) != cudaSuccess) {
+        cudaGetLastError();
+        return EFM_ECUDA;
+    }
+    int rc = model_pass(m, (const int32_t *)m->tiles.p, n_tiles, m->n_rows, pos_weight);
+    if (rc) return rc;
+    float l = 0.f;
+    if (cudaMemcpyAsync(grad, m->grad.p, pb, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&l, m->loss.p, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemsetAsync(m->grad.p, 0, pb, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return EFM_ECUDA;
+    }
+    if (loss) *loss = l;
+    return model_check_err(m);
+}
+
+extern "C" int efm_model_train(efm_model *m, int32_t epochs, int32_t batch_tiles, float lr, float pos_weight,
+                               uint64_t seed, float *last_loss)
+{
+    if (!m || epochs < 0 || batch_tiles < 1 || !(lr > 0.f) || !(pos_weight > 0.f) || m->n_rows <= 0)
+        return EFM_EINVAL;
+    cudaStream_t s = m->stream;
+    const int n_tiles = (int)((m->n_rows + kMlpTileRows - 1) / kMlpTileRows);
+    std::vector<int32_t> order((size_t)n_tiles);
+    uint64_t st = seed;
+    float epoch_loss = 0.f;
+    for (int e = 0; e < epochs; ++e) {
+        for (int i = 0; i < n_tiles; ++i) order[i] = i;
+        for (int i = n_tiles - 1; i > 0; --i) std::swap(order[i], order[splitmix64(st) % (uint64_t)(i + 1)]);
+        if (cudaMemcpyAsync(m->tiles.p, order.data(), order.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemsetAsync(m->loss.p, 0, 4, s) != cudaSuccess) {
+            cudaGetLastError();
+            return EFM_ECUDA;
+        }
+        int batches = 0;
+        for (int b0 = 0; b0 < n_tiles; b0 += batch_tiles) {
+            const int nb = std::min(batch_tiles, n_tiles - b0);
+            int64_t rows = 0;
+            for (int i = 0; i < nb; ++i) rows += tile_rows(m, order[b0 + i]);
+            int rc = model_pass(m, (const int32_t *)m->tiles.p + b0, nb, rows, pos_weight);
+            if (rc) return rc;
+            if (launch_adam((float *)m->params.p, (float *)m->grad.p, (float *)m->mom.p, lr, ++m->step, m->wb.p, s) !=
+                cudaSuccess) {
+                cudaGetLastError();
+                return EFM_ECUDA;
+            }
+            ++batches;
+        }
+        float l = 0.f;
+        if (cudaMemcpyAsync(&l, m->loss.p, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            return EFM_ECUDA;
+        }
+        epoch_loss = l / (float)std::max(batches, 1);
+    }
+    if (last_loss) *last_loss = epoch_loss;
+    return model_check_err(m);
+}
+
+extern "C" int efm_model_trace(efm_model *m, efm_net *net, const int32_t *targets, int32_t n_targets,
+                               const efm_limits *limits, int64_t rows_per_level)
+{
+    if (!m || !net || !targets || n_targets <= 0 || !limits || rows_per_level < 1) return EFM_EINVAL;
+    efm_limits lim = *limits;
+    lim.proposal = EFM_PLAIN;
+    if (lim.max_len < 1 || lim.max_len > EFM_MAX_LEN || lim.max_secondary < 0 || lim.first_k <= 0 ||
+        lim.max_results != 0)
+        return EFM_EINVAL;
+    for (int i = 0; i < n_targets; ++i)
+        if (targets[i] < -1 || targets[i] >= net->n_met) return EFM_EINVAL;
+    Work w;
+    const int total_warps = expand_grid(net->nv, net->sm_count) * kExpandWarps;
+    int rc = alloc_work(w, net, lim, total_warps, net->stream);
+    for (int i = 0; rc == EFM_OK && i < n_targets; ++i) {
+        TargetOut ans;
+        rc = run_target(net, w, lim, targets[i], ans);  // the answer, then the traced rerun
+        if (rc == EFM_OK && ans.n > 0 && !(ans.status & EFM_TRUNCATED)) {
+            Trace tr;
+            tr.m = m;
+            tr.ans = (const uint64_t *)ans.sup.p;
+            tr.n_ans = ans.n;
+            tr.rows_per_level = rows_per_level;
+            TargetOut again;
+            rc = run_target(net, w, lim, targets[i], again, nullptr, &tr);
+            dev_free(again.sup, net->stream);
+        }
+        dev_free(ans.sup, net->stream);
+    }
+    free_work(w, net->stream);
+    if (cudaStreamSynchronize(net->stream) != cudaSuccess && rc == EFM_OK) rc = EFM_ECUDA;
+    cudaGetLastError();
+    return rc;
+}
+
+extern "C" void efm_model_free(efm_model *m)
+{
+    if (!m) return;
+    cudaStream_t s = m->stream;
+    DevBuf *bufs[] = {&m->params, &m->grad, &m->mom, &m->wb, &m->loss, &m->err, &m->X, &m->y, &m->tiles};
+    for (DevBuf *b : bufs) dev_free(*b, s);
+    cudaStreamSynchronize(s);
+    delete m;
 }

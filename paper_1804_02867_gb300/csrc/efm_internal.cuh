@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "../../include/efmgraph.h"
 
 namespace efm {
@@ -15,6 +17,8 @@ constexpr uint32_t kPending = 0xFFFFFFFFu;
 constexpr uint32_t kOverflowIdx = 0xFFFFFFFEu;
 constexpr int kNumPrimes = 24;
 constexpr int kStageLimitBytes = 72 * 1024;  // static network staged in smem up to this size
+constexpr int64_t kFirstKChunkMin = 8192;     // first-K search: fewest parents per expansion launch
+constexpr int64_t kFirstKChunks = 32;         // first-K search: launches per level, at most
 
 // device error bits (ctr[C_ERR])
 enum : unsigned { ERR_TIMEOUT = 1u, ERR_CAND_CAP = 2u, ERR_RES_CAP = 4u, ERR_TABLE_FULL = 8u,
@@ -85,6 +89,10 @@ struct LevelArgs {
     int level, max_len, max_sec;
     int cpw;                    // parents per warp chunk (1..32)
     unsigned long long *ctr;
+    // first-K search (zero / null otherwise)
+    const uint32_t *perm;       // parent order: position -> arena index (null = arena order)
+    int fk_pc;                  // bound: |U| of the K-th smallest result found so far (0 = no bound)
+    const uint64_t *fk_sup;     // bound: its support (W words)
 };
 
 constexpr int kRcolStride = 65;  // column count + up to 64 columns per result
@@ -126,6 +134,42 @@ struct BatchArgs {
     int64_t max_frontier, max_results;
 };
 
+// Learned proposal: MLP 128 -> 256 (ReLU) -> 1.  FP32 parameters in one
+// buffer: W1 [256][128] (hidden unit, feature; the bias of the hidden layer
+// is the weight of the constant feature), w2 [256], b2.
+constexpr int kMlpFeatures = 128;
+constexpr int kMlpHidden = 256;
+constexpr int kMlpTileRows = 128;
+constexpr int kMlpW1 = 0;
+constexpr int kMlpW2 = kMlpHidden * kMlpFeatures;
+constexpr int kMlpB2 = kMlpW2 + kMlpHidden;
+constexpr int kMlpParams = kMlpB2 + 1;
+
+// Byte offset of element (row, k) in a 128-column BF16 tile laid out as the
+// K-major operand of tcgen05 without swizzling: 8 x 8 core matrices (8 rows
+// of 16 bytes), 16 of them along K per group of 8 rows.
+__host__ __device__ inline uint32_t mlp_blk_off(int row, int k)
+{
+    return (uint32_t)((((row >> 3) * 16 + (k >> 3)) * 128) + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// kernels (efm_mlp.cu)
+cudaError_t launch_features(const NetView &nv, const Arena &par, int64_t first, int64_t stride, int64_t n, int level,
+                            int max_len, int max_sec, void *X, int64_t row0, cudaStream_t s);
+cudaError_t launch_labels(const uint64_t *U, int W, int64_t first, int64_t stride, int64_t n, const uint64_t *ans,
+                          int64_t n_ans, float *y, int64_t row0, cudaStream_t s);
+cudaError_t launch_mlp_score(const void *X, int64_t n_rows, const void *wb, const float *params, float *score,
+                             unsigned *err, cudaStream_t s);
+cudaError_t launch_mlp_train(const void *X, const float *y, int64_t n_rows, const int32_t *tiles, int n_tiles,
+                             const void *wb, const float *params, float pos_weight, float inv_n, float *grad,
+                             float *loss, unsigned *err, cudaStream_t s);
+cudaError_t launch_adam(float *params, float *grad, float *mom, float lr, int step, void *wb, cudaStream_t s);
+cudaError_t launch_pack_w(const float *params, void *wb, cudaStream_t s);
+cudaError_t launch_score_order(const float *score, int64_t n, unsigned *hist, uint32_t *perm, cudaStream_t s);
+cudaError_t launch_pack_rows(const float *x, int64_t n, void *X, int64_t row0, cudaStream_t s);
+size_t mlp_score_smem();
+size_t mlp_train_smem();
+
 // kernels (efm_kernels.cu)
 cudaError_t launch_seed(const NetView &nv, const LevelArgs &a, int target, cudaStream_t s);
 cudaError_t launch_expand(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s);
@@ -135,6 +179,7 @@ cudaError_t launch_buckets(const NetView &nv, const uint64_t *res, int64_t n_res
 cudaError_t launch_sort_results(const uint64_t *res, int64_t n, int W, uint32_t *idx, int64_t n_pow2,
                                 uint64_t *out, int64_t n_keep, cudaStream_t s);
 int expand_grid(const NetView &nv, int sm_count);
+cudaError_t launch_iota(uint32_t *perm, int64_t n, cudaStream_t s);
 cudaError_t launch_batch(const BatchArgs &ba, int grid, cudaStream_t s);
 int batch_blocks_per_sm();
 size_t batch_smem_bytes();

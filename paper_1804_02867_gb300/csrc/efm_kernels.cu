@@ -473,6 +473,20 @@ __device__ __forceinline__ void hash_entry(uint32_t m, uint32_t v, uint32_t &lo,
 
 // children per warp batch for a row of 16-byte chunks nch (shared memory
 // per warp: NB padded rows plus 32 bytes of bookkeeping per child)
+// First-K bound (output order: |U|, then the ascending column list): true
+// when the child support (U with column k) comes after R, both of size |R|.
+// Of two sets of equal size, the one holding the lowest column of their
+// symmetric difference comes first.
+__device__ __forceinline__ bool child_after(const uint64_t *pu, int k, const uint64_t *R, int W)
+{
+    for (int w = 0; w < W; ++w) {
+        const uint64_t c = child_word(pu, w, k);
+        const uint64_t d = c ^ __ldg(R + w);
+        if (d) return (c & (d & (~d + 1))) == 0;
+    }
+    return false;
+}
+
 template <int G, int CPL>
 struct BatchShape {
     static constexpr int NCH = G * CPL;          // 16-byte chunks per row
@@ -760,21 +774,25 @@ __device__ void expand_range(const NetView &nv, const LevelArgs &a, const uint32
     for (int64_t p0 = worker * cpw; p0 < a.n_par; p0 += wstride) {
         const int64_t pl = p0 + lane;
         const bool pin = lane < cpw && pl < a.n_par;
+        const int64_t pid = pin ? (a.perm ? (int64_t)a.perm[pl] : pl) : 0;  // this lane's parent
         // pull this chunk's and the next chunk's parents toward L2
         if (pin) {
-            const char *rp = reinterpret_cast<const char *>(a.par.B + (size_t)pl * Mpad);
+            const char *rp = reinterpret_cast<const char *>(a.par.B + (size_t)pid * Mpad);
             for (int off = 0; off < Mpad * 4; off += 128) prefetch_l2(rp + off);
-            prefetch_l2(a.par.U + (size_t)pl * W);
+            prefetch_l2(a.par.U + (size_t)pid * W);
         }
         const int64_t pn = pl + wstride;
         if (lane < cpw && pn < a.n_par) {
-            const char *rp = reinterpret_cast<const char *>(a.par.B + (size_t)pn * Mpad);
+            const int64_t nid = a.perm ? (int64_t)a.perm[pn] : pn;
+            const char *rp = reinterpret_cast<const char *>(a.par.B + (size_t)nid * Mpad);
             for (int off = 0; off < Mpad * 4; off += 128) prefetch_l2(rp + off);
-            prefetch_l2(a.par.U + (size_t)pn * W);
-            prefetch_l2(a.par.meta + pn);
+            prefetch_l2(a.par.U + (size_t)nid * W);
+            prefetch_l2(a.par.meta + nid);
         }
-        const uint32_t mj = pin ? a.par.meta[pl] : 0u;
-        const int dj = pin ? (int)((mj >> 10) & 0x1FFFu) : 0;
+        const uint32_t mj = pin ? a.par.meta[pid] : 0u;
+        int dj = pin ? (int)((mj >> 10) & 0x1FFFu) : 0;
+        // first-K: a parent larger than the bound has no descendant among the K smallest
+        if (a.fk_pc > 0 && (int)((mj >> 23) & 0x7Fu) > a.fk_pc) dj = 0;
         int incl = dj;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -804,7 +822,7 @@ __device__ void expand_range(const NetView &nv, const LevelArgs &a, const uint32
             int k = 0, pc = 0;
             bool in_u = false;
             int32_t A = 0, C = 0;
-            const int64_t p = p0 + j;
+            const int64_t p = __shfl_sync(FULL, pid, j);
             const int32_t *prow = a.par.B + (size_t)p * Mpad;
             const uint64_t *pu = a.par.U + (size_t)p * W;
             if (ok) {
@@ -829,6 +847,13 @@ __device__ void expand_range(const NetView &nv, const LevelArgs &a, const uint32
                     in_u = bit_of(pu, k);
                     const int sec = a.level - pc;
                     ok = !(tw >= 0 && bit_of(pu, tw)) && (in_u ? sec + 1 <= a.max_sec : pc + 1 <= a.max_len);
+                    if (ok && a.fk_pc > 0) {
+                        // first-K branch and bound: the child's descendants keep
+                        // its support or grow it, so a child past the K-th
+                        // result found so far cannot yield one of the K smallest
+                        const int pc2 = pc + (in_u ? 0 : 1);
+                        ok = pc2 < a.fk_pc || (pc2 == a.fk_pc && !child_after(pu, k, a.fk_sup, W));
+                    }
                     const uint32_t g0 = (abi == 1u || sik == 1u) ? 1u : gcd32(abi, sik);
                     A = (int32_t)(sik / g0);
                     C = (int32_t)(abi / g0);
@@ -1651,6 +1676,19 @@ cudaError_t launch_buckets(const NetView &nv, const uint64_t *res, int64_t n_res
     if (items > 0) bucket_count_kernel<<<(int)((items + tb - 1) / tb), tb, 0, s>>>(res, n_res, nv.W, bcnt);
     bucket_scan_kernel<<<1, 1024, 0, s>>>(bcnt, nv.N, bptr);
     if (items > 0) bucket_fill_kernel<<<(int)((items + tb - 1) / tb), tb, 0, s>>>(res, n_res, nv.W, bptr, bfill, bres);
+    return cudaGetLastError();
+}
+
+__global__ void iota_kernel(uint32_t *perm, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) perm[i] = (uint32_t)i;
+}
+
+cudaError_t launch_iota(uint32_t *perm, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    iota_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(perm, n);
     return cudaGetLastError();
 }
 

@@ -21,8 +21,12 @@ COUNTER_FIELDS = ("levels", "seeds", "expansions", "overflow", "balanced", "cand
                   "frontier", "frontier_max", "status")
 EXPORTS = ("efm_load_network", "efm_network_shape", "efm_column_map", "efm_find_pathways", "efm_fetch_results",
            "efm_job_timing", "efm_free_job", "efm_free_net", "efm_status_str", "efm_set_allocator",
-           "efm_sort_supports_noalloc", "efm_find_pathways_batch", "efm_batch_tuning")
+           "efm_sort_supports_noalloc", "efm_find_pathways_batch", "efm_batch_tuning", "efm_model_create",
+           "efm_model_params", "efm_model_add_rows", "efm_model_rows", "efm_model_clear_rows", "efm_model_forward",
+           "efm_model_gradient", "efm_model_train", "efm_model_trace", "efm_model_free")
 EFM_NOALLOC_MAX_ROWS = 1 << 20
+EFM_MLP_FEATURES, EFM_MLP_HIDDEN = 128, 256
+EFM_MLP_PARAMS = 256 * 128 + 256 + 1
 
 
 class efm_limits(ctypes.Structure):
@@ -91,6 +95,24 @@ def load_library(path: str | None = None):
     lib.efm_find_pathways_batch.restype = ctypes.c_int
     lib.efm_batch_tuning.argtypes = [_P(ctypes.c_int32), _P(ctypes.c_int32)]
     lib.efm_batch_tuning.restype = ctypes.c_int
+    F = _P(ctypes.c_float)
+    lib.efm_model_create.argtypes = [ctypes.c_uint64, ctypes.c_size_t, _P(ctypes.c_void_p)]
+    lib.efm_model_params.argtypes = [ctypes.c_void_p, F, ctypes.c_int32]
+    lib.efm_model_add_rows.argtypes = [ctypes.c_void_p, F, F, ctypes.c_int64]
+    lib.efm_model_rows.argtypes = [ctypes.c_void_p, _P(ctypes.c_int64), _P(ctypes.c_int64)]
+    lib.efm_model_clear_rows.argtypes = [ctypes.c_void_p]
+    lib.efm_model_forward.argtypes = [ctypes.c_void_p, F, ctypes.c_int64, F]
+    lib.efm_model_gradient.argtypes = [ctypes.c_void_p, ctypes.c_float, F, F]
+    lib.efm_model_train.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_uint64, F]
+    lib.efm_model_trace.argtypes = [ctypes.c_void_p, ctypes.c_void_p, _P(ctypes.c_int32), ctypes.c_int32,
+                                    _P(efm_limits), ctypes.c_int64]
+    for name in ("efm_model_create", "efm_model_params", "efm_model_add_rows", "efm_model_rows",
+                 "efm_model_clear_rows", "efm_model_forward", "efm_model_gradient", "efm_model_train",
+                 "efm_model_trace"):
+        getattr(lib, name).restype = ctypes.c_int
+    lib.efm_model_free.argtypes = [ctypes.c_void_p]
+    lib.efm_model_free.restype = None
     _lib = lib
     return lib
 
@@ -149,12 +171,18 @@ def efm_column_map(net):
     return rx, d
 
 
-def efm_find_pathways(net, targets, max_len, max_secondary, max_results=0, max_frontier=0):
-    """Returns (job handle, warning flags)."""
+EFM_PLAIN, EFM_LEARNED = 0, 1
+
+
+def efm_find_pathways(net, targets, max_len, max_secondary, max_results=0, max_frontier=0, first_k=0,
+                      proposal=EFM_PLAIN, model=None):
+    """Returns (job handle, warning flags).  first_k > 0 asks for exactly the
+    K smallest results; proposal / model set the order of that search."""
     tg, ptg = _arr(targets, np.int32, ctypes.c_int32)
-    lim = efm_limits(int(max_len), int(max_secondary), int(max_results), int(max_frontier), 0, 0)
+    lim = efm_limits(int(max_len), int(max_secondary), int(max_results), int(max_frontier), int(first_k),
+                     int(proposal))
     job = ctypes.c_void_p()
-    rc = load_library().efm_find_pathways(net, ptg, len(tg), ctypes.byref(lim), None, ctypes.byref(job))
+    rc = load_library().efm_find_pathways(net, ptg, len(tg), ctypes.byref(lim), model, ctypes.byref(job))
     if rc < 0:
         raise EfmError(rc, "efm_find_pathways")
     return job.value, rc
@@ -260,6 +288,98 @@ def use_torch_allocator():
         raise EfmError(rc, "efm_set_allocator")
 
 
+# --- learned proposal ---------------------------------------------------------
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a, a.ctypes.data_as(_P(ctypes.c_float))
+
+
+def efm_model_create(seed=0, stream=None) -> int:
+    m = ctypes.c_void_p()
+    rc = load_library().efm_model_create(int(seed), _stream_handle(stream), ctypes.byref(m))
+    if rc != 0:
+        raise EfmError(rc, "efm_model_create")
+    return m.value
+
+
+def efm_model_params(model, params=None):
+    """Read the FP32 parameters (params None) or replace them."""
+    if params is None:
+        out = np.zeros(EFM_MLP_PARAMS, dtype=np.float32)
+        rc = load_library().efm_model_params(model, out.ctypes.data_as(_P(ctypes.c_float)), 0)
+        if rc != 0:
+            raise EfmError(rc, "efm_model_params")
+        return out
+    p, pp = _f32(params, (EFM_MLP_PARAMS,))
+    rc = load_library().efm_model_params(model, pp, 1)
+    if rc != 0:
+        raise EfmError(rc, "efm_model_params")
+    return p
+
+
+def efm_model_add_rows(model, x, y):
+    x, px = _f32(x, (-1, EFM_MLP_FEATURES))
+    y, py = _f32(y, (-1,))
+    rc = load_library().efm_model_add_rows(model, px, py, len(y))
+    if rc != 0:
+        raise EfmError(rc, "efm_model_add_rows")
+
+
+def efm_model_rows(model):
+    n, pos = ctypes.c_int64(), ctypes.c_int64()
+    rc = load_library().efm_model_rows(model, ctypes.byref(n), ctypes.byref(pos))
+    if rc != 0:
+        raise EfmError(rc, "efm_model_rows")
+    return n.value, pos.value
+
+
+def efm_model_clear_rows(model):
+    load_library().efm_model_clear_rows(model)
+
+
+def efm_model_forward(model, x):
+    x, px = _f32(x, (-1, EFM_MLP_FEATURES))
+    out = np.zeros(len(x), dtype=np.float32)
+    rc = load_library().efm_model_forward(model, px, len(x), out.ctypes.data_as(_P(ctypes.c_float)))
+    if rc != 0:
+        raise EfmError(rc, "efm_model_forward")
+    return out
+
+
+def efm_model_gradient(model, pos_weight=1.0):
+    g = np.zeros(EFM_MLP_PARAMS, dtype=np.float32)
+    loss = ctypes.c_float()
+    rc = load_library().efm_model_gradient(model, float(pos_weight), g.ctypes.data_as(_P(ctypes.c_float)),
+                                           ctypes.byref(loss))
+    if rc != 0:
+        raise EfmError(rc, "efm_model_gradient")
+    return g, loss.value
+
+
+def efm_model_train(model, epochs, batch_tiles=8, lr=1e-3, pos_weight=1.0, seed=0):
+    loss = ctypes.c_float()
+    rc = load_library().efm_model_train(model, int(epochs), int(batch_tiles), float(lr), float(pos_weight), int(seed),
+                                        ctypes.byref(loss))
+    if rc != 0:
+        raise EfmError(rc, "efm_model_train")
+    return loss.value
+
+
+def efm_model_trace(model, net, targets, max_len, max_secondary, first_k, max_frontier=0, rows_per_level=4096):
+    tg, ptg = _arr(targets, np.int32, ctypes.c_int32)
+    lim = efm_limits(int(max_len), int(max_secondary), 0, int(max_frontier), int(first_k), EFM_PLAIN)
+    rc = load_library().efm_model_trace(model, net, ptg, len(tg), ctypes.byref(lim), int(rows_per_level))
+    if rc != 0:
+        raise EfmError(rc, "efm_model_trace")
+
+
+def efm_model_free(model):
+    load_library().efm_model_free(model)
+
+
 # --- conveniences ------------------------------------------------------------
 
 class Network:
@@ -283,10 +403,11 @@ class Network:
 
 
 def enumerate_targets(network: Network, targets, max_len, max_secondary, max_results=0, max_frontier=0,
-                      timing=False):
+                      timing=False, first_k=0, proposal=EFM_PLAIN, model=None):
     """Run efm_find_pathways over `targets` and fetch every target's result.
     Returns a list of (supports, counters[, timing dict])."""
-    job, _ = efm_find_pathways(network.handle, list(targets), max_len, max_secondary, max_results, max_frontier)
+    job, _ = efm_find_pathways(network.handle, list(targets), max_len, max_secondary, max_results, max_frontier,
+                               first_k, proposal, model)
     try:
         out = []
         for i in range(len(targets)):

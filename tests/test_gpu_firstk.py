@@ -1,0 +1,90 @@
+"""First-K queries on the GPU against the oracle's definition.
+
+The first-K answer is the K smallest results of the complete traversal in
+the output order (|U|, then the ascending column list).  The oracle computes
+it by deepening the length bound; the CUDA path by one traversal with an
+exact branch and bound between chunks of each level.  The sets must be
+bit-identical, for every order the search may take.
+"""
+import numpy as np
+import pytest
+
+from paper_1804_02867_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def efm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1804_02867_gb300 import build, efmgraph
+
+    build.build()
+    efmgraph.load_library()
+    return efmgraph
+
+
+def gpu_first_k(efm, nw, targets, k, L, S, **kw):
+    return efm.enumerate_targets(nw, targets, L, S, 0, kw.pop("max_frontier", 0), first_k=k, **kw)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_tiny_first_k(oracle_lib, efm, seed):
+    net = synth.tiny(seed)
+    targets = list(net.targets) + [-1]
+    with efm.Network(net) as nw:
+        for k in (1, 4, 30, 100000):
+            got = gpu_first_k(efm, nw, targets, k, 9, 1)
+            for t, (sup, ctr) in zip(targets, got):
+                want, _ = oracle_lib.first_k(net, t, k, 9, 1)
+                assert np.array_equal(sup, want), (seed, t, k)
+
+
+# (target, K) pairs of the core-shaped network whose oracle answer takes seconds
+CORE_CASES = [(63, 10), (63, 40), (58, 50), (5, 10), (65, 50), (15, 50), (42, 10), (1, 100)]
+
+
+def test_core_first_k(oracle_lib, efm):
+    net = synth.core()
+    with efm.Network(net) as nw:
+        for t, k in CORE_CASES:
+            (sup, ctr), = gpu_first_k(efm, nw, [t], k, 30, 4)
+            want, P = oracle_lib.first_k(net, t, k, 30, 4)
+            assert np.array_equal(sup, want), (t, k, P)
+            assert len(sup) == k
+
+
+# genome-shaped network: targets and K whose answer lies at |U| <= 7
+GENOME_CASES = [(705, 100), (924, 200), (883, 80), (402, 80), (791, 6)]
+
+
+def test_genome_first_k(oracle_lib, efm):
+    net = synth.genome()
+    with efm.Network(net) as nw:
+        for t, k in GENOME_CASES:
+            (sup, ctr), = gpu_first_k(efm, nw, [t], k, 40, 4, max_frontier=1 << 21)
+            assert ctr["status"] & 1 == 0, (t, ctr)
+            want, P = oracle_lib.first_k(net, t, k, 40, 4)
+            assert np.array_equal(sup, want), (t, k, P)
+
+
+def test_first_k_is_prefix_of_exhaustive(efm):
+    """At a length bound the exhaustive traversal completes, the first-K
+    answer is the first K rows of the exhaustive output."""
+    net = synth.core()
+    with efm.Network(net) as nw:
+        for t in (63, 65, 42):
+            (full, _), = efm.enumerate_targets(nw, [t], 16, 4)
+            for k in (1, 7, len(full), len(full) + 5):
+                (sup, _), = gpu_first_k(efm, nw, [t], k, 16, 4)
+                assert np.array_equal(sup, full[:k]), (t, k)
+
+
+def test_first_k_rejects_cap(efm):
+    net = synth.tiny(0)
+    with efm.Network(net) as nw:
+        with pytest.raises(efm.EfmError):
+            efm.efm_find_pathways(nw.handle, [-1], 8, 1, max_results=5, first_k=3)

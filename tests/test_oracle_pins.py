@@ -212,3 +212,15 @@ def test_invalid_inputs_rejected(oracle_lib):
         oracle_lib.enumerate_pathways(net, net.n_met, oracle_lib.Limits(8, 1, 0, 0))
     with pytest.raises(RuntimeError):
         oracle_lib.enumerate_pathways(net, -1, oracle_lib.Limits(65, 1, 0, 0))
+
+
+def test_first_k_is_prefix_of_full_enumeration(oracle_lib):
+    """first_k by popcount deepening equals the k smallest of the complete
+    enumeration (no budget, no cap)."""
+    for seed in range(6):
+        net = synth.tiny(seed)
+        for t in list(net.targets) + [-1]:
+            full, _ = oracle_lib.enumerate_pathways(net, t, oracle_lib.Limits(9, 1, 0, 0))
+            for k in (1, 3, 10, 1000):
+                got, _ = oracle_lib.first_k(net, t, k, 9, 1)
+                assert np.array_equal(got, full[:k]), (seed, t, k)
