@@ -60,8 +60,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--budget", type=int, default=BUDGET)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["core", "batched", "genome"], default="core",
-                    help="core: the headline line; batched: 4096 uneven networks in one persistent launch")
+    ap.add_argument("--workload", choices=["core", "batched", "genome", "firstk"], default="core",
+                    help="core: the headline line; batched: 4096 uneven networks in one persistent launch; "
+                         "genome: the genome-shaped network; firstk: first-K queries, learned vs plain order")
     ap.add_argument("--jobs", type=int, default=4096)
     ap.add_argument("--targets", type=str, default="",
                     help="comma-separated positions among the 8 targets (profiling a smaller case)")
@@ -338,7 +339,7 @@ def run_ours(args):
         "expansions_per_step": tot_exp / args.steps / max(ws, 1),
         "results_per_step": tot_res / args.steps / max(ws, 1),
         "roofline": {
-            "kernel": "expand_kernel<2>",
+            "kernel": "expand_kernel<8,2>",
             "bound": "hbm",
             "achieved": achieved,
             "peak": float(peaks["hbm_gbs"]),
@@ -509,6 +510,102 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+FIRSTK_K = 1000
+FIRSTK_TRAIN = 64         # genome target positions [0, 64) train the model
+FIRSTK_BUDGET = 2**22
+
+
+def run_firstk(args):
+    """First-K queries (K = 1000 smallest results) on the genome-shaped
+    network, learned order against plain order, same kernels, same GPU.
+
+    Setup (untimed): a proposal model is trained on traces of plain first-K
+    searches: genome targets at positions 0-63 (K = 1000), the core network's
+    8 targets and 64 batched-workload networks (K = 100 each).  One step =
+    the first-K query of every held-out genome target (positions 64 .. 63 +
+    --jobs, at most 192), once in plain order and once in learned order.
+    value = plain time / learned time over the targets both orders certify
+    (the answer is exact only when no level overflows the frontier budget);
+    both answers must be identical there."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1804_02867_gb300 import build as libbuild
+    from paper_1804_02867_gb300 import efmgraph, synth
+
+    libbuild.build()
+    efmgraph.load_library()
+    stream = torch.cuda.current_stream()
+    net = synth.genome()
+    n_eval = min(args.jobs, len(net.targets) - FIRSTK_TRAIN)
+    train_t = [int(t) for t in net.targets[:FIRSTK_TRAIN]]
+    eval_t = [int(t) for t in net.targets[FIRSTK_TRAIN:FIRSTK_TRAIN + n_eval]]
+    nw = efmgraph.Network(net, stream)
+    model = efmgraph.efm_model_create(1, stream)
+    t0 = time.time()
+    efmgraph.efm_model_trace(model, nw.handle, train_t, 40, MAX_SEC, FIRSTK_K, FIRSTK_BUDGET, rows_per_level=8192)
+    core = synth.core()
+    with efmgraph.Network(core, stream) as cw:
+        efmgraph.efm_model_trace(model, cw.handle, list(core.targets), MAX_LEN, MAX_SEC, 100, FIRSTK_BUDGET, 8192)
+    for i in range(64):
+        bn = synth.batched_member(i)
+        with efmgraph.Network(bn, stream) as bw:
+            efmgraph.efm_model_trace(model, bw.handle, [bn.targets[0]], min(MAX_LEN, bw.n_columns), MAX_SEC, 100,
+                                     2**16, 2048)
+    n_rows, n_pos = efmgraph.efm_model_rows(model)
+    trace_s = time.time() - t0
+    pos_weight = float(min(50.0, max(1.0, (n_rows - n_pos) / max(n_pos, 1))))
+    t0 = time.time()
+    loss = efmgraph.efm_model_train(model, epochs=20, batch_tiles=16, lr=1e-3, pos_weight=pos_weight)
+    train_s = time.time() - t0
+
+    def query(t, learned):
+        kw = dict(first_k=FIRSTK_K, proposal=efmgraph.EFM_LEARNED, model=model) if learned else dict(first_k=FIRSTK_K)
+        (sup, ctr, tm), = efmgraph.enumerate_targets(nw, [t], 40, MAX_SEC, 0, FIRSTK_BUDGET, timing=True, **kw)
+        return sup, ctr, tm
+
+    for _ in range(args.warmup):
+        for t in eval_t[:4]:
+            query(t, False)
+            query(t, True)
+    torch.cuda.synchronize()
+    rows = []
+    for _ in range(args.steps):
+        for t in eval_t:
+            a, ca, ta = query(t, False)
+            b, cb, tb = query(t, True)
+            rows.append((t, a, ca, ta, b, cb, tb))
+    nw.close()
+    efmgraph.efm_model_free(model)
+    both = [r for r in rows if not (r[2]["status"] & 1) and not (r[5]["status"] & 1)]
+    plain_ms = sum(r[3]["total_ms"] for r in both)
+    learned_ms = sum(r[6]["total_ms"] for r in both)
+    identical = all(np.array_equal(r[1], r[4]) for r in both)
+    line = {
+        "metric": METRIC, "value": plain_ms / learned_ms if learned_ms else None,
+        "unit": "x (time to certified first-K: plain order / learned order)", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sum(r[3]["total_ms"] + r[6]["total_ms"] for r in rows) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32 (search), bf16 (model)",
+        "data": "synthetic (seeded genome-shaped network; model trained on traces of other targets and networks)",
+        "config": {"workload": f"first-K: genome-1000x2500, K={FIRSTK_K}, {n_eval} held-out targets",
+                   "max_len": 40, "max_secondary": MAX_SEC, "max_frontier": FIRSTK_BUDGET,
+                   "model": "MLP 128-256-1, BF16 weights, FP32 accumulate (tcgen05)"},
+        "first_k": {"certified_both": len(both) // args.steps,
+                    "certified_plain_only": sum(1 for r in rows if not (r[2]["status"] & 1) and r[5]["status"] & 1)
+                    // args.steps,
+                    "certified_learned_only": sum(1 for r in rows if r[2]["status"] & 1 and not (r[5]["status"] & 1))
+                    // args.steps,
+                    "identical_sets": identical,
+                    "plain_ms": plain_ms / args.steps, "learned_ms": learned_ms / args.steps,
+                    "plain_expansions": sum(r[2]["expansions"] for r in both) // args.steps,
+                    "learned_expansions": sum(r[5]["expansions"] for r in both) // args.steps},
+        "training": {"rows": n_rows, "positives": n_pos, "pos_weight": pos_weight, "epochs": 20,
+                     "final_loss": loss, "trace_s": trace_s, "train_s": train_s},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -517,6 +614,8 @@ def main():
         run_batched(args)
     elif args.workload == "genome":
         run_genome(args)
+    elif args.workload == "firstk":
+        run_firstk(args)
     else:
         run_ours(args)
 

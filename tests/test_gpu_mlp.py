@@ -169,3 +169,42 @@ def test_model_argument_rules(efm):
             efm.efm_model_add_rows(m, np.zeros((2, 128)), np.array([0.0, 0.5]))
     finally:
         efm.efm_model_free(m)
+
+
+def test_trained_model_reaches_k_sooner(efm):
+    """What the model gains: trained on traces of 16 genome targets, it
+    orders the first-K=1000 searches of 16 other targets.  Where both orders
+    certify their answer (no level overflowed the budget), the answers are
+    identical and the learned order takes less time in total."""
+    net = synth.genome()
+    tg = [int(t) for t in net.targets]
+    K = 1000
+    m = efm.efm_model_create(1)
+    try:
+        with efm.Network(net) as nw:
+            efm.efm_model_trace(m, nw.handle, tg[:16], 40, 4, K, max_frontier=1 << 22, rows_per_level=8192)
+            n, pos = efm.efm_model_rows(m)
+            assert 0 < pos < n
+            efm.efm_model_train(m, epochs=20, batch_tiles=16, lr=1e-3, pos_weight=min(50.0, (n - pos) / pos))
+
+            def best(t, **kw):
+                runs = [efm.enumerate_targets(nw, [t], 40, 4, 0, 1 << 22, timing=True, first_k=K, **kw)[0]
+                        for _ in range(2)]
+                return min(runs, key=lambda r: r[2]["total_ms"])
+
+            plain_ms = learned_ms = 0.0
+            both = 0
+            for t in tg[128:144]:
+                a, ca, ta = best(t)
+                b, cb, tb = best(t, proposal=efm.EFM_LEARNED, model=m)
+                if ca["status"] & 1 or cb["status"] & 1:
+                    continue
+                assert np.array_equal(a, b), t
+                both += 1
+                plain_ms += ta["total_ms"]
+                learned_ms += tb["total_ms"]
+    finally:
+        efm.efm_model_free(m)
+    print(f"certified by both: {both}; plain {plain_ms:.1f} ms, learned {learned_ms:.1f} ms")
+    assert both >= 4
+    assert learned_ms < plain_ms
