@@ -73,6 +73,13 @@ def _load():
         lib.oracle_column_map.argtypes = [ctypes.c_int32, P(ctypes.c_uint8), P(ctypes.c_int32),
                                           P(ctypes.c_int32)]
         lib.oracle_column_map.restype = ctypes.c_int
+        lib.oracle_sample.argtypes = [
+            ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32),
+            P(ctypes.c_uint8), P(ctypes.c_uint8), ctypes.c_int32, P(_Limits), ctypes.c_uint64, ctypes.c_int64,
+            P(P(ctypes.c_uint64)), P(ctypes.c_int64), P(ctypes.c_int32), P(_Counters)]
+        lib.oracle_sample.restype = ctypes.c_int
+        lib.oracle_splitmix_at.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        lib.oracle_splitmix_at.restype = ctypes.c_uint64
         lib.oracle_free.argtypes = [ctypes.c_void_p]
         lib.oracle_free.restype = None
         _lib = lib
@@ -112,6 +119,41 @@ def enumerate_pathways(net, target: int, limits: Limits):
         arr = np.zeros((0, w), dtype=np.uint64)
     lib.oracle_free(out)
     return arr, {f: int(getattr(ctr, f)) for f in COUNTER_FIELDS}
+
+
+def sample_pathways(net, target: int, limits: Limits, seed: int, n_walks: int):
+    """Monte-Carlo mode: n_walks random walks (one random OR branch per
+    step, SplitMix64 counters under `seed`).  Returns (distinct accepted
+    supports sorted like enumerate_pathways, counters dict)."""
+    lib = _load()
+    rp = np.ascontiguousarray(net.row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(net.col_idx, dtype=np.int32)
+    cf = np.ascontiguousarray(net.coef, dtype=np.int32)
+    rv = np.ascontiguousarray(net.reversible, dtype=np.uint8)
+    ex = np.ascontiguousarray(net.external, dtype=np.uint8)
+    lim = _Limits(limits.max_len, limits.max_secondary, 0, 0)
+    out = ctypes.POINTER(ctypes.c_uint64)()
+    n = ctypes.c_int64(0)
+    W = ctypes.c_int32(0)
+    ctr = _Counters()
+    rc = lib.oracle_sample(net.n_met, net.n_rxn, _ptr(rp, ctypes.c_int32), _ptr(ci, ctypes.c_int32),
+                           _ptr(cf, ctypes.c_int32), _ptr(rv, ctypes.c_uint8), _ptr(ex, ctypes.c_uint8), int(target),
+                           ctypes.byref(lim), ctypes.c_uint64(seed), int(n_walks), ctypes.byref(out), ctypes.byref(n),
+                           ctypes.byref(W), ctypes.byref(ctr))
+    if rc != 0:
+        if out:
+            lib.oracle_free(out)
+        raise RuntimeError(f"oracle_sample failed with code {rc}")
+    w = W.value
+    arr = np.ctypeslib.as_array(out, shape=(n.value * w,)).copy().reshape(n.value, w) if n.value > 0 else \
+        np.zeros((0, w), dtype=np.uint64)
+    lib.oracle_free(out)
+    return arr, {f: int(getattr(ctr, f)) for f in COUNTER_FIELDS}
+
+
+def splitmix_at(seed: int, c: int) -> int:
+    """The oracle's counter-based random number (SplitMix64 first output)."""
+    return int(_load().oracle_splitmix_at(ctypes.c_uint64(seed), ctypes.c_uint64(c)))
 
 
 def rank(A, force_big: bool = False) -> int:

@@ -955,6 +955,163 @@ done:
     return rc;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Monte-Carlo mode: the paper's own random walks                            */
+/* ------------------------------------------------------------------------ */
+
+/* The random number of counter c under key `seed`: the first output of the
+ * SplitMix64 generator (Steele, Lea and Flood, OOPSLA 2014) started from
+ * state seed + c * 0x9E3779B97F4A7C15. */
+static uint64_t splitmix_at(uint64_t seed, uint64_t c)
+{
+    uint64_t z = seed + (c + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+uint64_t oracle_splitmix_at(uint64_t seed, uint64_t c) { return splitmix_at(seed, c); }
+
+/*
+ * Walk w of n_walks (INIT then METAx of Alg. 3 with its random choices, in
+ * the exact integer form of the exhaustive traversal):
+ *   counter base c0 = 128 w;
+ *   seed column = the (r(c0) mod n)-th of the target's n seed columns in
+ *   ascending order (every column for target -1), EF = S_int[:, j] / gcd;
+ *   step s = 1, 2, ...: a balanced EF ends the walk (its support is judged
+ *   once per run, like the traversal's); otherwise the acting metabolite is
+ *   chosen as in the traversal, its valid branches (ascending columns, the
+ *   traversal's twin and length / secondary rules) are counted, none ends
+ *   the walk as a dead end, else branch number r(c0 + s) mod count is taken
+ *   and the AND update applied (an entry outside int32 ends the walk as
+ *   overflow).
+ * Counters: seeds = walks started, expansions = AND updates, overflow and
+ * balanced = walks ended so, pruned = walks ended at a dead end,
+ * levels = the most steps of a walk; frontier counters stay 0.
+ */
+int oracle_sample(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, const int32_t *col_idx,
+                  const int32_t *coef, const uint8_t *reversible, const uint8_t *external, int32_t target,
+                  const or_limits *lim, uint64_t seed, int64_t n_walks, uint64_t **out_supports, int64_t *out_n,
+                  int32_t *out_W, or_counters *ctr)
+{
+    or_net g;
+    int rc = net_build(&g, n_met, n_rxn, row_ptr, col_idx, coef, reversible, external);
+    *out_supports = NULL;
+    *out_n = 0;
+    memset(ctr, 0, sizeof(*ctr));
+    if (rc != OR_OK) {
+        net_free(&g);
+        return rc;
+    }
+    if (target < -1 || target >= n_met || lim->max_len < 1 || lim->max_len > 64 || lim->max_secondary < 0 ||
+        lim->max_secondary > 63 || n_walks < 0 || g.W > 64) {
+        net_free(&g);
+        return OR_EINVAL;
+    }
+    *out_W = g.W;
+    const int M = g.M, N = g.N, W = g.W;
+    or_run R;
+    memset(&R, 0, sizeof(R));
+    R.g = &g;
+    R.lim = lim;
+    R.ctr = ctr;
+    R.seen.W = W;
+    R.results.stride = sizeof(uint64_t) * (size_t)(W + 1);
+    int *seeds = (int *)malloc(sizeof(int) * (size_t)N);
+    int *valid = (int *)malloc(sizeof(int) * (size_t)N);
+    int64_t *ef = (int64_t *)malloc(sizeof(int64_t) * (size_t)(M > 0 ? M : 1));
+    int32_t *EF = (int32_t *)malloc(sizeof(int32_t) * (size_t)(M > 0 ? M : 1));
+    uint64_t U[64];
+    if (!seeds || !valid || !ef || !EF) { rc = OR_ENOMEM; goto done; }
+    int n_seeds = 0;
+    for (int j = 0; j < N; ++j)
+        if (target < 0 || full_coef(target, j, &g, row_ptr, col_idx, coef) > 0) seeds[n_seeds++] = j;
+    for (int64_t w = 0; w < n_walks && n_seeds > 0; ++w) {
+        const uint64_t c0 = (uint64_t)w * 128u;
+        const int j = seeds[splitmix_at(seed, c0) % (uint64_t)n_seeds];
+        ctr->seeds++;
+        memset(U, 0, sizeof(U));
+        U[j >> 6] |= 1ull << (j & 63);
+        for (int i = 0; i < M; ++i) ef[i] = g.S[(size_t)i * N + j];
+        int zero = 0, pc = 1, sec = 0;
+        int64_t steps = 0;
+        if (normalise(ef, M, EF, &zero)) {
+            ctr->overflow++;
+            continue;
+        }
+        for (int s = 1;; ++s) {
+            if (zero) {
+                ctr->balanced++;
+                if ((rc = judge(&R, U, 0)) != OR_OK) goto done;
+                break;
+            }
+            int piv = -1, best = 0;
+            for (int i = 0; i < M; ++i) {
+                if (EF[i] == 0) continue;
+                int d = EF[i] > 0 ? g.deg_out[i] : g.deg_in[i];
+                if (piv < 0 || d < best) { piv = i; best = d; }
+            }
+            const int64_t ef_i = EF[piv];
+            int n_valid = 0;
+            for (int k = 0; k < N; ++k) {
+                const int64_t s_ik = g.S[(size_t)piv * N + k];
+                if (!(ef_i > 0 ? s_ik < 0 : s_ik > 0)) continue;
+                if (g.twin[k] >= 0 && bit_test(U, g.twin[k])) continue;
+                const int in_u = bit_test(U, k);
+                if (!in_u && pc + 1 > lim->max_len) continue;
+                if (in_u && sec + 1 > lim->max_secondary) continue;
+                valid[n_valid++] = k;
+            }
+            if (n_valid == 0) {
+                ctr->pruned++;
+                break;
+            }
+            const int k = valid[splitmix_at(seed, c0 + (uint64_t)s) % (uint64_t)n_valid];
+            const int64_t s_ik = g.S[(size_t)piv * N + k];
+            ctr->expansions++;
+            ++steps;
+            const uint64_t g0 = gcd_u64(abs_i64(ef_i), abs_i64(s_ik));
+            const int64_t a = (int64_t)(abs_i64(s_ik) / g0);
+            const int64_t c = (int64_t)(abs_i64(ef_i) / g0);
+            for (int i = 0; i < M; ++i) ef[i] = a * (int64_t)EF[i] + c * g.S[(size_t)i * N + k];
+            if (bit_test(U, k)) {
+                ++sec;
+            } else {
+                U[k >> 6] |= 1ull << (k & 63);
+                ++pc;
+            }
+            if (normalise(ef, M, EF, &zero)) {
+                ctr->overflow++;
+                break;
+            }
+        }
+        if (steps > ctr->levels) ctr->levels = steps;
+    }
+    if (ctr->overflow) ctr->status |= OR_OVERFLOW_DROPPED;
+    {
+        size_t n = R.results.n;
+        uint64_t *out = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)W * (n > 0 ? n : 1));
+        if (!out) { rc = OR_ENOMEM; goto done; }
+        for (size_t r = 0; r < n; ++r)
+            memcpy(out + r * W, vec_at(&R.results, r), sizeof(uint64_t) * (size_t)W);
+        g_W = W;
+        qsort(out, n, sizeof(uint64_t) * (size_t)W, cmp_support);
+        *out_supports = out;
+        *out_n = (int64_t)n;
+    }
+    rc = OR_OK;
+done:
+    free(seeds);
+    free(valid);
+    free(ef);
+    free(EF);
+    free(R.results.data);
+    free(R.seen.keys);
+    free(R.seen.used);
+    net_free(&g);
+    return rc;
+}
+
 /* column -> (original reaction, direction), as used for supports */
 int oracle_column_map(int32_t n_rxn, const uint8_t *reversible, int32_t *col_rxn, int32_t *col_dir)
 {

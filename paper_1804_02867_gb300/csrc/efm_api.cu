@@ -686,8 +686,9 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
                 const double n_child = (double)(h[C_EXP] - exp_before);
                 out.expand_bytes += state_bytes * ((double)cn + n_new) + 16.0 * n_child;
                 if (getenv("EFM_DEBUG"))
-                    fprintf(stderr, "efm: level %d parents %lld children %.0f new %.0f bytes %.0f ms %.3f\n", level,
-                            (long long)cn, n_child, n_new, state_bytes * ((double)cn + n_new) + 16.0 * n_child, ms);
+                    fprintf(stderr, "efm: level %d parents %lld items %llu children %.0f new %.0f bytes %.0f ms %.3f\n",
+                            level, (long long)cn, (unsigned long long)(c0 == 0 && chunk >= n_front ? deg_sum : 0),
+                            n_child, n_new, state_bytes * ((double)cn + n_new) + 16.0 * n_child, ms);
                 exp_before = h[C_EXP];
                 next_before = next_now;
             }

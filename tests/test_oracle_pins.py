@@ -224,3 +224,44 @@ def test_first_k_is_prefix_of_full_enumeration(oracle_lib):
             for k in (1, 3, 10, 1000):
                 got, _ = oracle_lib.first_k(net, t, k, 9, 1)
                 assert np.array_equal(got, full[:k]), (seed, t, k)
+
+
+def test_splitmix_published_outputs(oracle_lib):
+    """The walks' counter-based generator is SplitMix64: from state 0 its
+    first outputs are the published 0xe220a8397b1dcdaf, 0x6e789e6aa1b965f4,
+    0x06c45d188009454f."""
+    assert [oracle_lib.splitmix_at(0, c) for c in range(3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4,
+                                                                0x06C45D188009454F]
+
+
+def test_sampled_results_are_exhaustive_results(oracle_lib):
+    """Every walk follows one branch sequence of the traversal, so the
+    sampled results lie inside the exhaustive result set; each walk ends in
+    exactly one way; enough walks find every result of a tiny network."""
+    for seed in range(6):
+        net = synth.tiny(seed)
+        for t in list(net.targets) + [-1]:
+            full, _ = oracle_lib.enumerate_pathways(net, t, oracle_lib.Limits(9, 1, 0, 0))
+            sup, c = oracle_lib.sample_pathways(net, t, oracle_lib.Limits(9, 1), 11, 3000)
+            assert set(oracle_lib.supports_to_lists(sup)) <= set(oracle_lib.supports_to_lists(full))
+            assert c["balanced"] + c["overflow"] + c["pruned"] == c["seeds"]
+            assert c["results"] == len(sup) <= c["candidates"] <= c["balanced"]
+    net = synth.tiny(3)
+    full, _ = oracle_lib.enumerate_pathways(net, -1, oracle_lib.Limits(9, 1, 0, 0))
+    sup, _ = oracle_lib.sample_pathways(net, -1, oracle_lib.Limits(9, 1), 5, 200000)
+    assert np.array_equal(sup, full)
+    net = synth.core()
+    full, _ = oracle_lib.enumerate_pathways(net, 63, oracle_lib.Limits(16, 4, 0, 0))
+    sup, _ = oracle_lib.sample_pathways(net, 63, oracle_lib.Limits(16, 4), 3, 20000)
+    assert set(oracle_lib.supports_to_lists(sup)) <= set(oracle_lib.supports_to_lists(full)) and len(sup) > 0
+
+
+def test_sampling_a_chain_is_deterministic(oracle_lib):
+    """On the hand-worked chain every step has one valid branch, so every
+    walk reaches the one pathway."""
+    case = next(c for c in _handworked() if c["name"] == "chain")
+    net = synth.Network.from_dense(case["S"], case["reversible"], case["external"])
+    sup, c = oracle_lib.sample_pathways(net, case["target"], oracle_lib.Limits(case["max_len"], case["max_secondary"]),
+                                        1, 50)
+    assert oracle_lib.supports_to_lists(sup) == [tuple(x) for x in case["expected"]]
+    assert c["balanced"] == 50 and c["candidates"] == 1
