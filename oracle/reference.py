@@ -76,7 +76,11 @@ def _normalise(ef):
     return tuple(x // g for x in ef), False
 
 
-def enumerate_reference(net, target, max_len=64, max_secondary=4, max_results=0, max_frontier=0):
+def enumerate_reference(net, target, max_len=64, max_secondary=4, max_results=0, max_frontier=0, fluxes=None):
+    """The traversal in pure Python.  Returns (sorted result supports as
+    int bitmasks, counters).  fluxes: optional dict, filled with support ->
+    the flux vector {column: flux} of the first path reaching each balanced
+    support (S_int v = 0 there)."""
     S_int, twin, full, cols = split_network(net)
     M = len(S_int)
     N = len(cols)
@@ -126,6 +130,8 @@ def enumerate_reference(net, target, max_len=64, max_secondary=4, max_results=0,
         check_invariant(U, ef, v)
         if zero:
             ctr["balanced"] += 1
+            if fluxes is not None and U not in fluxes:
+                fluxes[U] = v
             judge(U, 0)
         else:
             F[(U, ef)] = (0, v, scale)
@@ -185,6 +191,8 @@ def enumerate_reference(net, target, max_len=64, max_secondary=4, max_results=0,
                 check_invariant(U2, nef, v2)
                 if zero:
                     ctr["balanced"] += 1
+                    if fluxes is not None and U2 not in fluxes:
+                        fluxes[U2] = v2
                     judge(U2, level)
                     continue
                 # the new column completes a result accepted at an earlier level

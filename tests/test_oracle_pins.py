@@ -265,3 +265,41 @@ def test_sampling_a_chain_is_deterministic(oracle_lib):
                                         1, 50)
     assert oracle_lib.supports_to_lists(sup) == [tuple(x) for x in case["expected"]]
     assert c["balanced"] == 50 and c["candidates"] == 1
+
+
+def test_flux_vectors_hand_worked(oracle_lib):
+    from oracle import flux
+
+    for case in _handworked():
+        if "flux" not in case:
+            continue
+        net = synth.Network.from_dense(case["S"], case["reversible"], case["external"])
+        sup, _ = oracle_lib.enumerate_pathways(net, case["target"],
+                                               oracle_lib.Limits(case["max_len"], case["max_secondary"], 0, 0))
+        assert flux.flux_vectors(net, sup) == case["flux"], case["name"]
+
+
+def test_flux_vectors_match_the_walked_flux(oracle_lib):
+    """The null-space vector of each result equals, up to scale, the flux
+    vector the pure-Python traversal carries along the path that reached it
+    (a different computation: accumulated AND updates, Eq. 3 / Eq. 4)."""
+    from math import gcd
+
+    from oracle import bruteforce, flux, reference
+
+    for seed in range(6):
+        net = synth.tiny(seed)
+        S_int, _, _ = bruteforce.split(net)
+        for t in list(net.targets) + [-1]:
+            walked = {}
+            res, _ = reference.enumerate_reference(net, t, 9, 1, fluxes=walked)
+            for U in res:
+                cols = [k for k in range(64) if (U >> k) & 1]
+                v = [walked[U][k] for k in cols]
+                g = 0
+                for x in v:
+                    g = gcd(g, x)
+                want = [x // g for x in v]
+                got = flux.flux_vector(S_int, cols)
+                assert got == want, (seed, t, cols)
+                assert not np.any(S_int[:, cols] @ np.array(got, dtype=np.int64))
