@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--budget", type=int, default=BUDGET)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["core", "batched", "genome", "firstk"], default="core",
+    ap.add_argument("--workload", choices=["core", "batched", "genome", "firstk", "sample"], default="core",
                     help="core: the headline line; batched: 4096 uneven networks in one persistent launch; "
                          "genome: the genome-shaped network; firstk: first-K queries, learned vs plain order")
     ap.add_argument("--jobs", type=int, default=4096)
@@ -606,6 +606,82 @@ def run_firstk(args):
     print(json.dumps(line), flush=True)
 
 
+SAMPLE_WALKS = 2**20
+COVERAGE_TARGET, COVERAGE_LEN = 63, 16
+
+
+def run_sample(args):
+    """Monte-Carlo mode (the paper's own random walks) on the core-shaped
+    network: one step = 2^20 walks for each of the 8 targets (max_len 30,
+    4 secondary steps).  value = AND updates per second; walks, balanced
+    walks and distinct results per second alongside.  Coverage: for target
+    63 at max_len 16, where the exhaustive traversal is complete, the share
+    of its results the walks find as the walk count grows, next to the
+    coupon-collector curve N (1 - (1 - 1/N)^C) of N equally likely results
+    and its expected count N H_N to see them all (Theorem 1)."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1804_02867_gb300 import build as libbuild
+    from paper_1804_02867_gb300 import efmgraph, synth
+
+    libbuild.build()
+    efmgraph.load_library()
+    stream = torch.cuda.current_stream()
+    net = synth.core()
+    targets = [int(t) for t in net.targets]
+    nw = efmgraph.Network(net, stream)
+
+    def step(seed):
+        tot = {"expansions": 0, "seeds": 0, "balanced": 0, "results": 0}
+        for t in targets:
+            _, c = efmgraph.sample_target(nw, t, MAX_LEN, MAX_SEC, seed, SAMPLE_WALKS)
+            for k in tot:
+                tot[k] += c[k]
+        return tot
+
+    for i in range(args.warmup):
+        step(1000 + i)
+    torch.cuda.synchronize()
+    tot_ms = 0.0
+    agg = {"expansions": 0, "seeds": 0, "balanced": 0, "results": 0}
+    for i in range(args.steps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        r = step(i)
+        ev1.record(stream)
+        ev1.synchronize()
+        tot_ms += ev0.elapsed_time(ev1)
+        for k in agg:
+            agg[k] += r[k]
+    (full, _), = efmgraph.enumerate_targets(nw, [COVERAGE_TARGET], COVERAGE_LEN, MAX_SEC)
+    n_all = len(full)
+    full_set = set(map(bytes, full))
+    coverage = []
+    for lg in range(10, 23, 2):
+        sup, c = efmgraph.sample_target(nw, COVERAGE_TARGET, COVERAGE_LEN, MAX_SEC, 7, 2**lg)
+        found = set(map(bytes, sup))
+        assert found <= full_set
+        coverage.append({"walks": 2**lg, "found": len(found), "of": n_all,
+                         "uniform_coupon_expectation": n_all * (1 - (1 - 1 / n_all) ** (2**lg))})
+    nw.close()
+    h_n = sum(1.0 / k for k in range(1, n_all + 1))
+    sec = tot_ms * 1e-3
+    line = {
+        "metric": METRIC, "value": agg["expansions"] / sec, "unit": "expansions/s (AND updates of random walks)",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (seeded core-shaped network)",
+        "config": {"workload": f"Monte-Carlo walks: core-72x95, 8 targets x {SAMPLE_WALKS} walks",
+                   "max_len": MAX_LEN, "max_secondary": MAX_SEC, "rng": "SplitMix64 counters"},
+        "walks_per_s": agg["seeds"] / sec, "balanced_walks_per_s": agg["balanced"] / sec,
+        "distinct_results_per_step": agg["results"] / args.steps,
+        "coverage": {"target": COVERAGE_TARGET, "max_len": COVERAGE_LEN, "results_exhaustive": n_all,
+                     "uniform_coupon_walks_to_all": n_all * h_n, "curve": coverage},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -616,6 +692,8 @@ def main():
         run_genome(args)
     elif args.workload == "firstk":
         run_firstk(args)
+    elif args.workload == "sample":
+        run_sample(args)
     else:
         run_ours(args)
 

@@ -133,6 +133,45 @@ int efm_column_map(const efm_net *net, int32_t *orig_rxn, int8_t *dir);
 int efm_find_pathways(efm_net *net, const int32_t *targets, int32_t n_targets, const efm_limits *limits,
                       const efm_model *model, efm_job **out);
 
+/* Exact flux vectors of results (Def. 3).  For a support U whose columns
+ * have nullity(S_int[:, U]) = 1, the balanced flux modes on U form one ray;
+ * this returns its primitive integer representative (entries with gcd 1),
+ * which is positive on every column of U.  Computed on the device, one warp
+ * per support, by exact integer elimination of the rows U touches.
+ *  supports  host, n x words_per_set uint64 (e.g. rows of efm_fetch_results)
+ *  flux      host, n x EFM_FLUX_COLUMNS int64: row r holds the flux of the
+ *            support's columns in ascending column order, zero-padded
+ *  status    host, n: 1 = exact vector; 0 = an intermediate value left int64
+ *            (row zeroed); -1 = not a single positive ray (nullity != 1, no
+ *            columns, more than 64 columns, or mixed signs; row zeroed)
+ * Synchronous on the network's stream.  Errors: EFM_EINVAL, EFM_ENOMEM,
+ * EFM_ECUDA. */
+#define EFM_FLUX_COLUMNS 64
+int efm_flux_vectors(efm_net *net, const uint64_t *supports, int64_t n, int64_t *flux, int8_t *status);
+
+/* Monte-Carlo mode: the paper's own method (Alg. 3 with its random
+ * choices, Theorem 1), in the exact integer form of the traversal.  Walk w
+ * (0 <= w < n_walks) starts at a random seed column of the target and takes
+ * one random valid OR branch per step until its pathway is balanced (its
+ * support is then judged once, like the traversal's), has no valid branch
+ * (dead end) or leaves the int32 range (overflow).  Random numbers: walk w
+ * uses counters 128 w + s, s = 0 for the seed and s >= 1 for step s; the
+ * number of counter c is the first output of SplitMix64 started from state
+ * seed + c * 0x9E3779B97F4A7C15, reduced modulo the number of choices
+ * (seed columns in ascending order; valid branches in ascending column
+ * order).  The result set is therefore reproducible and lies inside the
+ * exhaustive traversal's result set for the same limits.
+ *  limits   max_len and max_secondary as for efm_find_pathways
+ *           (max_secondary <= 63); the other fields must be 0
+ *  out      one job entry; efm_fetch_results returns the distinct accepted
+ *           supports, sorted; counters: seeds = walks started, expansions =
+ *           AND updates, balanced / overflow / pruned = walks that ended
+ *           balanced / by overflow / at a dead end, levels = the most steps
+ *           of one walk, frontier counters 0.
+ * Returns the warning flags (EFM_OVERFLOW_DROPPED) or an error. */
+int efm_sample_pathways(efm_net *net, int32_t target, const efm_limits *limits, uint64_t seed, int64_t n_walks,
+                        efm_job **out);
+
 /* Batched traversal: job i enumerates the pathways of targets[i] in
  * nets[i] (Prop. 1 seeds, the same method and counters as
  * efm_find_pathways), for thousands of uneven networks in ONE persistent

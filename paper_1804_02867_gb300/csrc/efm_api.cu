@@ -812,6 +812,129 @@ extern "C" int efm_find_pathways(efm_net *net, const int32_t *targets, int32_t n
     return flags;
 }
 
+extern "C" int efm_flux_vectors(efm_net *net, const uint64_t *supports, int64_t n, int64_t *flux, int8_t *status)
+{
+    if (!net || n < 0 || (n > 0 && (!supports || !flux || !status))) return EFM_EINVAL;
+    if (n == 0) return EFM_OK;
+    cudaStream_t s = net->stream;
+    const size_t W = (size_t)net->nv.W;
+    DevBuf dsup, dflux, dst;
+    int rc = EFM_OK;
+    if (!dev_alloc(dsup, (size_t)n * W * 8, s) || !dev_alloc(dflux, (size_t)n * EFM_FLUX_COLUMNS * 8, s) ||
+        !dev_alloc(dst, (size_t)n, s)) {
+        rc = EFM_ENOMEM;
+    } else if (cudaMemcpyAsync(dsup.p, supports, (size_t)n * W * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+               launch_flux(net->nv, (const uint64_t *)dsup.p, n, (int64_t *)dflux.p, (int8_t *)dst.p, net->sm_count,
+                           s) != cudaSuccess ||
+               cudaMemcpyAsync(flux, dflux.p, (size_t)n * EFM_FLUX_COLUMNS * 8, cudaMemcpyDeviceToHost, s) !=
+                   cudaSuccess ||
+               cudaMemcpyAsync(status, dst.p, (size_t)n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+               cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        rc = EFM_ECUDA;
+    }
+    dev_free(dsup, s);
+    dev_free(dflux, s);
+    dev_free(dst, s);
+    return rc;
+}
+
+extern "C" int efm_sample_pathways(efm_net *net, int32_t target, const efm_limits *limits, uint64_t seed,
+                                   int64_t n_walks, efm_job **out)
+{
+    if (!out) return EFM_EINVAL;
+    *out = nullptr;
+    if (!net || !limits || n_walks < 0) return EFM_EINVAL;
+    efm_limits lim = *limits;
+    if (lim.max_len < 1 || lim.max_len > EFM_MAX_LEN || lim.max_secondary < 0 || lim.max_secondary > 63 ||
+        lim.first_k != 0 || lim.proposal != EFM_PLAIN || target < -1 || target >= net->n_met)
+        return EFM_EINVAL;
+    lim.max_frontier = 1;  // walks keep their state in registers: no arenas
+    cudaStream_t s = net->stream;
+    const NetView &nv = net->nv;
+    auto *job = new (std::nothrow) efm_job();
+    if (!job) return EFM_ENOMEM;
+    job->net = net;
+    job->out.resize(1);
+    TargetOut &o = job->out[0];
+    Work w;
+    int rc = alloc_work(w, net, lim, 0, s);
+    unsigned long long h[C_COUNT];
+    auto fail = [&](int code) {
+        cudaGetLastError();
+        free_work(w, s);
+        efm_free_job(job);
+        return code;
+    };
+    if (rc != EFM_OK) return fail(rc);
+    LevelArgs a{};
+    a.cslots = (unsigned long long *)w.cslots.p;
+    a.cslot_mask = w.cslot_cap - 1;
+    a.cand = (uint64_t *)w.cand.p;
+    a.cand_cap = w.cand_cap;
+    a.max_len = lim.max_len;
+    a.max_sec = lim.max_secondary;
+    a.ctr = (unsigned long long *)w.ctr.p;
+    AcceptArgs acc{};
+    acc.cand = (const uint64_t *)w.cand.p;
+    acc.res = (uint64_t *)w.res.p;
+    acc.res_cap = w.res_cap;
+    acc.rcols = nv.W > 2 ? (uint16_t *)w.rcols.p : nullptr;
+    acc.ctr = a.ctr;
+    auto sync_ctr = [&]() -> int {
+        if (cudaMemcpyAsync(h, a.ctr, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return EFM_ECUDA;
+        return err_from_bits(h[C_ERR]);
+    };
+    float ms = 0.f;
+    if (cudaMemsetAsync(a.ctr, 0, C_COUNT * 8, s) != cudaSuccess ||
+        cudaMemsetAsync(w.cslots.p, 0xFF, w.cslot_cap * 8, s) != cudaSuccess || cudaEventRecord(w.ev[0], s) != cudaSuccess ||
+        launch_walks(nv, a, target, seed, n_walks, net->sm_count, s) != cudaSuccess || cudaEventRecord(w.ev[2], s) != cudaSuccess)
+        return fail(EFM_ECUDA);
+    if ((rc = sync_ctr())) return fail(rc);
+    acc.cand_begin = 0;
+    acc.cand_end = (int64_t)h[C_CAND_N];
+    if (launch_accept(nv, acc, s) != cudaSuccess) return fail(EFM_ECUDA);
+    if ((rc = sync_ctr())) return fail(rc);
+    if ((int64_t)h[C_RES_N] > w.res_cap) return fail(EFM_ECAPACITY);
+    const int64_t res_n = (int64_t)h[C_RES_N];
+    const uint64_t n2 = next_pow2((uint64_t)std::max<int64_t>(res_n, 1));
+    if (!dev_alloc(w.sortidx, n2 * 4, s) || !dev_alloc(o.sup, (size_t)std::max<int64_t>(res_n, 1) * nv.W * 8, s))
+        return fail(EFM_ENOMEM);
+    if (launch_sort_results((const uint64_t *)w.res.p, res_n, nv.W, (uint32_t *)w.sortidx.p, (int64_t)n2,
+                            (uint64_t *)o.sup.p, res_n, s) != cudaSuccess ||
+        cudaEventRecord(w.ev[1], s) != cudaSuccess || cudaEventSynchronize(w.ev[1]) != cudaSuccess)
+        return fail(EFM_ECUDA);
+    cudaEventElapsedTime(&ms, w.ev[0], w.ev[1]);
+    o.total_ms = ms;
+    cudaEventElapsedTime(&ms, w.ev[0], w.ev[2]);
+    o.expand_ms = ms;  // the walk kernel
+    o.expand_launches = n_walks > 0 ? 1 : 0;
+    o.kernel_launches = 2 + (res_n > 0 ? 2 : 0);
+    o.n = res_n;
+    efm_counters &c = o.ctr;
+    memset(&c, 0, sizeof(c));
+    c.levels = (int64_t)h[C_LEVELS];
+    c.seeds = (int64_t)h[C_SEEDS];
+    c.expansions = (int64_t)h[C_EXP];
+    c.overflow = (int64_t)h[C_OVF];
+    c.balanced = (int64_t)h[C_BAL];
+    c.candidates = (int64_t)h[C_CAND_N];
+    c.results = (int64_t)h[C_RES];
+    c.pruned = (int64_t)h[C_PRUNED];
+    c.status = c.overflow ? EFM_OVERFLOW_DROPPED : 0;
+    o.status = (int)c.status;
+    free_work(w, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        efm_free_job(job);
+        return EFM_ECUDA;
+    }
+    *out = job;
+    return o.status;
+}
+
 namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }

@@ -394,6 +394,180 @@ __global__ void __launch_bounds__(kExpandWarps * 32) seed_kernel(NetView nv, Lev
 }
 
 // ---------------------------------------------------------------------------
+// Monte-Carlo mode: the paper's own random walks (Alg. 3 with one random OR
+// branch per step), in the exact integer form of the traversal.  One warp
+// per walk; entry m of the extra-flux row sits in lane m % 32.  Walk w draws
+// its numbers from counters 128 w + s (s = 0 picks the seed column, s >= 1
+// the branch of step s): the first output of SplitMix64 (Steele, Lea and
+// Flood, 2014) started from state seed + counter * 0x9E3779B97F4A7C15.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint64_t splitmix_at(uint64_t seed, uint64_t c)
+{
+    uint64_t z = seed + (c + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// gcd normalisation of a row held across the warp, with the int32 range test
+template <int EPL>
+__device__ __forceinline__ void walk_normalise(const int64_t (&t64)[EPL], int32_t (&t)[EPL], bool &zero, bool &ovf)
+{
+    uint64_t g = 0;
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) g = gcd64(g, abs64(t64[e]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) g = gcd64(g, __shfl_xor_sync(FULL, g, off));
+    zero = g == 0;
+    bool bad = false;
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+        const int64_t v = g > 1 ? t64[e] / (int64_t)g : t64[e];
+        bad = bad || v > 2147483647ll || v < -2147483647ll;
+        t[e] = (int32_t)v;
+    }
+    ovf = __any_sync(FULL, bad);
+}
+
+template <int EPL>
+__global__ void __launch_bounds__(kExpandWarps * 32) walk_kernel(NetView nv, LevelArgs a, int target, uint64_t seed,
+                                                                 int64_t n_walks)
+{
+    __shared__ uint64_t sU[kExpandWarps][kMaxW];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint64_t *U = sU[wid];
+    const uint32_t *bl = nv.blob;
+    const int W = nv.W, Mpad = nv.Mpad;
+    const int32_t *dcol = reinterpret_cast<const int32_t *>(bl + nv.o_dcols);
+    unsigned long long n_walk = 0, n_exp = 0, n_ovf = 0, n_bal = 0, n_dead = 0, max_steps = 0;
+    bool fatal = false;
+    // the target's seed columns: its row's positive entries, ascending columns
+    const int tb = target >= 0 ? nv.metptr[target] : 0;
+    const int te = target >= 0 ? nv.metptr[target + 1] : 0;
+    int n_seeds = target >= 0 ? 0 : nv.N;
+    for (int q0 = tb; q0 < te; q0 += 32) {
+        const int q = q0 + lane;
+        n_seeds += __popc(__ballot_sync(FULL, q < te && ent_coef(nv.metent[q]) > 0));
+    }
+    const int64_t gw = (int64_t)blockIdx.x * kExpandWarps + wid, nw = (int64_t)gridDim.x * kExpandWarps;
+    for (int64_t w = gw; w < n_walks && n_seeds > 0 && !fatal; w += nw) {
+        const uint64_t c0 = (uint64_t)w * 128u;
+        int pick = (int)(splitmix_at(seed, c0) % (uint64_t)n_seeds);
+        int j = pick;
+        if (target >= 0) {
+            for (int q0 = tb; q0 < te; q0 += 32) {
+                const int q = q0 + lane;
+                const unsigned m = __ballot_sync(FULL, q < te && ent_coef(nv.metent[q]) > 0);
+                const int c = __popc(m);
+                if (pick < c) {
+                    j = ent_index(nv.metent[q0 + (int)__fns(m, 0, pick + 1)]);
+                    break;
+                }
+                pick -= c;
+            }
+        }
+        ++n_walk;
+        for (int x = lane; x < W; x += 32) U[x] = x == (j >> 6) ? 1ull << (j & 63) : 0ull;
+        __syncwarp();
+        int64_t t64[EPL];
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) t64[e] = dcol[(size_t)j * Mpad + lane + 32 * e];
+        int32_t t[EPL];
+        bool zero, ovf;
+        walk_normalise<EPL>(t64, t, zero, ovf);
+        if (ovf) {
+            ++n_ovf;
+            continue;
+        }
+        int pc = 1, sec = 0;
+        unsigned long long steps = 0;
+        for (int s = 1;; ++s) {
+            if (zero) {
+                ++n_bal;
+                if (lane == 0 && insert_support(a, W, U, j) < INS_DUP) fatal = true;
+                fatal = __any_sync(FULL, fatal);
+                break;
+            }
+            if (s > 127) {  // every step adds a column or a secondary step: unreachable
+                if (lane == 0) record_diag(a.ctr, ERR_BOUNDS, 5, s, 127, 0);
+                fatal = true;
+                break;
+            }
+            const uint32_t key = pivot_key<EPL>(bl, nv, t, lane);
+            const int piv = (int)(key & 0xFFFFu);
+            int32_t mine = 0;
+#pragma unroll
+            for (int e = 0; e < EPL; ++e)
+                if (e == (piv >> 5)) mine = t[e];
+            const int32_t bi = __shfl_sync(FULL, mine, piv & 31);
+            const bool fwd = bi > 0;
+            const int lptr = (fwd ? nv.o_consptr : nv.o_prodptr) + piv;
+            const int lb = (int)bl[lptr], le = (int)bl[lptr + 1];
+            const int lent = fwd ? nv.o_consent : nv.o_prodent;
+            auto valid_at = [&](int q) -> bool {
+                if (q >= le) return false;
+                const int k = ent_index(bl[lent + q]);
+                const int tw = (int)bl[nv.o_twin + k];
+                if (tw >= 0 && bit_of(U, tw)) return false;
+                return bit_of(U, k) ? sec + 1 <= a.max_sec : pc + 1 <= a.max_len;
+            };
+            int cnt = 0;
+            for (int q0 = lb; q0 < le; q0 += 32) cnt += __popc(__ballot_sync(FULL, valid_at(q0 + lane)));
+            if (cnt == 0) {
+                ++n_dead;
+                break;
+            }
+            int r = (int)(splitmix_at(seed, c0 + (uint64_t)s) % (uint64_t)cnt);
+            int qs = lb;
+            for (int q0 = lb; q0 < le; q0 += 32) {
+                const unsigned m = __ballot_sync(FULL, valid_at(q0 + lane));
+                const int c = __popc(m);
+                if (r < c) {
+                    qs = q0 + (int)__fns(m, 0, r + 1);
+                    break;
+                }
+                r -= c;
+            }
+            const uint32_t br = bl[lent + qs];
+            const int k = ent_index(br);
+            const uint32_t sik = (uint32_t)ent_coef(br);  // |S_ik|
+            const uint32_t abi = (uint32_t)(bi < 0 ? -bi : bi);
+            const uint32_t g0 = gcd32(abi, sik);
+            const int64_t A = (int64_t)(sik / g0), C = (int64_t)(abi / g0);
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) t64[e] = A * t[e] + C * dcol[(size_t)k * Mpad + lane + 32 * e];
+            ++n_exp;
+            ++steps;
+            const bool in_u = bit_of(U, k);
+            __syncwarp();
+            if (in_u) {
+                ++sec;
+            } else {
+                if (lane == 0) U[k >> 6] |= 1ull << (k & 63);
+                ++pc;
+            }
+            __syncwarp();
+            j = k;
+            walk_normalise<EPL>(t64, t, zero, ovf);
+            if (ovf) {
+                ++n_ovf;
+                break;
+            }
+        }
+        max_steps = steps > max_steps ? steps : max_steps;
+    }
+    if (lane == 0) {
+        if (n_walk) atomicAdd(&a.ctr[C_SEEDS], n_walk);
+        if (n_exp) atomicAdd(&a.ctr[C_EXP], n_exp);
+        if (n_ovf) atomicAdd(&a.ctr[C_OVF], n_ovf);
+        if (n_bal) atomicAdd(&a.ctr[C_BAL], n_bal);
+        if (n_dead) atomicAdd(&a.ctr[C_PRUNED], n_dead);
+        if (max_steps) atomicMax(&a.ctr[C_LEVELS], max_steps);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // a1-a6: one level of expansion.
 //
 // Phase 1 (a group of G lanes per child): a warp takes 32 consecutive
@@ -1683,6 +1857,25 @@ __global__ void iota_kernel(uint32_t *perm, int64_t n)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) perm[i] = (uint32_t)i;
+}
+
+cudaError_t launch_walks(const NetView &nv, const LevelArgs &a, int target, uint64_t seed, int64_t n_walks, int sm_count,
+                         cudaStream_t s)
+{
+    if (n_walks <= 0) return cudaSuccess;
+    const int64_t want = (n_walks + kExpandWarps - 1) / kExpandWarps;
+    const int grid = (int)std::min<int64_t>(want, (int64_t)sm_count * 8);
+    switch (nv.EPL) {
+#define EFM_WALK(E)                                                                       \
+    case E:                                                                               \
+        walk_kernel<E><<<grid, kExpandWarps * 32, 0, s>>>(nv, a, target, seed, n_walks); \
+        break;
+        EFM_WALK(1) EFM_WALK(2) EFM_WALK(4) EFM_WALK(8) EFM_WALK(16) EFM_WALK(28) EFM_WALK(32)
+#undef EFM_WALK
+    default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_iota(uint32_t *perm, int64_t n, cudaStream_t s)

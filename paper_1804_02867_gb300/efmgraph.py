@@ -23,7 +23,8 @@ EXPORTS = ("efm_load_network", "efm_network_shape", "efm_column_map", "efm_find_
            "efm_job_timing", "efm_free_job", "efm_free_net", "efm_status_str", "efm_set_allocator",
            "efm_sort_supports_noalloc", "efm_find_pathways_batch", "efm_batch_tuning", "efm_model_create",
            "efm_model_params", "efm_model_add_rows", "efm_model_rows", "efm_model_clear_rows", "efm_model_forward",
-           "efm_model_gradient", "efm_model_train", "efm_model_trace", "efm_model_free")
+           "efm_model_gradient", "efm_model_train", "efm_model_trace", "efm_model_free", "efm_sample_pathways",
+           "efm_flux_vectors")
 EFM_NOALLOC_MAX_ROWS = 1 << 20
 EFM_MLP_FEATURES, EFM_MLP_HIDDEN = 128, 256
 EFM_MLP_PARAMS = 256 * 128 + 256 + 1
@@ -111,6 +112,12 @@ def load_library(path: str | None = None):
                  "efm_model_clear_rows", "efm_model_forward", "efm_model_gradient", "efm_model_train",
                  "efm_model_trace"):
         getattr(lib, name).restype = ctypes.c_int
+    lib.efm_flux_vectors.argtypes = [ctypes.c_void_p, _P(ctypes.c_uint64), ctypes.c_int64, _P(ctypes.c_int64),
+                                     _P(ctypes.c_int8)]
+    lib.efm_flux_vectors.restype = ctypes.c_int
+    lib.efm_sample_pathways.argtypes = [ctypes.c_void_p, ctypes.c_int32, _P(efm_limits), ctypes.c_uint64,
+                                        ctypes.c_int64, _P(ctypes.c_void_p)]
+    lib.efm_sample_pathways.restype = ctypes.c_int
     lib.efm_model_free.argtypes = [ctypes.c_void_p]
     lib.efm_model_free.restype = None
     _lib = lib
@@ -186,6 +193,45 @@ def efm_find_pathways(net, targets, max_len, max_secondary, max_results=0, max_f
     if rc < 0:
         raise EfmError(rc, "efm_find_pathways")
     return job.value, rc
+
+
+EFM_FLUX_COLUMNS = 64
+
+
+def efm_flux_vectors(net, supports):
+    """Flux vectors of uint64[n, W] supports: (int64[n, 64] fluxes in
+    ascending column order, int8[n] status: 1 exact, 0 overflow, -1 not a
+    single positive ray)."""
+    sup = np.ascontiguousarray(supports, dtype=np.uint64)
+    n = sup.shape[0] if sup.ndim == 2 else 0
+    flux = np.zeros((max(n, 1), EFM_FLUX_COLUMNS), dtype=np.int64)
+    st = np.zeros(max(n, 1), dtype=np.int8)
+    rc = load_library().efm_flux_vectors(net, sup.ctypes.data_as(_P(ctypes.c_uint64)), n,
+                                         flux.ctypes.data_as(_P(ctypes.c_int64)), st.ctypes.data_as(_P(ctypes.c_int8)))
+    if rc != 0:
+        raise EfmError(rc, "efm_flux_vectors")
+    return flux[:n], st[:n]
+
+
+def efm_sample_pathways(net, target, max_len, max_secondary, seed, n_walks):
+    """Monte-Carlo walks.  Returns (job handle, warning flags)."""
+    lim = efm_limits(int(max_len), int(max_secondary), 0, 0, 0, 0)
+    job = ctypes.c_void_p()
+    rc = load_library().efm_sample_pathways(net, int(target), ctypes.byref(lim), ctypes.c_uint64(int(seed)),
+                                            int(n_walks), ctypes.byref(job))
+    if rc < 0:
+        raise EfmError(rc, "efm_sample_pathways")
+    return job.value, rc
+
+
+def sample_target(network, target, max_len, max_secondary, seed, n_walks, timing=False):
+    """efm_sample_pathways + fetch: (supports, counters[, timing dict])."""
+    job, _ = efm_sample_pathways(network.handle, target, max_len, max_secondary, seed, n_walks)
+    try:
+        sup, ctr, _ = efm_fetch_results(job, 0)
+        return (sup, ctr, efm_job_timing(job, 0)) if timing else (sup, ctr)
+    finally:
+        efm_free_job(job)
 
 
 def efm_find_pathways_batch(nets, targets, max_len, max_secondary, max_results=0, max_frontier=1 << 12):
