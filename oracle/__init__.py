@@ -73,6 +73,11 @@ def _load():
         lib.oracle_column_map.argtypes = [ctypes.c_int32, P(ctypes.c_uint8), P(ctypes.c_int32),
                                           P(ctypes.c_int32)]
         lib.oracle_column_map.restype = ctypes.c_int
+        lib.oracle_enumerate_from.argtypes = [
+            ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32),
+            P(ctypes.c_uint8), P(ctypes.c_uint8), P(ctypes.c_int32), ctypes.c_int32, P(_Limits),
+            P(P(ctypes.c_uint64)), P(ctypes.c_int64), P(ctypes.c_int32), P(_Counters)]
+        lib.oracle_enumerate_from.restype = ctypes.c_int
         lib.oracle_sample.argtypes = [
             ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32),
             P(ctypes.c_uint8), P(ctypes.c_uint8), ctypes.c_int32, P(_Limits), ctypes.c_uint64, ctypes.c_int64,
@@ -117,6 +122,37 @@ def enumerate_pathways(net, target: int, limits: Limits):
         arr = np.ctypeslib.as_array(out, shape=(n.value * w,)).copy().reshape(n.value, w)
     else:
         arr = np.zeros((0, w), dtype=np.uint64)
+    lib.oracle_free(out)
+    return arr, {f: int(getattr(ctr, f)) for f in COUNTER_FIELDS}
+
+
+def enumerate_from(net, columns, limits: Limits):
+    """The traversal from one seed set R_in of split columns (Prop. 1):
+    every column of R_in starts with flux 1.  Returns (supports, counters)
+    like enumerate_pathways."""
+    lib = _load()
+    rp = np.ascontiguousarray(net.row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(net.col_idx, dtype=np.int32)
+    cf = np.ascontiguousarray(net.coef, dtype=np.int32)
+    rv = np.ascontiguousarray(net.reversible, dtype=np.uint8)
+    ex = np.ascontiguousarray(net.external, dtype=np.uint8)
+    cols = np.ascontiguousarray(columns, dtype=np.int32)
+    lim = _Limits(limits.max_len, limits.max_secondary, limits.max_results, limits.max_frontier)
+    out = ctypes.POINTER(ctypes.c_uint64)()
+    n = ctypes.c_int64(0)
+    W = ctypes.c_int32(0)
+    ctr = _Counters()
+    rc = lib.oracle_enumerate_from(net.n_met, net.n_rxn, _ptr(rp, ctypes.c_int32), _ptr(ci, ctypes.c_int32),
+                                   _ptr(cf, ctypes.c_int32), _ptr(rv, ctypes.c_uint8), _ptr(ex, ctypes.c_uint8),
+                                   _ptr(cols, ctypes.c_int32), len(cols), ctypes.byref(lim), ctypes.byref(out),
+                                   ctypes.byref(n), ctypes.byref(W), ctypes.byref(ctr))
+    if rc != 0:
+        if out:
+            lib.oracle_free(out)
+        raise RuntimeError(f"oracle_enumerate_from failed with code {rc}")
+    w = W.value
+    arr = np.ctypeslib.as_array(out, shape=(n.value * w,)).copy().reshape(n.value, w) if n.value > 0 else \
+        np.zeros((0, w), dtype=np.uint64)
     lib.oracle_free(out)
     return arr, {f: int(getattr(ctr, f)) for f in COUNTER_FIELDS}
 

@@ -766,10 +766,14 @@ static int normalise(const int64_t *ef, int M, int32_t *out, int *zero)
     return ovf;
 }
 
-int oracle_enumerate(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, const int32_t *col_idx,
-                     const int32_t *coef, const uint8_t *reversible, const uint8_t *external, int32_t target,
-                     const or_limits *lim, uint64_t **out_supports, int64_t *out_n, int32_t *out_W,
-                     or_counters *ctr)
+/* The traversal from the seeds of a target (seedset == NULL), or from the
+ * one state of a seed set R_in (Prop. 1): U = R_in with flux 1 on each of
+ * its columns, EF = sum of their S_int columns / gcd, no secondary step,
+ * at level |R_in| - 1 (a state's level is |U| - 1 + sec throughout). */
+static int enumerate_impl(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, const int32_t *col_idx,
+                          const int32_t *coef, const uint8_t *reversible, const uint8_t *external, int32_t target,
+                          const int32_t *seedset, int32_t n_seedset, const or_limits *lim, uint64_t **out_supports,
+                          int64_t *out_n, int32_t *out_W, or_counters *ctr)
 {
     or_net g;
     int rc = net_build(&g, n_met, n_rxn, row_ptr, col_idx, coef, reversible, external);
@@ -785,8 +789,27 @@ int oracle_enumerate(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, const
         net_free(&g);
         return OR_EINVAL;
     }
+    if (seedset) {
+        /* distinct columns, no twin pair, at most max_len of them */
+        if (n_seedset < 1 || n_seedset > lim->max_len) {
+            net_free(&g);
+            return OR_EINVAL;
+        }
+        for (int a = 0; a < n_seedset; ++a) {
+            if (seedset[a] < 0 || seedset[a] >= g.N) {
+                net_free(&g);
+                return OR_EINVAL;
+            }
+            for (int b = 0; b < a; ++b)
+                if (seedset[b] == seedset[a] || g.twin[seedset[a]] == seedset[b]) {
+                    net_free(&g);
+                    return OR_EINVAL;
+                }
+        }
+    }
     *out_W = g.W;
     const int M = g.M, N = g.N, W = g.W;
+    const int64_t level0 = seedset ? n_seedset - 1 : 0;
     const size_t key = sizeof(uint64_t) * (size_t)W + sizeof(int32_t) * (size_t)M;
     const size_t stride = key + sizeof(int32_t);
     or_run R;
@@ -802,14 +825,23 @@ int oracle_enumerate(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, const
     int32_t *efn = (int32_t *)malloc(sizeof(int32_t) * (size_t)(M > 0 ? M : 1));
     if (!rec || !ef || !efn) { rc = OR_ENOMEM; goto done; }
 
-    /* level 0: seeds (INIT) */
-    for (int j = 0; j < N; ++j) {
-        if (target >= 0 && full_coef(target, j, &g, row_ptr, col_idx, coef) <= 0) continue;
-        ctr->seeds++;
-        for (int i = 0; i < M; ++i) ef[i] = g.S[(size_t)i * N + j]; /* Eq. 2 with flux 1 on j */
+    /* level 0: seeds (INIT) -- or the one state of the seed set */
+    for (int j = 0; j < (seedset ? 1 : N); ++j) {
         uint64_t *U = (uint64_t *)rec;
         memset(U, 0, sizeof(uint64_t) * (size_t)W);
-        U[j >> 6] |= 1ull << (j & 63);
+        if (seedset) {
+            for (int i = 0; i < M; ++i) ef[i] = 0;
+            for (int a = 0; a < n_seedset; ++a) {
+                const int k = seedset[a];
+                for (int i = 0; i < M; ++i) ef[i] += g.S[(size_t)i * N + k]; /* Eq. 2, flux 1 on each */
+                U[k >> 6] |= 1ull << (k & 63);
+            }
+        } else {
+            if (target >= 0 && full_coef(target, j, &g, row_ptr, col_idx, coef) <= 0) continue;
+            for (int i = 0; i < M; ++i) ef[i] = g.S[(size_t)i * N + j]; /* Eq. 2 with flux 1 on j */
+            U[j >> 6] |= 1ull << (j & 63);
+        }
+        ctr->seeds++;
         int zero = 0;
         if (normalise(ef, M, (int32_t *)(rec + sizeof(uint64_t) * W), &zero)) {
             ctr->overflow++;
@@ -818,7 +850,7 @@ int oracle_enumerate(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, const
         *(int32_t *)(rec + key) = 0;
         if (zero) {
             ctr->balanced++;
-            if ((rc = judge(&R, U, 0)) != OR_OK) goto done;
+            if ((rc = judge(&R, U, level0)) != OR_OK) goto done;
         } else if (vec_push(&F, rec)) {
             rc = OR_ENOMEM;
             goto done;
@@ -838,7 +870,7 @@ int oracle_enumerate(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, const
         goto finish;
     }
 
-    for (int64_t level = 1; F.n > 0; ++level) {
+    for (int64_t level = level0 + 1; F.n > 0; ++level) {
         C.n = 0;
         for (size_t s = 0; s < F.n; ++s) {
             const uint8_t *st = (const uint8_t *)vec_at(&F, s);
@@ -914,7 +946,7 @@ int oracle_enumerate(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, const
         vec t = F;
         F = C;
         C = t;
-        ctr->levels = level + 1;
+        ctr->levels = level - level0 + 1;
         if (lim->max_frontier > 0 && (int64_t)F.n > lim->max_frontier) {
             ctr->status |= OR_TRUNCATED;
             break;
@@ -953,6 +985,25 @@ done:
     free(R.seen.used);
     net_free(&g);
     return rc;
+}
+
+int oracle_enumerate(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, const int32_t *col_idx,
+                     const int32_t *coef, const uint8_t *reversible, const uint8_t *external, int32_t target,
+                     const or_limits *lim, uint64_t **out_supports, int64_t *out_n, int32_t *out_W,
+                     or_counters *ctr)
+{
+    return enumerate_impl(n_met, n_rxn, row_ptr, col_idx, coef, reversible, external, target, NULL, 0, lim,
+                          out_supports, out_n, out_W, ctr);
+}
+
+int oracle_enumerate_from(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, const int32_t *col_idx,
+                          const int32_t *coef, const uint8_t *reversible, const uint8_t *external,
+                          const int32_t *seedset, int32_t n_seedset, const or_limits *lim, uint64_t **out_supports,
+                          int64_t *out_n, int32_t *out_W, or_counters *ctr)
+{
+    if (!seedset) return OR_EINVAL;
+    return enumerate_impl(n_met, n_rxn, row_ptr, col_idx, coef, reversible, external, -1, seedset, n_seedset, lim,
+                          out_supports, out_n, out_W, ctr);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -303,3 +303,42 @@ def test_flux_vectors_match_the_walked_flux(oracle_lib):
                 got = flux.flux_vector(S_int, cols)
                 assert got == want, (seed, t, cols)
                 assert not np.any(S_int[:, cols] @ np.array(got, dtype=np.int64))
+
+
+def test_seed_sets(oracle_lib):
+    """Traversal from a seed set R_in (Prop. 1): the union over single
+    columns j of the results from {j} is the result set of the all-column
+    run; every result from R_in contains R_in and is an EFM; a seed set that
+    is itself balanced with unit fluxes is its own result; twin pairs and
+    repeated columns are rejected."""
+    from oracle import bruteforce
+
+    for seed in range(5):
+        net = synth.tiny(seed)
+        S_int, twin, _ = bruteforce.split(net)
+        full, _ = oracle_lib.enumerate_pathways(net, -1, oracle_lib.Limits(9, 1, 0, 0))
+        union = set()
+        for j in range(S_int.shape[1]):
+            sup, c = oracle_lib.enumerate_from(net, [j], oracle_lib.Limits(9, 1, 0, 0))
+            got = oracle_lib.supports_to_lists(sup)
+            assert all(j in cols for cols in got)
+            union |= set(got)
+        assert union == set(oracle_lib.supports_to_lists(full)), seed
+        rng = np.random.default_rng(seed)
+        for _ in range(10):
+            R = sorted(int(x) for x in rng.choice(S_int.shape[1], size=2, replace=False))
+            if twin[R[0]] == R[1]:
+                continue
+            sup, _ = oracle_lib.enumerate_from(net, R, oracle_lib.Limits(9, 2, 0, 0))
+            for cols in oracle_lib.supports_to_lists(sup):
+                assert set(R) <= set(cols) and bruteforce.is_efm_support(S_int, cols)
+    case = next(c for c in _handworked() if c["name"] == "chain")
+    net = synth.Network.from_dense(case["S"], case["reversible"], case["external"])
+    sup, c = oracle_lib.enumerate_from(net, [0, 1], oracle_lib.Limits(4, 0, 0, 0))
+    assert oracle_lib.supports_to_lists(sup) == [(0, 1)] and c["balanced"] == 1 and c["levels"] == 1
+    net = synth.tiny(0)
+    _, twin, _ = bruteforce.split(net)
+    a = next(k for k in range(len(twin)) if twin[k] >= 0)
+    for bad in ([a, twin[a]], [1, 1], [], [10**6]):
+        with pytest.raises(RuntimeError):
+            oracle_lib.enumerate_from(net, bad, oracle_lib.Limits(9, 1, 0, 0))
