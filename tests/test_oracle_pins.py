@@ -342,3 +342,59 @@ def test_seed_sets(oracle_lib):
     for bad in ([a, twin[a]], [1, 1], [], [10**6]):
         with pytest.raises(RuntimeError):
             oracle_lib.enumerate_from(net, bad, oracle_lib.Limits(9, 1, 0, 0))
+
+
+def _dep_from_cycles(net, L):
+    """Flux-dependent pairs from the simple cycles through each metabolite
+    of the bipartite metabolite / column digraph (networkx), at most L
+    columns long: a first-return walk shortens to a simple cycle with the
+    same leaving and returning columns."""
+    import networkx as nx
+
+    from oracle import bruteforce
+
+    S_int, _, _ = bruteforce.split(net)
+    M, N = S_int.shape
+    G = nx.DiGraph()
+    for k in range(N):
+        for m in range(M):
+            if S_int[m, k] < 0:
+                G.add_edge(("m", m), ("c", k))
+            if S_int[m, k] > 0:
+                G.add_edge(("c", k), ("m", m))
+    dep_out = np.zeros((M, N), dtype=bool)
+    dep_in = np.zeros((M, N), dtype=bool)
+    for cyc in nx.simple_cycles(G, length_bound=2 * L):
+        for pos, node in enumerate(cyc):
+            if node[0] != "m":
+                continue
+            i = node[1]
+            dep_out[i, cyc[(pos + 1) % len(cyc)][1]] = True
+            dep_in[i, cyc[pos - 1][1]] = True
+    return dep_out, dep_in
+
+
+def test_dependent_reactions_match_simple_cycles():
+    from oracle import depthy
+
+    for seed in range(4):
+        for net in (synth.tiny(seed), synth.type1(seed)):
+            for L in (1, 2, 3, 4):
+                a_out, a_in = depthy.dependent_reactions(net, L)
+                b_out, b_in = _dep_from_cycles(net, L)
+                assert np.array_equal(a_out, b_out) and np.array_equal(a_in, b_in), (seed, net.name, L)
+
+
+def test_dependent_reactions_hand_worked():
+    """Internal A, B; columns c0: A -> B, c1: B -> A, c2: B -> (out), c3:
+    (in) -> A.  The only cycle is A -c0-> B -c1-> A: for A, c0 leaves and c1
+    returns; for B, c1 leaves and c0 returns.  Depth 1 finds nothing."""
+    from oracle import depthy
+
+    S = [[-1, 1, 0, 1], [1, -1, -1, 0], [0, 0, 1, 0], [0, 0, 0, -1]]
+    net = synth.Network.from_dense(S, [0, 0, 0, 0], [0, 0, 1, 1])
+    o, i = depthy.dependent_reactions(net, 2)
+    assert o.tolist() == [[True, False, False, False], [False, True, False, False]]
+    assert i.tolist() == [[False, True, False, False], [True, False, False, False]]
+    o, i = depthy.dependent_reactions(net, 1)
+    assert not o.any() and not i.any()
