@@ -133,6 +133,38 @@ int efm_column_map(const efm_net *net, int32_t *orig_rxn, int8_t *dir);
 int efm_find_pathways(efm_net *net, const int32_t *targets, int32_t n_targets, const efm_limits *limits,
                       const efm_model *model, efm_job **out);
 
+/* The traversal from a seed set R_in (Prop. 1): one starting pathway with
+ * flux 1 on each of the given split columns (EF = the sum of their S_int
+ * columns, normalised), then the same level loop, limits, pruning and
+ * minimality test as efm_find_pathways; the results are the elementary
+ * pathways reached from it (each contains R_in).  The starting state sits
+ * at level n_columns - 1 (a state's level is |U| - 1 + secondary steps).
+ *  columns    host, n_columns distinct split columns (efm_column_map), no
+ *             two of the same reaction, 1 <= n_columns <= max_len
+ *  limits     as efm_find_pathways (first_k allowed; proposal must be
+ *             EFM_PLAIN)
+ *  out        one job entry
+ * Returns the warning flags or an error (EFM_EINVAL for a bad set). */
+int efm_find_pathways_from(efm_net *net, const int32_t *columns, int32_t n_columns, const efm_limits *limits,
+                           efm_job **out);
+
+/* Flux-dependent reactions (Def. 11): the DEPTHy pre-pass (Alg. 2).
+ * A step from internal metabolite m goes through a split column k that
+ * consumes m to an internal metabolite that k produces; steps out of m are
+ * ordered by (column, product row) and r is the most steps out of any
+ * internal metabolite.  For each internal metabolite i, every walk of at
+ * most `depth` steps from i is enumerated as in Alg. 2 (r^depth digit
+ * strings, one per thread); a walk that comes back to i tags its leaving
+ * column in dep_out and its returning column in dep_in.
+ *  depth      1 .. 16, with r^depth <= 2^40 (else EFM_EUNSUPPORTED)
+ *  dep_out    host, M_int x words_per_set uint64 bitsets over split
+ *  dep_in     columns, one row per internal metabolite (original order)
+ *  steps_max  receives r (may be NULL)
+ *  kernel_ms  receives the kernel's device time (may be NULL)
+ * Synchronous on the network's stream. */
+int efm_dependent_reactions(efm_net *net, int32_t depth, uint64_t *dep_out, uint64_t *dep_in, int32_t *steps_max,
+                            double *kernel_ms);
+
 /* Exact flux vectors of results (Def. 3).  For a support U whose columns
  * have nullity(S_int[:, U]) = 1, the balanced flux modes on U form one ray;
  * this returns its primitive integer representative (entries with gcd 1),

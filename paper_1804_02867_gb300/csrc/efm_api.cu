@@ -483,8 +483,11 @@ struct Trace {
 
 bool model_reserve_rows(efm_model *m, int64_t rows);
 
+// seedset (device, n_seedset columns): start from that one state instead of
+// the target's seeds (Prop. 1), at level n_seedset - 1.
 int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetOut &out,
-               const efm_model *model = nullptr, Trace *trace = nullptr)
+               const efm_model *model = nullptr, Trace *trace = nullptr, const int32_t *seedset = nullptr,
+               int n_seedset = 0)
 {
     const NetView &nv = net->nv;
     cudaStream_t s = net->stream;
@@ -523,11 +526,15 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
     CK(cudaMemsetAsync(w.bptr.p, 0, (size_t)(nv.N + 1) * 4, s));
     CK(cudaEventRecord(w.ev[0], s));
 
-    // level 0: seeds
+    // level 0: seeds (or the seed set's one state, at level |R_in| - 1)
     int cur = 0;
-    a.level = 0;
+    const int level0 = seedset ? n_seedset - 1 : 0;
+    a.level = level0;
     a.child = arena(cur);
-    CK(launch_seed(nv, a, target, s));
+    if (seedset)
+        CK(launch_seedset(nv, a, seedset, n_seedset, s));
+    else
+        CK(launch_seed(nv, a, target, s));
     out.kernel_launches += 1;
     AcceptArgs acc{};
     acc.cand = (const uint64_t *)w.cand.p;
@@ -589,7 +596,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
     unsigned long long exp_before = 0;
     int64_t buckets_built_for = 0;
     float ms = 0.f;
-    for (int level = 1; !stop && n_front > 0; ++level) {
+    for (int level = level0 + 1; !stop && n_front > 0; ++level) {
         // every step adds a column or a secondary step, so depth is bounded
         if (level > lim.max_len + lim.max_secondary + 1) return EFM_ETIMEOUT;
         // buckets over every accepted result so far (all of them come from levels < `level`)
@@ -715,7 +722,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
         }
         n_front = (int64_t)h[C_NEXT];
         deg_sum = h[C_DEGSUM];
-        c.levels = level + 1;
+        c.levels = level - level0 + 1;
         cur ^= 1;
         if (lim.max_frontier > 0 && n_front > lim.max_frontier) {
             status |= EFM_TRUNCATED;
@@ -810,6 +817,102 @@ extern "C" int efm_find_pathways(efm_net *net, const int32_t *targets, int32_t n
     }
     *out = job;
     return flags;
+}
+
+extern "C" int efm_find_pathways_from(efm_net *net, const int32_t *columns, int32_t n_columns,
+                                      const efm_limits *limits, efm_job **out)
+{
+    if (!out) return EFM_EINVAL;
+    *out = nullptr;
+    if (!net || !columns || !limits) return EFM_EINVAL;
+    const efm_limits lim = *limits;
+    if (lim.max_len < 1 || lim.max_len > EFM_MAX_LEN || lim.max_secondary < 0 || lim.first_k < 0 ||
+        lim.proposal != EFM_PLAIN || (lim.first_k > 0 && lim.max_results != 0))
+        return EFM_EINVAL;
+    if (n_columns < 1 || n_columns > lim.max_len) return EFM_EINVAL;
+    for (int i = 0; i < n_columns; ++i) {
+        if (columns[i] < 0 || columns[i] >= net->nv.N) return EFM_EINVAL;
+        for (int j = 0; j < i; ++j) {
+            const int a = columns[i], b = columns[j];
+            const bool twins = net->col_rxn[a] == net->col_rxn[b];  // same reaction: the two directions
+            if (a == b || twins) return EFM_EINVAL;
+        }
+    }
+    auto *job = new (std::nothrow) efm_job();
+    if (!job) return EFM_ENOMEM;
+    job->net = net;
+    job->out.resize(1);
+    cudaStream_t s = net->stream;
+    Work w;
+    DevBuf cols;
+    const int total_warps = expand_grid(net->nv, net->sm_count) * kExpandWarps;
+    int rc = alloc_work(w, net, lim, total_warps, s);
+    if (rc == EFM_OK && !dev_alloc(cols, (size_t)n_columns * 4, s)) rc = EFM_ENOMEM;
+    if (rc == EFM_OK && cudaMemcpyAsync(cols.p, columns, (size_t)n_columns * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        rc = EFM_ECUDA;
+    if (rc == EFM_OK)
+        rc = run_target(net, w, lim, -1, job->out[0], nullptr, nullptr, (const int32_t *)cols.p, n_columns);
+    free_work(w, s);
+    dev_free(cols, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess && rc == EFM_OK) rc = EFM_ECUDA;
+    if (rc != EFM_OK) {
+        cudaGetLastError();
+        efm_free_job(job);
+        return rc;
+    }
+    *out = job;
+    return job->out[0].status;
+}
+
+extern "C" int efm_dependent_reactions(efm_net *net, int32_t depth, uint64_t *dep_out, uint64_t *dep_in,
+                                       int32_t *steps_max, double *kernel_ms)
+{
+    if (!net || depth < 1 || depth > 16 || !dep_out || !dep_in) return EFM_EINVAL;
+    cudaStream_t s = net->stream;
+    const NetView &nv = net->nv;
+    const size_t words = (size_t)std::max(nv.M, 1) * nv.W;
+    DevBuf r, dout, din;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = EFM_OK;
+    unsigned rh = 0;
+    if (!dev_alloc(r, 4, s) || !dev_alloc(dout, words * 8, s) || !dev_alloc(din, words * 8, s)) rc = EFM_ENOMEM;
+    if (rc == EFM_OK &&
+        (cudaMemsetAsync(r.p, 0, 4, s) != cudaSuccess || launch_step_count(nv, (unsigned *)r.p, s) != cudaSuccess ||
+         cudaMemcpyAsync(&rh, r.p, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess))
+        rc = EFM_ECUDA;
+    // r^depth walks per metabolite (Alg. 2 enumerates them all)
+    unsigned long long n_paths = 1;
+    for (int l = 0; rc == EFM_OK && l < depth; ++l) {
+        if (rh == 0) {
+            n_paths = 0;
+            break;
+        }
+        if (n_paths > (1ull << 40) / rh) rc = EFM_EUNSUPPORTED;
+        n_paths *= rh;
+    }
+    float ms = 0.f;
+    if (rc == EFM_OK &&
+        (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+         cudaMemsetAsync(dout.p, 0, words * 8, s) != cudaSuccess || cudaMemsetAsync(din.p, 0, words * 8, s) != cudaSuccess ||
+         cudaEventRecord(e0, s) != cudaSuccess ||
+         launch_depthy(nv, depth, rh, n_paths, (unsigned long long *)dout.p, (unsigned long long *)din.p, net->sm_count,
+                       s) != cudaSuccess ||
+         cudaEventRecord(e1, s) != cudaSuccess ||
+         cudaMemcpyAsync(dep_out, dout.p, (size_t)nv.M * nv.W * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         cudaMemcpyAsync(dep_in, din.p, (size_t)nv.M * nv.W * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         cudaStreamSynchronize(s) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        rc = EFM_ECUDA;
+    if (rc == EFM_OK) {
+        if (steps_max) *steps_max = (int32_t)rh;
+        if (kernel_ms) *kernel_ms = ms;
+    }
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dev_free(r, s);
+    dev_free(dout, s);
+    dev_free(din, s);
+    return rc;
 }
 
 extern "C" int efm_flux_vectors(efm_net *net, const uint64_t *supports, int64_t n, int64_t *flux, int8_t *status)

@@ -180,6 +180,10 @@ cudaError_t launch_sort_results(const uint64_t *res, int64_t n, int W, uint32_t 
                                 uint64_t *out, int64_t n_keep, cudaStream_t s);
 int expand_grid(const NetView &nv, int sm_count);
 cudaError_t launch_iota(uint32_t *perm, int64_t n, cudaStream_t s);
+cudaError_t launch_seedset(const NetView &nv, const LevelArgs &a, const int32_t *cols, int n_cols, cudaStream_t s);
+cudaError_t launch_step_count(const NetView &nv, unsigned *r, cudaStream_t s);
+cudaError_t launch_depthy(const NetView &nv, int L, unsigned r, unsigned long long n_paths, unsigned long long *dep_out,
+                          unsigned long long *dep_in, int sm_count, cudaStream_t s);
 cudaError_t launch_flux(const NetView &nv, const uint64_t *sup, int64_t n, int64_t *flux, int8_t *status, int sm_count,
                         cudaStream_t s);
 cudaError_t launch_walks(const NetView &nv, const LevelArgs &a, int target, uint64_t seed, int64_t n_walks, int sm_count,

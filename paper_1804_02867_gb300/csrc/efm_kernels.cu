@@ -567,6 +567,54 @@ __global__ void __launch_bounds__(kExpandWarps * 32) walk_kernel(NetView nv, Lev
     }
 }
 
+// Seed set R_in (Prop. 1): one state with flux 1 on each column of R_in,
+// EF = the sum of their S_int columns, normalised.  One warp.
+template <int EPL>
+__global__ void __launch_bounds__(32) seedset_kernel(NetView nv, LevelArgs a, const int32_t *cols, int n_cols)
+{
+    __shared__ uint64_t U[kMaxW];
+    const int lane = threadIdx.x & 31;
+    const int W = nv.W, Mpad = nv.Mpad;
+    const int32_t *dcol = reinterpret_cast<const int32_t *>(nv.blob + nv.o_dcols);
+    for (int x = lane; x < W; x += 32) U[x] = 0ull;
+    __syncwarp();
+    int64_t t64[EPL];
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) t64[e] = 0;
+    for (int i = 0; i < n_cols; ++i) {
+        const int k = cols[i];
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) t64[e] += dcol[(size_t)k * Mpad + lane + 32 * e];
+        if (lane == 0) U[k >> 6] |= 1ull << (k & 63);
+        __syncwarp();
+    }
+    int32_t t[EPL];
+    bool zero, ovf;
+    walk_normalise<EPL>(t64, t, zero, ovf);
+    if (lane == 0) atomicAdd(&a.ctr[C_SEEDS], 1ull);
+    if (ovf) {
+        if (lane == 0) atomicAdd(&a.ctr[C_OVF], 1ull);
+        return;
+    }
+    if (zero) {
+        if (lane == 0) {
+            atomicAdd(&a.ctr[C_BAL], 1ull);
+            insert_support(a, W, U, cols[0]);
+        }
+        return;
+    }
+    const uint32_t key = pivot_key<EPL>(nv.blob, nv, t, lane);
+    if (a.child.cap < 1) return;
+    for (int x = lane; x < W; x += 32) a.child.U[x] = U[x];
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) a.child.B[lane + 32 * e] = t[e];
+    if (lane == 0) {
+        a.child.meta[0] = pack_meta(key, n_cols);
+        atomicAdd(&a.ctr[C_NEXT], 1ull);
+        atomicAdd(&a.ctr[C_DEGSUM], (unsigned long long)(key >> 16));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // a1-a6: one level of expansion.
 //
@@ -1872,6 +1920,21 @@ cudaError_t launch_walks(const NetView &nv, const LevelArgs &a, int target, uint
         break;
         EFM_WALK(1) EFM_WALK(2) EFM_WALK(4) EFM_WALK(8) EFM_WALK(16) EFM_WALK(28) EFM_WALK(32)
 #undef EFM_WALK
+    default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seedset(const NetView &nv, const LevelArgs &a, const int32_t *cols, int n_cols, cudaStream_t s)
+{
+    switch (nv.EPL) {
+#define EFM_SEEDSET(E)                                                \
+    case E:                                                           \
+        seedset_kernel<E><<<1, 32, 0, s>>>(nv, a, cols, n_cols);      \
+        break;
+        EFM_SEEDSET(1) EFM_SEEDSET(2) EFM_SEEDSET(4) EFM_SEEDSET(8) EFM_SEEDSET(16) EFM_SEEDSET(28) EFM_SEEDSET(32)
+#undef EFM_SEEDSET
     default:
         return cudaErrorInvalidValue;
     }

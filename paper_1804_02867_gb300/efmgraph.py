@@ -24,7 +24,7 @@ EXPORTS = ("efm_load_network", "efm_network_shape", "efm_column_map", "efm_find_
            "efm_sort_supports_noalloc", "efm_find_pathways_batch", "efm_batch_tuning", "efm_model_create",
            "efm_model_params", "efm_model_add_rows", "efm_model_rows", "efm_model_clear_rows", "efm_model_forward",
            "efm_model_gradient", "efm_model_train", "efm_model_trace", "efm_model_free", "efm_sample_pathways",
-           "efm_flux_vectors")
+           "efm_flux_vectors", "efm_find_pathways_from", "efm_dependent_reactions")
 EFM_NOALLOC_MAX_ROWS = 1 << 20
 EFM_MLP_FEATURES, EFM_MLP_HIDDEN = 128, 256
 EFM_MLP_PARAMS = 256 * 128 + 256 + 1
@@ -112,6 +112,12 @@ def load_library(path: str | None = None):
                  "efm_model_clear_rows", "efm_model_forward", "efm_model_gradient", "efm_model_train",
                  "efm_model_trace"):
         getattr(lib, name).restype = ctypes.c_int
+    lib.efm_dependent_reactions.argtypes = [ctypes.c_void_p, ctypes.c_int32, _P(ctypes.c_uint64), _P(ctypes.c_uint64),
+                                            _P(ctypes.c_int32), _P(ctypes.c_double)]
+    lib.efm_dependent_reactions.restype = ctypes.c_int
+    lib.efm_find_pathways_from.argtypes = [ctypes.c_void_p, _P(ctypes.c_int32), ctypes.c_int32, _P(efm_limits),
+                                           _P(ctypes.c_void_p)]
+    lib.efm_find_pathways_from.restype = ctypes.c_int
     lib.efm_flux_vectors.argtypes = [ctypes.c_void_p, _P(ctypes.c_uint64), ctypes.c_int64, _P(ctypes.c_int64),
                                      _P(ctypes.c_int8)]
     lib.efm_flux_vectors.restype = ctypes.c_int
@@ -193,6 +199,48 @@ def efm_find_pathways(net, targets, max_len, max_secondary, max_results=0, max_f
     if rc < 0:
         raise EfmError(rc, "efm_find_pathways")
     return job.value, rc
+
+
+def efm_find_pathways_from(net, columns, max_len, max_secondary, max_results=0, max_frontier=0, first_k=0):
+    """Traversal from a seed set of split columns.  Returns (job, flags)."""
+    cols, pc = _arr(columns, np.int32, ctypes.c_int32)
+    lim = efm_limits(int(max_len), int(max_secondary), int(max_results), int(max_frontier), int(first_k), EFM_PLAIN)
+    job = ctypes.c_void_p()
+    rc = load_library().efm_find_pathways_from(net, pc, len(cols), ctypes.byref(lim), ctypes.byref(job))
+    if rc < 0:
+        raise EfmError(rc, "efm_find_pathways_from")
+    return job.value, rc
+
+
+def enumerate_from(network, columns, max_len, max_secondary, max_results=0, max_frontier=0, first_k=0):
+    """efm_find_pathways_from + fetch: (supports, counters)."""
+    job, _ = efm_find_pathways_from(network.handle, columns, max_len, max_secondary, max_results, max_frontier,
+                                    first_k)
+    try:
+        sup, ctr, _ = efm_fetch_results(job, 0)
+        return sup, ctr
+    finally:
+        efm_free_job(job)
+
+
+def efm_dependent_reactions(network, depth):
+    """DEPTHy: (dep_out, dep_in) bool[M_int, N] flux-dependent column tags,
+    r (most steps out of a metabolite), kernel ms."""
+    M, W, N = network.n_internal, network.words, network.n_columns
+    o = np.zeros((max(M, 1), W), dtype=np.uint64)
+    i = np.zeros((max(M, 1), W), dtype=np.uint64)
+    r = ctypes.c_int32()
+    ms = ctypes.c_double()
+    rc = load_library().efm_dependent_reactions(network.handle, int(depth), o.ctypes.data_as(_P(ctypes.c_uint64)),
+                                                i.ctypes.data_as(_P(ctypes.c_uint64)), ctypes.byref(r),
+                                                ctypes.byref(ms))
+    if rc != 0:
+        raise EfmError(rc, "efm_dependent_reactions")
+
+    def bits(a):
+        b = np.unpackbits(a[:M].view(np.uint8), axis=1, bitorder="little").astype(bool)
+        return b[:, :N]
+    return bits(o), bits(i), r.value, ms.value
 
 
 EFM_FLUX_COLUMNS = 64
