@@ -868,10 +868,10 @@ __device__ void expand_range(const NetView &nv, const LevelArgs &a, const uint32
         if (todo) {
             // superset pruning (counted on a truncated level too): the new
             // column k completes a result accepted at an earlier level (the
-            // results containing k, bucket loads issued eight at a time)
+            // results containing k, bucket loads issued four at a time)
             const int64_t b1 = in_u ? 0 : a.bptr[k];
             const int64_t n = in_u ? 0 : a.bptr[k + 1] - b1;
-            constexpr int PU = 8;
+            constexpr int PU = 4;
             bool pr = false;
             uint64_t u0 = 0, u1 = 0;
             if (W <= 2) {
