@@ -758,28 +758,6 @@ __device__ void expand_range(const NetView &nv, const LevelArgs &a, const uint32
             const int k = (int)(info & 0xFFFu);
             const bool in_u = (info >> 12) & 1u;
             const uint64_t *pu = a.par.U + (size_t)bpar[b] * W;
-            // superset pruning: lanes take the results containing k in parallel
-            const int64_t b1 = in_u ? 0 : a.bptr[k];
-            const int64_t n = in_u ? 0 : a.bptr[k + 1] - b1;
-            bool pr = false;
-            for (int64_t i0 = 0; i0 < n && !pr; i0 += 32) {
-                const int64_t i = i0 + lane;
-                bool sub = false;
-                if (i < n) {
-                    if (W > 2) {
-                        sub = result_inside_wide(a, pu, k, b1 + i);
-                    } else {
-                        const uint64_t *E = a.bres + (size_t)(b1 + i) * W;
-                        sub = true;
-                        for (int w = 0; w < W && sub; ++w) sub = (__ldg(E + w) & ~child_word(pu, w, k)) == 0;
-                    }
-                }
-                pr = __any_sync(FULL, sub);
-            }
-            if (pr) {
-                if (lane == 0) ++n_pruned;
-                continue;
-            }
             if (full) continue;
             uint64_t pos = bpos[b];
             const uint32_t tag = btag[b];
@@ -865,40 +843,6 @@ __device__ void expand_range(const NetView &nv, const LevelArgs &a, const uint32
         const bool in_u = (info >> 12) & 1u;
         const uint64_t *pu = a.par.U + (size_t)(mine ? bpar[lane] : 0u) * W;
         bool todo = mine;
-        if (todo) {
-            // superset pruning (counted on a truncated level too): the new
-            // column k completes a result accepted at an earlier level (the
-            // results containing k, bucket loads issued four at a time)
-            const int64_t b1 = in_u ? 0 : a.bptr[k];
-            const int64_t n = in_u ? 0 : a.bptr[k + 1] - b1;
-            constexpr int PU = 4;
-            bool pr = false;
-            uint64_t u0 = 0, u1 = 0;
-            if (W <= 2) {
-                u0 = child_word(pu, 0, k);
-                u1 = W == 2 ? child_word(pu, 1, k) : 0ull;
-            }
-            for (int64_t i0 = 0; i0 < n && !pr; i0 += PU) {
-                if (W <= 2) {
-                    uint64_t e0[PU], e1[PU];
-#pragma unroll
-                    for (int u = 0; u < PU; ++u) {
-                        const int64_t i = i0 + u;
-                        const uint64_t *E = a.bres + (size_t)(b1 + i) * W;
-                        e0[u] = i < n ? __ldg(E) : ~0ull;
-                        e1[u] = (i < n && W == 2) ? __ldg(E + 1) : 0ull;
-                    }
-#pragma unroll
-                    for (int u = 0; u < PU; ++u) pr = pr || (((e0[u] & ~u0) | (e1[u] & ~u1)) == 0);
-                } else {
-                    for (int64_t i = i0; i < i0 + PU && i < n && !pr; ++i) pr = result_inside_wide(a, pu, k, b1 + i);
-                }
-            }
-            if (pr) {
-                ++n_pruned;
-                todo = false;
-            }
-        }
         if (full) todo = false;
         const uint64_t row_i = (uint64_t)lane * BS::ROW;
         uint64_t pos = mine ? bpos[lane] : 0ull;
@@ -1160,13 +1104,34 @@ __device__ void expand_range(const NetView &nv, const LevelArgs &a, const uint32
                 }
             }
             const bool bal = ok && !nz;
-            const bool norm = ok && nz && !ovf;
+            const bool grown = ok && nz && !ovf;
             if (ovf && gl == 0) ++n_ovf;
             if (bal && gl == 0) {
                 ++n_bal;  // all metabolites stable: to the arbiter
                 if (insert_support(a, W, pu, k) < INS_DUP) fatal = true;
             }
             fatal = group_or<G>(fatal ? 1u : 0u) != 0;
+            // superset pruning (counted on a truncated level too): the new
+            // column k completes a result accepted at an earlier level.  The
+            // G lanes of the group split the results containing k.
+            bool pr = false;
+            if (grown && !in_u) {
+                const int64_t b1 = a.bptr[k];
+                const int64_t n = a.bptr[k + 1] - b1;
+                if (W <= 2) {
+                    const uint64_t u0 = child_word(pu, 0, k), u1 = W == 2 ? child_word(pu, 1, k) : 0ull;
+                    for (int64_t i = gl; i < n && !pr; i += G) {
+                        const uint64_t *E = a.bres + (size_t)(b1 + i) * W;
+                        const uint64_t e0 = __ldg(E), e1 = W == 2 ? __ldg(E + 1) : 0ull;
+                        pr = ((e0 & ~u0) | (e1 & ~u1)) == 0;
+                    }
+                } else {
+                    for (int64_t i = gl; i < n && !pr; i += G) pr = result_inside_wide(a, pu, k, b1 + i);
+                }
+            }
+            pr = group_or<G>(pr ? 1u : 0u) != 0;
+            if (pr && gl == 0) ++n_pruned;
+            const bool norm = grown && !pr;
 
             // --- pivot key and fingerprint, then append to the batch ---
             uint32_t key = 0xFFFFFFFFu, hlo = 0, hhi = 0;
