@@ -88,3 +88,25 @@ def test_first_k_rejects_cap(efm):
     with efm.Network(net) as nw:
         with pytest.raises(efm.EfmError):
             efm.efm_find_pathways(nw.handle, [-1], 8, 1, max_results=5, first_k=3)
+
+
+def test_genome_first_1000_at_full_size(oracle_lib, efm):
+    """At the learned-proposal workload's size (K = 1000, max_len 40, frontier
+    budget 2^22): the answer is certified, has 1000 distinct rows in the
+    output order, its first 80 rows are the oracle's first 80 (the smallest
+    80 of any first-K answer with K >= 80), and every row has nullity 1
+    (the oracle's exact rank)."""
+    from oracle import bruteforce
+
+    net = synth.genome()
+    S_int, _, _ = bruteforce.split(net)
+    with efm.Network(net) as nw:
+        for t in (883, 924):
+            (sup, ctr), = gpu_first_k(efm, nw, [t], 1000, 40, 4, max_frontier=1 << 22)
+            assert not ctr["status"] & 1 and len(sup) == 1000
+            want, _ = oracle_lib.first_k(net, t, 80, 40, 4)
+            assert np.array_equal(sup[:80], want)
+            lists = oracle_lib.supports_to_lists(sup)
+            assert lists == sorted(lists, key=lambda c: (len(c), c)) and len(set(lists)) == len(lists)
+            for cols in lists:
+                assert len(cols) - oracle_lib.rank(S_int[:, list(cols)]) == 1
