@@ -542,6 +542,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
     acc.res_cap = w.res_cap;
     acc.rcols = nv.W > 2 ? (uint16_t *)w.rcols.p : nullptr;
     acc.ctr = ctr;
+    acc.cand_cap = w.cand_cap;
     auto read_ctr = [&]() -> int {
         if (cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
@@ -556,17 +557,14 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
         return e;
     };
     const bool fk = lim.first_k > 0;
+    std::vector<uint64_t> window(fk ? (size_t)kResultWindow * nv.W : 0);
     TopK top;
     top.K = lim.first_k;
     top.W = nv.W;
+    CK(launch_accept_new(nv, acc, net->sm_count, s));
+    out.kernel_launches += 2;
     int rc = read_ctr();
     if (rc) return rc;
-    acc.cand_begin = 0;
-    acc.cand_end = (int64_t)h[C_CAND_N];
-    CK(launch_accept(nv, acc, s));
-    out.kernel_launches += acc.cand_end > acc.cand_begin ? 1 : 0;
-    if ((rc = read_ctr())) return rc;
-    int64_t cand_done = (int64_t)h[C_CAND_N];
     int64_t res_n = (int64_t)std::min<unsigned long long>(h[C_RES_N], (unsigned long long)w.res_cap);
     if (fk && res_n > 0) {
         std::vector<uint64_t> fresh((size_t)res_n * nv.W);
@@ -681,11 +679,19 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
             CK(cudaEventRecord(w.ev[2], s));
             CK(launch_expand(nv, a, grid, s));
             CK(cudaEventRecord(w.ev[3], s));
+            // minimality test of the new candidates, range taken on the device
+            CK(launch_accept_new(nv, acc, net->sm_count, s));
+            // one round trip per chunk: the counters and, in a first-K search, a
+            // window of the results that follow the ones already seen
+            const int64_t win = fk ? std::min<int64_t>(kResultWindow, w.res_cap - res_n) : 0;
+            if (win > 0)
+                CK(cudaMemcpyAsync(window.data(), (const uint64_t *)w.res.p + (size_t)res_n * nv.W,
+                                   (size_t)win * nv.W * 8, cudaMemcpyDeviceToHost, s));
             if ((rc = read_ctr())) return rc;
             CK(cudaEventElapsedTime(&ms, w.ev[2], w.ev[3]));
             out.expand_ms += ms;
             out.expand_launches += 1;
-            out.kernel_launches += 1;
+            out.kernel_launches += 3;
             {
                 const double state_bytes = 8.0 * nv.W + 4.0 * nv.M + 4.0;
                 const uint64_t next_now = std::min<unsigned long long>(h[C_NEXT], (unsigned long long)w.F_cap);
@@ -699,22 +705,21 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
                 exp_before = h[C_EXP];
                 next_before = next_now;
             }
-            acc.cand_begin = cand_done;
-            acc.cand_end = (int64_t)h[C_CAND_N];
-            CK(launch_accept(nv, acc, s));
-            out.kernel_launches += acc.cand_end > acc.cand_begin ? 1 : 0;
-            if ((rc = read_ctr())) return rc;
-            cand_done = (int64_t)h[C_CAND_N];
             const int64_t res_now = (int64_t)std::min<unsigned long long>(h[C_RES_N], (unsigned long long)w.res_cap);
             if (fk && res_now > res_n) {
-                // fetch the new results and tighten the bound
-                std::vector<uint64_t> fresh((size_t)(res_now - res_n) * nv.W);
-                CK(cudaMemcpyAsync(fresh.data(), (const uint64_t *)w.res.p + (size_t)res_n * nv.W,
-                                   fresh.size() * 8, cudaMemcpyDeviceToHost, s));
-                CK(cudaStreamSynchronize(s));
+                // the new results (beyond the window: fetched now) tighten the bound
+                const uint64_t *fresh = window.data();
+                std::vector<uint64_t> more;
+                if (res_now - res_n > win) {
+                    more.resize((size_t)(res_now - res_n) * nv.W);
+                    CK(cudaMemcpyAsync(more.data(), (const uint64_t *)w.res.p + (size_t)res_n * nv.W,
+                                       more.size() * 8, cudaMemcpyDeviceToHost, s));
+                    CK(cudaStreamSynchronize(s));
+                    fresh = more.data();
+                }
                 const int pc_before = top.pc;
                 const std::vector<uint64_t> kth_before = top.kth;
-                top.add(fresh.data(), res_now - res_n);
+                top.add(fresh, res_now - res_n);
                 if (top.pc > 0 && (top.pc != pc_before || top.kth != kth_before))
                     CK(cudaMemcpyAsync(w.fkb.p, top.kth.data(), (size_t)nv.W * 8, cudaMemcpyHostToDevice, s));
             }

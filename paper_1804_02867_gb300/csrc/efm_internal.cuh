@@ -19,6 +19,7 @@ constexpr int kNumPrimes = 24;
 constexpr int kStageLimitBytes = 72 * 1024;  // static network staged in smem up to this size
 constexpr int64_t kFirstKChunkMin = 8192;     // first-K search: fewest parents per expansion launch
 constexpr int64_t kFirstKChunks = 32;         // first-K search: launches per level, at most
+constexpr int64_t kResultWindow = 256;        // first-K search: new results fetched with the counters
 
 // device error bits (ctr[C_ERR])
 enum : unsigned { ERR_TIMEOUT = 1u, ERR_CAND_CAP = 2u, ERR_RES_CAP = 4u, ERR_TABLE_FULL = 8u,
@@ -34,6 +35,7 @@ enum {
     C_ERR,        // ERR_* bits
     C_OUT_N = 20, // batched traversal: rows written to the job's output
     C_DONE,       // batched traversal: job finished
+    C_ACC_BEGIN,  // first candidate the next device-range minimality launch judges
     C_DIAG = 24,  // first bounds/watchdog record: code, value, limit, level
     C_COUNT = 32
 };
@@ -99,7 +101,9 @@ constexpr int kRcolStride = 65;  // column count + up to 64 columns per result
 
 struct AcceptArgs {
     const uint64_t *cand;
-    int64_t cand_begin, cand_end;
+    int64_t cand_begin, cand_end;  // ignored when dev_range: [ctr[C_ACC_BEGIN], ctr[C_CAND_N]) instead
+    int dev_range;
+    int64_t cand_cap;
     uint64_t *res;
     uint16_t *rcols;            // written on accept when non-null
     int64_t res_cap;
@@ -174,6 +178,9 @@ size_t mlp_train_smem();
 cudaError_t launch_seed(const NetView &nv, const LevelArgs &a, int target, cudaStream_t s);
 cudaError_t launch_expand(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_accept(const NetView &nv, const AcceptArgs &a, cudaStream_t s);
+// minimality test of the candidates appended since the last such launch (range read on the
+// device, so no host round trip is needed between expansion and test); then advance the range
+cudaError_t launch_accept_new(const NetView &nv, const AcceptArgs &a, int sm_count, cudaStream_t s);
 cudaError_t launch_buckets(const NetView &nv, const uint64_t *res, int64_t n_res, int32_t *bcnt, int32_t *bptr,
                            int32_t *bfill, uint64_t *bres, cudaStream_t s);  // W > 2: bres holds int32 ids
 cudaError_t launch_sort_results(const uint64_t *res, int64_t n, int W, uint32_t *idx, int64_t n_pow2,

@@ -1378,8 +1378,20 @@ __global__ void __launch_bounds__(kAcceptWarps * 32) accept_kernel(NetView nv, A
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const int wid = threadIdx.x >> 5;
+    if (a.dev_range) {
+        // the expansion launches before this one have finished: the range is stable
+        a.cand_begin = (int64_t)a.ctr[C_ACC_BEGIN];
+        const int64_t n = (int64_t)a.ctr[C_CAND_N];
+        a.cand_end = n < a.cand_cap ? n : a.cand_cap;
+    }
     accept_range(nv, a, smem + wid * kAcceptWarpWords, (int64_t)blockIdx.x * kAcceptWarps + wid,
                  (int64_t)gridDim.x * kAcceptWarps);
+}
+
+__global__ void accept_advance_kernel(unsigned long long *ctr, int64_t cand_cap)
+{
+    const unsigned long long n = ctr[C_CAND_N];
+    ctr[C_ACC_BEGIN] = n < (unsigned long long)cand_cap ? n : (unsigned long long)cand_cap;
 }
 
 // ---------------------------------------------------------------------------
@@ -1834,6 +1846,17 @@ int expand_grid(const NetView &nv, int sm_count)
     EFM_GROUP_DISPATCH(nv.EPL, CALL_GRID)
 #undef CALL_GRID
     return sm_count;
+}
+
+cudaError_t launch_accept_new(const NetView &nv, const AcceptArgs &a, int sm_count, cudaStream_t s)
+{
+    const size_t sm = (size_t)kAcceptWarps * kAcceptWarpWords * 4;
+    cudaFuncSetAttribute(accept_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    AcceptArgs d = a;
+    d.dev_range = 1;
+    accept_kernel<<<sm_count * 2, kAcceptWarps * 32, sm, s>>>(nv, d);
+    accept_advance_kernel<<<1, 1, 0, s>>>(a.ctr, a.cand_cap);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_accept(const NetView &nv, const AcceptArgs &a, cudaStream_t s)
