@@ -712,7 +712,7 @@ __device__ __forceinline__ bool child_after(const uint64_t *pu, int k, const uin
 template <int G, int CPL>
 struct BatchShape {
     static constexpr int NCH = G * CPL;          // 16-byte chunks per row
-    static constexpr int NB = NCH <= 16 ? 16 : (NCH <= 32 ? 8 : 4);
+    static constexpr int NB = NCH <= 16 ? 16 : (NCH <= 32 ? 8 : 2);
     static constexpr int ROW = NCH + 1;          // padded row (int4 units): conflict-free per-lane access
     static constexpr int BYTES = NB * ROW * 16 + NB * 32;
 };
@@ -1026,6 +1026,9 @@ __device__ void expand_range(const NetView &nv, const LevelArgs &a, const uint32
                 }
             }
             if (ok && gl == 0) ++n_exp;
+            // no group of the warp has a child this round (branches ruled out
+            // by the twin, length or first-K rules): skip the rest of it
+            if (!__any_sync(FULL, ok)) continue;
 
             // --- AND update (Eq. 3 / Eq. 4 in integers), group-parallel ---
             int32_t t32[EPL];
