@@ -971,10 +971,11 @@ __device__ void expand_range(const NetView &nv, const LevelArgs &a, const uint32
             if (lane == 0) record_diag(a.ctr, ERR_BOUNDS, 3, T, 32 * nv.N, a.level);
             fatal = true;
         }
-        for (int base = 0; base < T; base += NG) {
+        for (int base = 0; base < T; base += 32) {
             if (__any_sync(FULL, fatal)) break;
-            const int c = base + gi;  // this group's item
-            int j = 0;                // largest j with pre_j <= c
+            // --- branch selection: one (parent, branch) item per lane ---
+            const int c = base + lane;
+            int j = 0;  // largest j with pre_j <= c
 #pragma unroll
             for (int step = 16; step > 0; step >>= 1) {
                 const int v = __shfl_sync(FULL, prej, j + step);
@@ -982,205 +983,219 @@ __device__ void expand_range(const NetView &nv, const LevelArgs &a, const uint32
             }
             const uint32_t pm = __shfl_sync(FULL, mj, j);
             const int q = c - __shfl_sync(FULL, prej, j);
-
-            // --- branch selection (group-uniform) ---
-            bool ok = c < T;
-            int k = 0, pc = 0;
-            bool in_u = false;
-            int32_t A = 0, C = 0;
-            const int64_t p = __shfl_sync(FULL, pid, j);
-            const int32_t *prow = a.par.B + (size_t)p * Mpad;
-            const uint64_t *pu = a.par.U + (size_t)p * W;
-            if (ok) {
+            const int64_t pl_ = __shfl_sync(FULL, pid, j);
+            bool okl = c < T;
+            int kl = 0, pcl = 0;
+            bool inl = false;
+            int32_t Al = 0, Cl = 0;
+            if (okl) {
+                const int32_t *prow_l = a.par.B + (size_t)pl_ * Mpad;
+                const uint64_t *pu_l = a.par.U + (size_t)pl_ * W;
                 const int piv = (int)(pm & 0x3FFu);
-                pc = (int)((pm >> 23) & 0x7Fu);
-                const int32_t bi = piv < nv.M ? prow[piv] : 0;
+                pcl = (int)((pm >> 23) & 0x7Fu);
+                const int32_t bi = piv < nv.M ? prow_l[piv] : 0;
                 const bool fwd = bi > 0;  // forward flow: consume the surplus
                 const uint32_t abi = (uint32_t)(bi < 0 ? -bi : bi);
                 const int lptr = (fwd ? nv.o_consptr : nv.o_prodptr) + (piv < nv.M ? piv : 0);
                 const int lb = (int)bl[lptr];
                 const int le = (int)bl[lptr + 1];
                 if (piv >= nv.M || bi == 0 || lb + q >= le) {
-                    if (gl == 0) record_diag(a.ctr, ERR_BOUNDS, 1 + (piv >= nv.M ? 10 : 0) + (bi == 0 ? 100 : 0),
-                                             (long long)q, (long long)(le - lb), a.level);
+                    record_diag(a.ctr, ERR_BOUNDS, 1 + (piv >= nv.M ? 10 : 0) + (bi == 0 ? 100 : 0), (long long)q,
+                                (long long)(le - lb), a.level);
                     fatal = true;
-                    ok = false;
+                    okl = false;
                 } else {
                     const uint32_t br = bl[(fwd ? nv.o_consent : nv.o_prodent) + lb + q];
-                    k = ent_index(br);
+                    kl = ent_index(br);
                     const uint32_t sik = (uint32_t)ent_coef(br);  // |S_ik|
-                    const int tw = (int)bl[nv.o_twin + k];
-                    in_u = bit_of(pu, k);
-                    const int sec = a.level - pc;
-                    ok = !(tw >= 0 && bit_of(pu, tw)) && (in_u ? sec + 1 <= a.max_sec : pc + 1 <= a.max_len);
-                    if (ok && a.fk_pc > 0) {
+                    const int tw = (int)bl[nv.o_twin + kl];
+                    inl = bit_of(pu_l, kl);
+                    const int sec = a.level - pcl;
+                    okl = !(tw >= 0 && bit_of(pu_l, tw)) && (inl ? sec + 1 <= a.max_sec : pcl + 1 <= a.max_len);
+                    if (okl && a.fk_pc > 0) {
                         // first-K branch and bound: the child's descendants keep
                         // its support or grow it, so a child past the K-th
                         // result found so far cannot yield one of the K smallest
-                        const int pc2 = pc + (in_u ? 0 : 1);
-                        ok = pc2 < a.fk_pc || (pc2 == a.fk_pc && !child_after(pu, k, a.fk_sup, W));
+                        const int pc2 = pcl + (inl ? 0 : 1);
+                        okl = pc2 < a.fk_pc || (pc2 == a.fk_pc && !child_after(pu_l, kl, a.fk_sup, W));
                     }
                     const uint32_t g0 = (abi == 1u || sik == 1u) ? 1u : gcd32(abi, sik);
-                    A = (int32_t)(sik / g0);
-                    C = (int32_t)(abi / g0);
+                    Al = (int32_t)(sik / g0);
+                    Cl = (int32_t)(abi / g0);
                 }
             }
-            if (ok && gl == 0) ++n_exp;
-            // no group of the warp has a child this round (branches ruled out
-            // by the twin, length or first-K rules): skip the rest of it
-            if (!__any_sync(FULL, ok)) continue;
+            if (okl) ++n_exp;
+            // the groups take the valid items of this pass NG at a time, in order
+            unsigned vmask = __ballot_sync(FULL, okl);
+            while (vmask) {
+                if (__any_sync(FULL, fatal)) break;
+                const int src = gi < __popc(vmask) ? (int)__fns(vmask, 0, gi + 1) : -1;
+#pragma unroll
+                for (int t = 0; t < NG; ++t) vmask &= vmask - 1;
+                const int sl = src < 0 ? 0 : src;
+                const bool ok = src >= 0;
+                const int k = __shfl_sync(FULL, kl, sl);
+                const int pc = __shfl_sync(FULL, pcl, sl);
+                const bool in_u = __shfl_sync(FULL, inl ? 1 : 0, sl) != 0;
+                const int32_t A = __shfl_sync(FULL, Al, sl);
+                const int32_t C = __shfl_sync(FULL, Cl, sl);
+                const int64_t p = __shfl_sync(FULL, pl_, sl);
+                const int32_t *prow = a.par.B + (size_t)p * Mpad;
+                const uint64_t *pu = a.par.U + (size_t)p * W;
 
-            // --- AND update (Eq. 3 / Eq. 4 in integers), group-parallel ---
-            int32_t t32[EPL];
-            uint32_t fl = 0;  // bit0 nonzero, bit1 some |t| == 1, bit2 some t outside int32
-            const int4 *prow4 = reinterpret_cast<const int4 *>(prow);
-            const int4 *col4 = dcol + (size_t)k * (Mpad >> 2);
-            if (ok) {
-#pragma unroll
-                for (int i = 0; i < CPL; ++i) {
-                    const int4 v = prow4[gl + G * i];
-                    const int4 w = col4[gl + G * i];
-                    const int32_t pv[4] = {v.x, v.y, v.z, v.w}, cv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) {
-                        const int64_t tt = (int64_t)A * pv[jj] + (int64_t)C * cv[jj];
-                        const int32_t lo = (int32_t)tt;
-                        const bool fits = tt == (int64_t)lo && lo != INT32_MIN;
-                        t32[4 * i + jj] = lo;
-                        fl |= (tt != 0 ? 1u : 0u) | ((lo == 1 || lo == -1) ? 2u : 0u) | (fits ? 0u : 4u);
+                // --- AND update (Eq. 3 / Eq. 4 in integers), group-parallel ---
+                int32_t t32[EPL];
+                uint32_t fl = 0;  // bit0 nonzero, bit1 some |t| == 1, bit2 some t outside int32
+                const int4 *prow4 = reinterpret_cast<const int4 *>(prow);
+                const int4 *col4 = dcol + (size_t)k * (Mpad >> 2);
+                if (ok) {
+    #pragma unroll
+                    for (int i = 0; i < CPL; ++i) {
+                        const int4 v = prow4[gl + G * i];
+                        const int4 w = col4[gl + G * i];
+                        const int32_t pv[4] = {v.x, v.y, v.z, v.w}, cv[4] = {w.x, w.y, w.z, w.w};
+    #pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) {
+                            const int64_t tt = (int64_t)A * pv[jj] + (int64_t)C * cv[jj];
+                            const int32_t lo = (int32_t)tt;
+                            const bool fits = tt == (int64_t)lo && lo != INT32_MIN;
+                            t32[4 * i + jj] = lo;
+                            fl |= (tt != 0 ? 1u : 0u) | ((lo == 1 || lo == -1) ? 2u : 0u) | (fits ? 0u : 4u);
+                        }
                     }
+                } else {
+    #pragma unroll
+                    for (int e = 0; e < EPL; ++e) t32[e] = 0;
                 }
-            } else {
-#pragma unroll
-                for (int e = 0; e < EPL; ++e) t32[e] = 0;
-            }
-            fl = group_or<G>(fl);
-            const bool nz = fl & 1u;
-            // slow path: the gcd is needed (no unit entry), or an entry is
-            // outside int32 (then the raw entries are recomputed in 64 bits)
-            const bool slow = ok && nz && ((fl & 6u) != 2u);
-            const bool big = (fl & 4u) != 0u;
-            bool ovf = false;
-            if (__any_sync(FULL, slow)) {
-                uint64_t gg = 0, amax = 0;
-                if (slow && !big) {
-#pragma unroll
-                    for (int e = 0; e < EPL; ++e) {
-                        const uint32_t at = (uint32_t)(t32[e] < 0 ? -t32[e] : t32[e]);
-                        if (at != 0) gg = gg == 0 ? at : gcd32((uint32_t)gg, at);
+                fl = group_or<G>(fl);
+                const bool nz = fl & 1u;
+                // slow path: the gcd is needed (no unit entry), or an entry is
+                // outside int32 (then the raw entries are recomputed in 64 bits)
+                const bool slow = ok && nz && ((fl & 6u) != 2u);
+                const bool big = (fl & 4u) != 0u;
+                bool ovf = false;
+                if (__any_sync(FULL, slow)) {
+                    uint64_t gg = 0, amax = 0;
+                    if (slow && !big) {
+    #pragma unroll
+                        for (int e = 0; e < EPL; ++e) {
+                            const uint32_t at = (uint32_t)(t32[e] < 0 ? -t32[e] : t32[e]);
+                            if (at != 0) gg = gg == 0 ? at : gcd32((uint32_t)gg, at);
+                        }
+                    } else if (slow) {
+                        const GcdMax gm = raw_gcd_max(prow4, col4, gl, G, CPL, A, C);
+                        gg = gm.g;
+                        amax = gm.m;
                     }
-                } else if (slow) {
-                    const GcdMax gm = raw_gcd_max(prow4, col4, gl, G, CPL, A, C);
-                    gg = gm.g;
-                    amax = gm.m;
-                }
-#pragma unroll
-                for (int off = G / 2; off > 0; off >>= 1) {
-                    const uint64_t og = __shfl_xor_sync(FULL, gg, off);
-                    gg = og == 0 ? gg : (gg == 0 ? og : gcd64(gg, og));
-                    const uint64_t y = __shfl_xor_sync(FULL, amax, off);
-                    amax = y > amax ? y : amax;
-                }
-                if (slow) {
-                    ovf = big && amax / gg > 2147483647ull;
-                    if (!ovf && gg > 1) {
-                        const bool pow2 = (gg & (gg - 1)) == 0;
-                        const int sh = __ffsll((long long)gg) - 1;
-                        if (!big) {
-#pragma unroll
-                            for (int e = 0; e < EPL; ++e)
-                                t32[e] = t32[e] == 0 ? 0 : (pow2 ? (t32[e] >> sh) : t32[e] / (int32_t)gg);
-                        } else {
-#pragma unroll
-                            for (int i = 0; i < CPL; ++i) {
-                                const int4 v = prow4[gl + G * i];
-                                const int4 w = col4[gl + G * i];
-                                const int32_t pv[4] = {v.x, v.y, v.z, v.w}, cv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                                for (int jj = 0; jj < 4; ++jj) {
-                                    const int64_t tt = (int64_t)A * pv[jj] + (int64_t)C * cv[jj];
-                                    t32[4 * i + jj] = (int32_t)(tt / (int64_t)gg);
+    #pragma unroll
+                    for (int off = G / 2; off > 0; off >>= 1) {
+                        const uint64_t og = __shfl_xor_sync(FULL, gg, off);
+                        gg = og == 0 ? gg : (gg == 0 ? og : gcd64(gg, og));
+                        const uint64_t y = __shfl_xor_sync(FULL, amax, off);
+                        amax = y > amax ? y : amax;
+                    }
+                    if (slow) {
+                        ovf = big && amax / gg > 2147483647ull;
+                        if (!ovf && gg > 1) {
+                            const bool pow2 = (gg & (gg - 1)) == 0;
+                            const int sh = __ffsll((long long)gg) - 1;
+                            if (!big) {
+    #pragma unroll
+                                for (int e = 0; e < EPL; ++e)
+                                    t32[e] = t32[e] == 0 ? 0 : (pow2 ? (t32[e] >> sh) : t32[e] / (int32_t)gg);
+                            } else {
+    #pragma unroll
+                                for (int i = 0; i < CPL; ++i) {
+                                    const int4 v = prow4[gl + G * i];
+                                    const int4 w = col4[gl + G * i];
+                                    const int32_t pv[4] = {v.x, v.y, v.z, v.w}, cv[4] = {w.x, w.y, w.z, w.w};
+    #pragma unroll
+                                    for (int jj = 0; jj < 4; ++jj) {
+                                        const int64_t tt = (int64_t)A * pv[jj] + (int64_t)C * cv[jj];
+                                        t32[4 * i + jj] = (int32_t)(tt / (int64_t)gg);
+                                    }
                                 }
                             }
                         }
                     }
                 }
-            }
-            const bool bal = ok && !nz;
-            const bool grown = ok && nz && !ovf;
-            if (ovf && gl == 0) ++n_ovf;
-            if (bal && gl == 0) {
-                ++n_bal;  // all metabolites stable: to the arbiter
-                if (insert_support(a, W, pu, k) < INS_DUP) fatal = true;
-            }
-            fatal = group_or<G>(fatal ? 1u : 0u) != 0;
-            // superset pruning (counted on a truncated level too): the new
-            // column k completes a result accepted at an earlier level.  The
-            // G lanes of the group split the results containing k.
-            bool pr = false;
-            if (grown && !in_u) {
-                const int64_t b1 = a.bptr[k];
-                const int64_t n = a.bptr[k + 1] - b1;
-                if (W <= 2) {
-                    const uint64_t u0 = child_word(pu, 0, k), u1 = W == 2 ? child_word(pu, 1, k) : 0ull;
-                    for (int64_t i = gl; i < n && !pr; i += G) {
-                        const uint64_t *E = a.bres + (size_t)(b1 + i) * W;
-                        const uint64_t e0 = __ldg(E), e1 = W == 2 ? __ldg(E + 1) : 0ull;
-                        pr = ((e0 & ~u0) | (e1 & ~u1)) == 0;
-                    }
-                } else {
-                    for (int64_t i = gl; i < n && !pr; i += G) pr = result_inside_wide(a, pu, k, b1 + i);
+                const bool bal = ok && !nz;
+                const bool grown = ok && nz && !ovf;
+                if (ovf && gl == 0) ++n_ovf;
+                if (bal && gl == 0) {
+                    ++n_bal;  // all metabolites stable: to the arbiter
+                    if (insert_support(a, W, pu, k) < INS_DUP) fatal = true;
                 }
-            }
-            pr = group_or<G>(pr ? 1u : 0u) != 0;
-            if (pr && gl == 0) ++n_pruned;
-            const bool norm = grown && !pr;
-
-            // --- pivot key and fingerprint, then append to the batch ---
-            uint32_t key = 0xFFFFFFFFu, hlo = 0, hhi = 0;
-            if (norm) {
-#pragma unroll
-                for (int i = 0; i < CPL; ++i)
-#pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) {
-                        const int m = 4 * (gl + G * i) + jj;
-                        const int32_t v = t32[4 * i + jj];
-                        if (v != 0) {
-                            const uint32_t kk = bl[(v > 0 ? nv.o_keypos : nv.o_keyneg) + m];
-                            key = kk < key ? kk : key;
+                fatal = group_or<G>(fatal ? 1u : 0u) != 0;
+                // superset pruning (counted on a truncated level too): the new
+                // column k completes a result accepted at an earlier level.  The
+                // G lanes of the group split the results containing k.
+                bool pr = false;
+                if (grown && !in_u) {
+                    const int64_t b1 = a.bptr[k];
+                    const int64_t n = a.bptr[k + 1] - b1;
+                    if (W <= 2) {
+                        const uint64_t u0 = child_word(pu, 0, k), u1 = W == 2 ? child_word(pu, 1, k) : 0ull;
+                        for (int64_t i = gl; i < n && !pr; i += G) {
+                            const uint64_t *E = a.bres + (size_t)(b1 + i) * W;
+                            const uint64_t e0 = __ldg(E), e1 = W == 2 ? __ldg(E + 1) : 0ull;
+                            pr = ((e0 & ~u0) | (e1 & ~u1)) == 0;
                         }
-                        hash_entry((uint32_t)m, (uint32_t)v, hlo, hhi);
+                    } else {
+                        for (int64_t i = gl; i < n && !pr; i += G) pr = result_inside_wide(a, pu, k, b1 + i);
                     }
-                for (int w = gl; w < W; w += G) {
-                    const uint64_t x = mix64(child_word(pu, w, k) ^ (0x2545f4914f6cdd1dull * (uint64_t)(w + 1)));
-                    hlo += (uint32_t)x;
-                    hhi ^= (uint32_t)(x >> 32);
                 }
-            }
-            key = group_min<G>(key);
-            hlo = group_add<G>(hlo);
-            hhi = group_xor<G>(hhi);
-            const unsigned nm = __ballot_sync(FULL, norm && gl == 0);
-            if (norm) {
-                const int slot = nb + __popc(nm & ((1u << lead) - 1u));
-                int4 *r = brow + (size_t)slot * BS::ROW;
-#pragma unroll
-                for (int i = 0; i < CPL; ++i)
-                    r[gl + G * i] = make_int4(t32[4 * i + 0], t32[4 * i + 1], t32[4 * i + 2], t32[4 * i + 3]);
-                if (gl == 0) {
-                    uint64_t pos;
-                    uint32_t tag;
-                    slot_tag_pos(((uint64_t)hhi << 32) | hlo, a.slot_mask, pos, tag);
-                    prefetch_l2(&a.slots[pos]);
-                    bpos[slot] = pos;
-                    btag[slot] = tag;
-                    bkey[slot] = key;
-                    binfo[slot] = (uint32_t)k | (in_u ? 1u << 12 : 0u) | ((uint32_t)(pc + (in_u ? 0 : 1)) << 13);
-                    bpar[slot] = (uint32_t)p;
+                pr = group_or<G>(pr ? 1u : 0u) != 0;
+                if (pr && gl == 0) ++n_pruned;
+                const bool norm = grown && !pr;
+
+                // --- pivot key and fingerprint, then append to the batch ---
+                uint32_t key = 0xFFFFFFFFu, hlo = 0, hhi = 0;
+                if (norm) {
+    #pragma unroll
+                    for (int i = 0; i < CPL; ++i)
+    #pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) {
+                            const int m = 4 * (gl + G * i) + jj;
+                            const int32_t v = t32[4 * i + jj];
+                            if (v != 0) {
+                                const uint32_t kk = bl[(v > 0 ? nv.o_keypos : nv.o_keyneg) + m];
+                                key = kk < key ? kk : key;
+                            }
+                            hash_entry((uint32_t)m, (uint32_t)v, hlo, hhi);
+                        }
+                    for (int w = gl; w < W; w += G) {
+                        const uint64_t x = mix64(child_word(pu, w, k) ^ (0x2545f4914f6cdd1dull * (uint64_t)(w + 1)));
+                        hlo += (uint32_t)x;
+                        hhi ^= (uint32_t)(x >> 32);
+                    }
                 }
+                key = group_min<G>(key);
+                hlo = group_add<G>(hlo);
+                hhi = group_xor<G>(hhi);
+                const unsigned nm = __ballot_sync(FULL, norm && gl == 0);
+                if (norm) {
+                    const int slot = nb + __popc(nm & ((1u << lead) - 1u));
+                    int4 *r = brow + (size_t)slot * BS::ROW;
+    #pragma unroll
+                    for (int i = 0; i < CPL; ++i)
+                        r[gl + G * i] = make_int4(t32[4 * i + 0], t32[4 * i + 1], t32[4 * i + 2], t32[4 * i + 3]);
+                    if (gl == 0) {
+                        uint64_t pos;
+                        uint32_t tag;
+                        slot_tag_pos(((uint64_t)hhi << 32) | hlo, a.slot_mask, pos, tag);
+                        prefetch_l2(&a.slots[pos]);
+                        bpos[slot] = pos;
+                        btag[slot] = tag;
+                        bkey[slot] = key;
+                        binfo[slot] = (uint32_t)k | (in_u ? 1u << 12 : 0u) | ((uint32_t)(pc + (in_u ? 0 : 1)) << 13);
+                        bpar[slot] = (uint32_t)p;
+                    }
+                }
+                nb += __popc(nm);
+                if (nb > NB - NG) flush();
+
             }
-            nb += __popc(nm);
-            if (nb > NB - NG) flush();
         }
         if (__any_sync(FULL, fatal)) break;
     }
