@@ -63,7 +63,8 @@ typedef struct {
     int32_t max_len;       /* max |U| in split columns, 1..EFM_MAX_LEN */
     int32_t max_secondary; /* max secondary steps per pathway (Def. 10, Eq. 4), >= 0 */
     int64_t max_results;   /* <= 0: no cap; else stop after the level reaching it (EFM_CAPPED) */
-    int64_t max_frontier;  /* <= 0: no budget; else stop when a level exceeds it (EFM_TRUNCATED) */
+    int64_t max_frontier;  /* <= 0: no budget (2^22 states per level); else stop when a level
+                              exceeds it (EFM_TRUNCATED); at most 2^31 */
     int32_t first_k;       /* 0: every result; K > 0: exactly the K smallest results in the
                               output order (|U|, then the ascending column list), found by
                               the same traversal with an exact branch and bound; max_results

@@ -796,6 +796,7 @@ extern "C" int efm_find_pathways(efm_net *net, const int32_t *targets, int32_t n
         (lim.proposal != EFM_PLAIN && lim.proposal != EFM_LEARNED))
         return EFM_EINVAL;
     if (lim.first_k > 0 && lim.max_results != 0) return EFM_EINVAL;
+    if (lim.max_frontier > ((int64_t)1 << 31)) return EFM_EINVAL;  // arena indices are 32-bit
     // a model orders a first-K search and nothing else
     if ((lim.proposal == EFM_LEARNED) != (model != nullptr) || (model && lim.first_k <= 0)) return EFM_EINVAL;
     const efm_model *mdl = model;

@@ -1025,6 +1025,9 @@ __device__ void expand_range(const NetView &nv, const LevelArgs &a, const uint32
                 }
             }
             if (okl) ++n_exp;
+            // packed item: column | |U| << 12 | secondary << 19; parent as 32 bits
+            const uint32_t infol = (uint32_t)kl | ((uint32_t)pcl << 12) | (inl ? 1u << 19 : 0u);
+            const uint32_t pl32 = (uint32_t)pl_;
             // the groups take the valid items of this pass NG at a time, in order
             unsigned vmask = __ballot_sync(FULL, okl);
             while (vmask) {
@@ -1034,12 +1037,13 @@ __device__ void expand_range(const NetView &nv, const LevelArgs &a, const uint32
                 for (int t = 0; t < NG; ++t) vmask &= vmask - 1;
                 const int sl = src < 0 ? 0 : src;
                 const bool ok = src >= 0;
-                const int k = __shfl_sync(FULL, kl, sl);
-                const int pc = __shfl_sync(FULL, pcl, sl);
-                const bool in_u = __shfl_sync(FULL, inl ? 1 : 0, sl) != 0;
+                const uint32_t info_i = __shfl_sync(FULL, infol, sl);
+                const int k = (int)(info_i & 0xFFFu);
+                const int pc = (int)((info_i >> 12) & 0x7Fu);
+                const bool in_u = (info_i >> 19) & 1u;
                 const int32_t A = __shfl_sync(FULL, Al, sl);
                 const int32_t C = __shfl_sync(FULL, Cl, sl);
-                const int64_t p = __shfl_sync(FULL, pl_, sl);
+                const int64_t p = (int64_t)__shfl_sync(FULL, pl32, sl);
                 const int32_t *prow = a.par.B + (size_t)p * Mpad;
                 const uint64_t *pu = a.par.U + (size_t)p * W;
 
