@@ -286,7 +286,9 @@ int efm_sort_supports_noalloc(const uint64_t *supports_in, int64_t n_rows, int32
  *   the weight of feature 10, which is constant 1.
  * Features of a state: see the feature list in the library's kernel source
  * (counts of unbalanced metabolites, pivot degree, |U|, secondary steps,
- * lowest columns, a 64-bucket hashed embedding of the support).
+ * lowest columns, the share of U flux-dependent for the pivot from the
+ * DEPTHy tags of efm_dependent_reactions, a 64-bucket hashed embedding of
+ * the support).
  * Training: binary cross-entropy of s against labels of traced states
  * (1 = the state's support lies inside a support of the search's answer),
  * positives weighted by pos_weight, Adam (0.9, 0.999, 1e-8).

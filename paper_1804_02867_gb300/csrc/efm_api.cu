@@ -80,6 +80,8 @@ struct efm_net {
     NetView nv{};
     DevBuf blob, metptr, metent;
     int sm_count = 0;
+    DevBuf dep;             // DEPTHy tags (dep_out | dep_in) per internal metabolite, for the model's features
+    bool dep_ready = false;
 };
 
 struct TargetOut {
@@ -334,6 +336,7 @@ extern "C" void efm_free_net(efm_net *net)
     dev_free(net->blob, s);
     dev_free(net->metptr, s);
     dev_free(net->metent, s);
+    dev_free(net->dep, s);
     cudaStreamSynchronize(s);
     delete net;
 }
@@ -472,6 +475,46 @@ struct TopK {
 // branch and bound between chunks: once K results are known, a child that
 // would follow the K-th of them in the output order is not generated, since
 // every descendant keeps or grows its support.
+// DEPTHy tags of the network for the model's features: the deepest walk
+// length (at most 3) whose enumeration stays under 2^26 walks per
+// metabolite; dep_out | dep_in per internal metabolite.  Computed once.
+int ensure_dep_tags(efm_net *net)
+{
+    if (net->dep_ready) return EFM_OK;
+    const NetView &nv = net->nv;
+    cudaStream_t s = net->stream;
+    const size_t words = (size_t)std::max(nv.M, 1) * nv.W;
+    DevBuf r, din;
+    unsigned rh = 0;
+    int rc = EFM_OK;
+    if (!dev_alloc(r, 4, s) || !dev_alloc(net->dep, words * 8, s) || !dev_alloc(din, words * 8, s)) rc = EFM_ENOMEM;
+    if (rc == EFM_OK &&
+        (cudaMemsetAsync(r.p, 0, 4, s) != cudaSuccess || launch_step_count(nv, (unsigned *)r.p, s) != cudaSuccess ||
+         cudaMemcpyAsync(&rh, r.p, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess))
+        rc = EFM_ECUDA;
+    int depth = 0;
+    unsigned long long n_paths = 1;
+    while (rc == EFM_OK && rh > 0 && depth < 3 && n_paths * rh <= (1ull << 26)) {
+        n_paths *= rh;
+        ++depth;
+    }
+    if (rc == EFM_OK &&
+        (cudaMemsetAsync(net->dep.p, 0, words * 8, s) != cudaSuccess || cudaMemsetAsync(din.p, 0, words * 8, s) != cudaSuccess ||
+         (depth > 0 && launch_depthy(nv, depth, rh, n_paths, (unsigned long long *)net->dep.p,
+                                     (unsigned long long *)din.p, net->sm_count, s) != cudaSuccess) ||
+         launch_or_words((uint64_t *)net->dep.p, (const uint64_t *)din.p, (int64_t)words, s) != cudaSuccess))
+        rc = EFM_ECUDA;
+    dev_free(r, s);
+    dev_free(din, s);
+    if (rc != EFM_OK) {
+        cudaGetLastError();
+        dev_free(net->dep, s);
+        return rc;
+    }
+    net->dep_ready = true;
+    return EFM_OK;
+}
+
 // Training trace of a first-K search: features of a strided sample of each
 // level's frontier, labelled against the search's answer.
 struct Trace {
@@ -630,8 +673,9 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
             const int64_t cnt = (n_front + stride - 1) / stride;
             efm_model *m = trace->m;
             if (!model_reserve_rows(m, m->n_rows + cnt)) return EFM_ENOMEM;
-            CK(launch_features(nv, arena(cur), 0, stride, cnt, level - 1, lim.max_len, lim.max_secondary, m->X.p,
-                               m->n_rows, s));
+            if ((rc = ensure_dep_tags(net))) return rc;
+            CK(launch_features(nv, arena(cur), 0, stride, cnt, level - 1, lim.max_len, lim.max_secondary,
+                               (const uint64_t *)net->dep.p, m->X.p, m->n_rows, s));
             CK(launch_labels((const uint64_t *)w.U[cur].p, nv.W, 0, stride, cnt, trace->ans, trace->n_ans,
                              (float *)m->y.p, m->n_rows, s));
             m->n_rows += cnt;
@@ -655,8 +699,9 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
                     if (!dev_alloc(w.lhist, 4096 * 4, s) || !dev_alloc(w.lerr, 4, s)) return EFM_ENOMEM;
                     CK(cudaMemsetAsync(w.lerr.p, 0, 4, s));
                 }
-                CK(launch_features(nv, arena(cur), 0, 1, n_front, level - 1, lim.max_len, lim.max_secondary, w.lx.p, 0,
-                                   s));
+                if ((rc = ensure_dep_tags(net))) return rc;
+                CK(launch_features(nv, arena(cur), 0, 1, n_front, level - 1, lim.max_len, lim.max_secondary,
+                                   (const uint64_t *)net->dep.p, w.lx.p, 0, s));
                 CK(launch_mlp_score(w.lx.p, n_front, model->wb.p, (const float *)model->params.p,
                                     (float *)w.lscore.p, (unsigned *)w.lerr.p, s));
                 CK(launch_score_order((const float *)w.lscore.p, n_front, (unsigned *)w.lhist.p,

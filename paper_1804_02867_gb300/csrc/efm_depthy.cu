@@ -72,7 +72,20 @@ __global__ void depthy_kernel(NetView nv, int L, unsigned r, unsigned long long 
     }
 }
 
+__global__ void or_words_kernel(uint64_t *a, const uint64_t *b, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] |= b[i];
+}
+
 }  // namespace
+
+cudaError_t launch_or_words(uint64_t *a, const uint64_t *b, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    or_words_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, b, n);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_step_count(const NetView &nv, unsigned *r, cudaStream_t s)
 {

@@ -159,7 +159,7 @@ __host__ __device__ inline uint32_t mlp_blk_off(int row, int k)
 
 // kernels (efm_mlp.cu)
 cudaError_t launch_features(const NetView &nv, const Arena &par, int64_t first, int64_t stride, int64_t n, int level,
-                            int max_len, int max_sec, void *X, int64_t row0, cudaStream_t s);
+                            int max_len, int max_sec, const uint64_t *dep, void *X, int64_t row0, cudaStream_t s);
 cudaError_t launch_labels(const uint64_t *U, int W, int64_t first, int64_t stride, int64_t n, const uint64_t *ans,
                           int64_t n_ans, float *y, int64_t row0, cudaStream_t s);
 cudaError_t launch_mlp_score(const void *X, int64_t n_rows, const void *wb, const float *params, float *score,
@@ -189,6 +189,7 @@ int expand_grid(const NetView &nv, int sm_count);
 cudaError_t launch_iota(uint32_t *perm, int64_t n, cudaStream_t s);
 cudaError_t launch_seedset(const NetView &nv, const LevelArgs &a, const int32_t *cols, int n_cols, cudaStream_t s);
 cudaError_t launch_step_count(const NetView &nv, unsigned *r, cudaStream_t s);
+cudaError_t launch_or_words(uint64_t *a, const uint64_t *b, int64_t n, cudaStream_t s);
 cudaError_t launch_depthy(const NetView &nv, int L, unsigned r, unsigned long long n_paths, unsigned long long *dep_out,
                           unsigned long long *dep_in, int sm_count, cudaStream_t s);
 cudaError_t launch_flux(const NetView &nv, const uint64_t *sup, int64_t n, int64_t *flux, int8_t *status, int sm_count,

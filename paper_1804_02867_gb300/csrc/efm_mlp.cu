@@ -155,6 +155,8 @@ __device__ __forceinline__ uint32_t col_hash(uint32_t k)
 //   4-7 the four lowest columns of U / N        8 pivot row / M
 //   9 log2(1 + max |b|) / 32                    10 constant 1 (the hidden bias)
 //   11 level / (max_len + max_secondary)        12 mean column of U / N
+//   13 share of U's columns flux-dependent for the pivot (Def. 11, the DEPTHy tags)
+//   14 1 when the pivot has flux-dependent columns at all
 //   64-127 hashed embedding of U: column k adds +-1 to bucket h(k) mod 64,
 //          scaled by 1 / sqrt(|U|)
 // Row r takes the state at position first + r * stride of the arena.
@@ -163,7 +165,7 @@ constexpr int kFeatWarps = 8;
 
 __global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(NetView nv, Arena par, int64_t first, int64_t stride,
                                                                    int64_t n, int level, int max_len, int max_sec,
-                                                                   __nv_bfloat16 *X, int64_t row0)
+                                                                   const uint64_t *dep, __nv_bfloat16 *X, int64_t row0)
 {
     __shared__ float emb[kFeatWarps][64];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -226,6 +228,20 @@ __global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(NetView nv, A
         __syncwarp();
         const int pc = (int)((meta >> 23) & 0x7Fu);
         const int piv = (int)(meta & 0x3FFu);
+        // flux-dependent columns of the pivot (tags of dep_out | dep_in) inside U
+        int ndep = 0, anydep = 0;
+        if (dep && piv < nv.M) {
+            const uint64_t *D = dep + (size_t)piv * W;
+            for (int w = lane; w < W; w += 32) {
+                ndep += __popcll(U[w] & D[w]);
+                anydep |= D[w] != 0ull;
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                ndep += __shfl_xor_sync(FULLMASK, ndep, off);
+                anydep |= __shfl_xor_sync(FULLMASK, anydep, off);
+            }
+        }
         const int deg = (int)((meta >> 10) & 0x1FFFu);
         const int sec = level - (pc - 1);
         const float inv_sqrt = pcl > 0 ? rsqrtf((float)pcl) : 0.f;
@@ -256,6 +272,10 @@ __global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(NetView nv, A
                 v = (float)level / (float)(max_len + max_sec);
             } else if (i == 12) {
                 v = pcl > 0 ? colsum / (float)pcl / (float)nv.N : 0.f;
+            } else if (i == 13) {
+                v = pcl > 0 ? (float)ndep / (float)pcl : 0.f;
+            } else if (i == 14) {
+                v = anydep ? 1.f : 0.f;
             }
             f[t] = v;
         }
@@ -659,12 +679,12 @@ int sm_count_cached()
 }  // namespace
 
 cudaError_t launch_features(const NetView &nv, const Arena &par, int64_t first, int64_t stride, int64_t n, int level,
-                            int max_len, int max_sec, void *X, int64_t row0, cudaStream_t s)
+                            int max_len, int max_sec, const uint64_t *dep, void *X, int64_t row0, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     const int64_t blocks = std::min<int64_t>((n + kFeatWarps - 1) / kFeatWarps, (int64_t)sm_count_cached() * 16);
     features_kernel<<<(unsigned)blocks, kFeatWarps * 32, 0, s>>>(nv, par, first, stride, n, level, max_len, max_sec,
-                                                                 reinterpret_cast<__nv_bfloat16 *>(X), row0);
+                                                                 dep, reinterpret_cast<__nv_bfloat16 *>(X), row0);
     return cudaGetLastError();
 }
 
