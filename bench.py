@@ -76,6 +76,19 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_over_ranks(times, work, device):
+    """Replicas: the slowest rank's times (max) and all ranks' work (sum), over
+    the initialised process group (NCCL with device "cuda", gloo with "cpu")."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x) for x in times], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([float(x) for x in work], device=device, dtype=torch.float64)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t.tolist()], [int(x) for x in w.tolist()]
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -307,14 +320,8 @@ def run_ours(args):
 
     # max over ranks of the device time; sum of work over ranks
     if ws > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([tot_ms, e2e_t], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        w = torch.tensor([tot_exp, tot_res, e2e_exp], device="cuda", dtype=torch.float64)
-        dist.all_reduce(w, op=dist.ReduceOp.SUM)
-        tot_ms, e2e_t = float(t[0]), float(t[1])
-        tot_exp, tot_res, e2e_exp = int(w[0]), int(w[1]), int(w[2])
+        (tot_ms, e2e_t), (tot_exp, tot_res, e2e_exp) = reduce_over_ranks([tot_ms, e2e_t], [tot_exp, tot_res, e2e_exp],
+                                                                         "cuda")
     nw.close()
     if rank != 0:
         return
