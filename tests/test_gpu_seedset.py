@@ -80,3 +80,21 @@ def test_seed_set_rules(efm):
         for bad in ([a, int(twin[a])], [1, 1], [], [len(twin)], list(range(10))):
             with pytest.raises(efm.EfmError):
                 efm.efm_find_pathways_from(nw.handle, bad, 9, 1)
+
+
+def test_seed_set_first_k_and_fluxes(oracle_lib, efm):
+    """Features combined: a first-K search from a seed set returns the K
+    smallest of the seed set's results, and their flux vectors are exact."""
+    from oracle import flux
+
+    net = synth.core()
+    with efm.Network(net) as nw:
+        (res, _), = efm.enumerate_targets(nw, [63], 16, 4)
+        R = list(__import__("oracle").supports_to_lists(res)[3][:2])
+        full, _ = oracle_lib.enumerate_from(net, R, oracle_lib.Limits(16, 4, 0, 0))
+        for k in (1, 5, len(full)):
+            sup, _ = efm.enumerate_from(nw, R, 16, 4, first_k=k)
+            assert np.array_equal(sup, full[:k]), (R, k)
+        fl, st = efm.efm_flux_vectors(nw.handle, full)
+        for i, v in enumerate(flux.flux_vectors(net, full)):
+            assert st[i] == 1 and list(fl[i, :len(v)]) == v
