@@ -348,6 +348,7 @@ struct Work {
     DevBuf U[2], B[2], meta[2];
     DevBuf slots, cslots, cand, res, bcnt, bfill, bptr, bres, ctr, sortidx, rcols;
     DevBuf perm, fkb;  // first-K search: parent order of a level, bound support
+    DevBuf band;       // per column: intersection of the results containing it (W <= 2)
     DevBuf lx, lscore, lhist, lerr;  // learned order: features, scores, buckets, error flag
     int64_t lx_rows = 0;
     int64_t F_cap = 0, cand_cap = 0, res_cap = 0, bres_cap = 0;  // bres_cap in bucket entries
@@ -364,7 +365,7 @@ void free_work(Work &w, cudaStream_t s)
     }
     DevBuf *bufs[] = {&w.slots, &w.cslots, &w.cand, &w.res, &w.bcnt,    &w.bfill, &w.bptr,
                       &w.bres,  &w.ctr,    &w.sortidx, &w.rcols, &w.perm, &w.fkb,
-                      &w.lx,    &w.lscore, &w.lhist,   &w.lerr};
+                      &w.lx,    &w.lscore, &w.lhist,   &w.lerr, &w.band};
     for (DevBuf *b : bufs) dev_free(*b, s);
     for (auto &e : w.ev)
         if (e) cudaEventDestroy(e);
@@ -395,6 +396,7 @@ int alloc_work(Work &w, const efm_net *net, const efm_limits &lim, int total_war
     ok = ok && dev_alloc(w.bptr, (size_t)(nv.N + 1) * 4, s);
     ok = ok && dev_alloc(w.ctr, C_COUNT * 8, s);
     if (nv.W > 2) ok = ok && dev_alloc(w.rcols, (size_t)w.res_cap * kRcolStride * 2, s);
+    if (nv.W <= 2) ok = ok && dev_alloc(w.band, (size_t)nv.N * nv.W * 8, s);
     if (lim.first_k > 0) {
         ok = ok && dev_alloc(w.perm, F * 4, s);
         ok = ok && dev_alloc(w.fkb, W * 8, s);
@@ -552,6 +554,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
     a.bres = nullptr;
     a.bids = nullptr;
     a.rcols = nv.W > 2 ? (const uint16_t *)w.rcols.p : nullptr;
+    a.band = nv.W <= 2 ? (const uint64_t *)w.band.p : nullptr;
     a.max_len = lim.max_len;
     a.max_sec = lim.max_secondary;
     a.ctr = ctr;
@@ -653,7 +656,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
             a.bres = (const uint64_t *)w.bres.p;
             a.bids = (const int32_t *)w.bres.p;
             CK(launch_buckets(nv, (const uint64_t *)w.res.p, res_n, (int32_t *)w.bcnt.p, (int32_t *)w.bptr.p,
-                              (int32_t *)w.bfill.p, (uint64_t *)w.bres.p, s));
+                              (int32_t *)w.bfill.p, (uint64_t *)w.bres.p, (uint64_t *)w.band.p, s));
             out.kernel_launches += res_n > 0 ? 3 : 1;
             buckets_built_for = res_n;
         }

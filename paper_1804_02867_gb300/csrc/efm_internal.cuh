@@ -88,6 +88,7 @@ struct LevelArgs {
     const uint64_t *bres;       // bucket entries: the result's W support words (W <= 2)
     const int32_t *bids;        // bucket entries: result ids (W > 2), same buffer as bres
     const uint16_t *rcols;      // per result: column count, then its columns (stride kRcolStride)
+    const uint64_t *band;       // W <= 2: per column, the intersection of the results containing it (or null)
     int level, max_len, max_sec;
     int cpw;                    // parents per warp chunk (1..32)
     unsigned long long *ctr;
@@ -182,7 +183,8 @@ cudaError_t launch_accept(const NetView &nv, const AcceptArgs &a, cudaStream_t s
 // device, so no host round trip is needed between expansion and test); then advance the range
 cudaError_t launch_accept_new(const NetView &nv, const AcceptArgs &a, int sm_count, cudaStream_t s);
 cudaError_t launch_buckets(const NetView &nv, const uint64_t *res, int64_t n_res, int32_t *bcnt, int32_t *bptr,
-                           int32_t *bfill, uint64_t *bres, cudaStream_t s);  // W > 2: bres holds int32 ids
+                           int32_t *bfill, uint64_t *bres, uint64_t *band,
+                           cudaStream_t s);  // W > 2: bres holds int32 ids; band (W <= 2, may be null)
 cudaError_t launch_sort_results(const uint64_t *res, int64_t n, int W, uint32_t *idx, int64_t n_pow2,
                                 uint64_t *out, int64_t n_keep, cudaStream_t s);
 int expand_grid(const NetView &nv, int sm_count);

@@ -1140,7 +1140,14 @@ __device__ void expand_range(const NetView &nv, const LevelArgs &a, const uint32
                     const int64_t n = a.bptr[k + 1] - b1;
                     if (W <= 2) {
                         const uint64_t u0 = child_word(pu, 0, k), u1 = W == 2 ? child_word(pu, 1, k) : 0ull;
-                        for (int64_t i = gl; i < n && !pr; i += G) {
+                        // every result containing k holds their intersection: if the
+                        // child lacks part of it, none of them lies inside the child
+                        bool maybe = true;
+                        if (a.band) {
+                            const uint64_t i0 = __ldg(a.band + (size_t)k * W), i1 = W == 2 ? __ldg(a.band + (size_t)k * W + 1) : 0ull;
+                            maybe = ((i0 & ~u0) | (i1 & ~u1)) == 0;
+                        }
+                        for (int64_t i = gl; i < n && !pr && maybe; i += G) {
                             const uint64_t *E = a.bres + (size_t)(b1 + i) * W;
                             const uint64_t e0 = __ldg(E), e1 = W == 2 ? __ldg(E + 1) : 0ull;
                             pr = ((e0 & ~u0) | (e1 & ~u1)) == 0;
@@ -1453,7 +1460,7 @@ __global__ void bucket_scan_kernel(const int32_t *bcnt, int N, int32_t *bptr)
 }
 
 __global__ void bucket_fill_kernel(const uint64_t *res, int64_t n, int W, const int32_t *bptr, int32_t *bfill,
-                                   uint64_t *bres)
+                                   uint64_t *bres, unsigned long long *band)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n * W) return;
@@ -1462,10 +1469,15 @@ __global__ void bucket_fill_kernel(const uint64_t *res, int64_t n, int W, const 
     for (uint64_t x = res[i]; x; x &= x - 1) {
         const int k = w * 64 + __ffsll((long long)x) - 1;
         const int64_t pos = (int64_t)bptr[k] + atomicAdd(&bfill[k], 1);
-        if (W > 2)
+        if (W > 2) {
             reinterpret_cast<int32_t *>(bres)[pos] = (int32_t)r;
-        else
-            for (int v = 0; v < W; ++v) bres[pos * W + v] = res[r * W + v];
+        } else {
+            for (int v = 0; v < W; ++v) {
+                bres[pos * W + v] = res[r * W + v];
+                // intersection of the results containing k
+                if (band) atomicAnd(&band[(size_t)k * W + v], (unsigned long long)res[r * W + v]);
+            }
+        }
     }
 }
 
@@ -1898,16 +1910,19 @@ cudaError_t launch_accept(const NetView &nv, const AcceptArgs &a, cudaStream_t s
 }
 
 cudaError_t launch_buckets(const NetView &nv, const uint64_t *res, int64_t n_res, int32_t *bcnt, int32_t *bptr,
-                           int32_t *bfill, uint64_t *bres, cudaStream_t s)
+                           int32_t *bfill, uint64_t *bres, uint64_t *band, cudaStream_t s)
 {
     cudaError_t e;
     if ((e = cudaMemsetAsync(bcnt, 0, sizeof(int32_t) * (size_t)nv.N, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(bfill, 0, sizeof(int32_t) * (size_t)nv.N, s)) != cudaSuccess) return e;
+    if (band && (e = cudaMemsetAsync(band, 0xFF, sizeof(uint64_t) * (size_t)nv.N * nv.W, s)) != cudaSuccess) return e;
     const int64_t items = n_res * nv.W;
     const int tb = 256;
     if (items > 0) bucket_count_kernel<<<(int)((items + tb - 1) / tb), tb, 0, s>>>(res, n_res, nv.W, bcnt);
     bucket_scan_kernel<<<1, 1024, 0, s>>>(bcnt, nv.N, bptr);
-    if (items > 0) bucket_fill_kernel<<<(int)((items + tb - 1) / tb), tb, 0, s>>>(res, n_res, nv.W, bptr, bfill, bres);
+    if (items > 0)
+        bucket_fill_kernel<<<(int)((items + tb - 1) / tb), tb, 0, s>>>(res, n_res, nv.W, bptr, bfill, bres,
+                                                                      reinterpret_cast<unsigned long long *>(band));
     return cudaGetLastError();
 }
 
