@@ -618,21 +618,25 @@ __global__ void __launch_bounds__(32) seedset_kernel(NetView nv, LevelArgs a, co
 // ---------------------------------------------------------------------------
 // a1-a6: one level of expansion.
 //
-// Phase 1 (a group of G lanes per child): a warp takes 32 consecutive
-// parents; their branch counts (the static degree of each parent's acting
-// metabolite, kept in the state's meta word) are prefix-summed across the
-// lanes, and the warp walks the flattened (parent, branch) items 32 / G at a
-// time.  In a group, lane l holds the 16-byte chunks l, l + G, ... of the
-// extra-flux row (CPL chunks, 4 * CPL entries), so row loads are coalesced
-// and every reduction is log2(G) shuffles.  The AND update reads column k of
-// S_int from a dense column-major copy of S_int (staged in shared memory
-// with the rest of the static network when it fits) and stays in 32 bits
-// unless a group needs the gcd or has an entry outside int32.  Unbalanced
-// children are appended to a per-warp batch in shared memory.
+// Phase 1: a warp takes up to 32 consecutive parents; their branch counts
+// (the static degree of each parent's acting metabolite, kept in the state's
+// meta word) are prefix-summed across the lanes.  The warp then examines the
+// flattened (parent, branch) items 32 at a time, one per lane (branch
+// selection and the twin, length and first-K rules), and its groups of G
+// lanes take the valid items in order, one child per group.  In a group,
+// lane l holds the 16-byte chunks l, l + G, ... of the extra-flux row (CPL
+// chunks, 4 * CPL entries), so row loads are coalesced and every reduction
+// is log2(G) shuffles.  The AND update reads column k of S_int from a dense
+// column-major copy of S_int (staged in shared memory with the rest of the
+// static network when it fits) and stays in 32 bits unless a group needs the
+// gcd or has an entry outside int32.  The group then applies the superset
+// rule (its lanes split the results containing the new column) and appends
+// surviving unbalanced children to a per-warp batch in shared memory.
 //
-// Phase 2 (one lane per batched child, NB children at once): superset
-// pruning, then claim / write / publish / compare in the state hash table,
-// so the latency of the atomics is paid once per batch, not per child.
+// Phase 2 (one lane per batched child, NB children at once; the whole warp
+// per child for wide rows): claim / write / publish / compare in the state
+// hash table, so the latency of the atomics is paid once per batch, not per
+// child.
 // ---------------------------------------------------------------------------
 
 template <int G>
@@ -749,14 +753,13 @@ __device__ void expand_range(const NetView &nv, const LevelArgs &a, const uint32
     int nb = 0;         // children in the batch (warp-uniform)
     const uint64_t t_start = global_ns();
 
-    // Phase 2 for wide rows (more than 32 chunks): the whole warp prunes,
-    // claims and copies or compares one batched child at a time.
+    // Phase 2 for wide rows (more than 32 chunks): the whole warp claims and
+    // copies or compares one batched child at a time.
     auto flush_wide = [&]() {
         __syncwarp();
         for (int b = 0; b < nb; ++b) {
             const uint32_t info = binfo[b];
             const int k = (int)(info & 0xFFFu);
-            const bool in_u = (info >> 12) & 1u;
             const uint64_t *pu = a.par.U + (size_t)bpar[b] * W;
             if (full) continue;
             uint64_t pos = bpos[b];
@@ -830,7 +833,7 @@ __device__ void expand_range(const NetView &nv, const LevelArgs &a, const uint32
         __syncwarp();
     };
 
-    // Phase 2: prune and insert the batched children, one lane each.
+    // Phase 2: insert the batched children, one lane each.
     auto flush = [&]() {
         if (BS::NCH > 32) {
             flush_wide();
@@ -840,7 +843,6 @@ __device__ void expand_range(const NetView &nv, const LevelArgs &a, const uint32
         const bool mine = lane < nb;
         const uint32_t info = mine ? binfo[lane] : 0u;
         const int k = (int)(info & 0xFFFu);
-        const bool in_u = (info >> 12) & 1u;
         const uint64_t *pu = a.par.U + (size_t)(mine ? bpar[lane] : 0u) * W;
         bool todo = mine;
         if (full) todo = false;
