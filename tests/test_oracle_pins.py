@@ -398,3 +398,22 @@ def test_dependent_reactions_hand_worked():
     assert i.tolist() == [[False, True, False, False], [True, False, False, False]]
     o, i = depthy.dependent_reactions(net, 1)
     assert not o.any() and not i.any()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_python_reference_agrees_on_tiny_networks(oracle_lib, seed):
+    """Two independent restatements of the traversal (plain C with rays; pure
+    Python with exact fractions and explicit flux vectors) give the same
+    results and counters on random tiny networks, for every target."""
+    from oracle import reference
+
+    net = synth.tiny(seed)
+    for t in list(net.targets) + [-1]:
+        for L, S in ((6, 0), (8, 1), (9, 2)):
+            sup, ctr = oracle_lib.enumerate_pathways(net, t, oracle_lib.Limits(L, S, 0, 0))
+            res, rctr = reference.enumerate_reference(net, t, L, S)
+            got = [tuple(k for k in range(64) if (U >> k) & 1) for U in res]
+            assert got == oracle_lib.supports_to_lists(sup), (seed, t, L, S)
+            for key in ("levels", "seeds", "expansions", "overflow", "balanced", "candidates", "results", "pruned",
+                        "frontier", "frontier_max", "status"):
+                assert ctr[key] == rctr[key], (seed, t, L, S, key)
