@@ -213,3 +213,83 @@ def enumerate_reference(net, target, max_len=64, max_secondary=4, max_results=0,
             ctr["status"] |= CAPPED
             break
     return finish()
+
+
+def _splitmix_at(seed, c):
+    """First output of SplitMix64 started from state seed + c * golden."""
+    m = (1 << 64) - 1
+    z = (seed + (c + 1) * 0x9E3779B97F4A7C15) & m
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m
+    return z ^ (z >> 31)
+
+
+def sample_reference(net, target, max_len, max_secondary, seed, n_walks):
+    """The Monte-Carlo walks in pure Python (exact integers): walk w draws
+    counter 128 w for its seed column and 128 w + s for step s; one random
+    valid branch per step.  Returns (sorted result bitmasks, counters)."""
+    S_int, twin, full, cols = split_network(net)
+    M = len(S_int)
+    N = len(cols)
+    deg_out = [sum(1 for k in range(N) if S_int[i][k] < 0) for i in range(M)]
+    deg_in = [sum(1 for k in range(N) if S_int[i][k] > 0) for i in range(M)]
+    ctr = dict(levels=0, seeds=0, expansions=0, overflow=0, balanced=0, candidates=0, results=0,
+               pruned=0, frontier=0, frontier_max=0, status=0)
+    seeds = [j for j in range(N) if target < 0 or full[target][j] > 0]
+    seen, results = set(), []
+    for w in range(n_walks if seeds else 0):
+        c0 = 128 * w
+        j = seeds[_splitmix_at(seed, c0) % len(seeds)]
+        ctr["seeds"] += 1
+        U, sec, steps = 1 << j, 0, 0
+        ef, zero = _normalise([S_int[i][j] for i in range(M)])
+        if any(abs(x) > INT32_MAX for x in ef):
+            ctr["overflow"] += 1
+            continue
+        s = 1
+        while True:
+            if zero:
+                ctr["balanced"] += 1
+                if U not in seen:
+                    seen.add(U)
+                    ctr["candidates"] += 1
+                    if nullity_one(S_int, U, N):
+                        results.append(U)
+                        ctr["results"] += 1
+                break
+            _, piv = min((deg_out[i] if ef[i] > 0 else deg_in[i], i) for i in range(M) if ef[i] != 0)
+            e = ef[piv]
+            pc = bin(U).count("1")
+            valid = []
+            for k in range(N):
+                sk = S_int[piv][k]
+                if not ((sk < 0) if e > 0 else (sk > 0)):
+                    continue
+                if twin[k] >= 0 and (U >> twin[k]) & 1:
+                    continue
+                in_u = (U >> k) & 1
+                if (not in_u and pc + 1 > max_len) or (in_u and sec + 1 > max_secondary):
+                    continue
+                valid.append(k)
+            if not valid:
+                ctr["pruned"] += 1
+                break
+            k = valid[_splitmix_at(seed, c0 + s) % len(valid)]
+            sk = S_int[piv][k]
+            g = gcd(abs(e), abs(sk))
+            a, c = abs(sk) // g, abs(e) // g
+            ctr["expansions"] += 1
+            steps += 1
+            if (U >> k) & 1:
+                sec += 1
+            U |= 1 << k
+            ef, zero = _normalise([a * ef[i] + c * S_int[i][k] for i in range(M)])
+            if any(abs(x) > INT32_MAX for x in ef):
+                ctr["overflow"] += 1
+                break
+            s += 1
+        ctr["levels"] = max(ctr["levels"], steps)
+    if ctr["overflow"]:
+        ctr["status"] |= OVERFLOW_DROPPED
+    res = sorted(results, key=lambda U: (bin(U).count("1"), [k for k in range(N) if (U >> k) & 1]))
+    return res, ctr

@@ -417,3 +417,18 @@ def test_python_reference_agrees_on_tiny_networks(oracle_lib, seed):
             for key in ("levels", "seeds", "expansions", "overflow", "balanced", "candidates", "results", "pruned",
                         "frontier", "frontier_max", "status"):
                 assert ctr[key] == rctr[key], (seed, t, L, S, key)
+
+
+def test_python_walks_agree_with_c_walks(oracle_lib):
+    """The Monte-Carlo walks restated in pure Python give the C oracle's
+    results and counters."""
+    from oracle import reference
+
+    for seed in range(4):
+        net = synth.tiny(seed)
+        for t in list(net.targets) + [-1]:
+            sup, ctr = oracle_lib.sample_pathways(net, t, oracle_lib.Limits(9, 2), 100 + seed, 300)
+            res, rctr = reference.sample_reference(net, t, 9, 2, 100 + seed, 300)
+            got = [tuple(k for k in range(64) if (U >> k) & 1) for U in res]
+            assert got == oracle_lib.supports_to_lists(sup), (seed, t)
+            assert ctr == rctr, (seed, t, ctr, rctr)
