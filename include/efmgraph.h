@@ -306,7 +306,8 @@ int efm_sort_supports_noalloc(const uint64_t *supports_in, int64_t n_rows, int32
 int efm_model_create(uint64_t seed, uintptr_t cuda_stream, efm_model **out);
 
 /* Read (write = 0) or replace (write = 1; resets the Adam state) the FP32
- * parameters; params is a host array of EFM_MLP_PARAMS floats. */
+ * parameters; params is a host array of EFM_MLP_PARAMS floats.  Saving and
+ * loading a model is reading and writing this array. */
 int efm_model_params(efm_model *model, float *params, int32_t write);
 
 /* Append n training rows: x host [n][128] FP32 (stored as BF16), y host [n]

@@ -474,6 +474,25 @@ def efm_model_free(model):
     load_library().efm_model_free(model)
 
 
+def save_model(model, path):
+    """Write the model's FP32 parameters (efm_model_params) to a .npy file."""
+    np.save(path, efm_model_params(model))
+
+
+def load_model(path, stream=None):
+    """A new model with the parameters of a file written by save_model."""
+    p = np.load(path)
+    if p.shape != (EFM_MLP_PARAMS,) or p.dtype != np.float32:
+        raise ValueError(f"{path}: not a saved proposal model")
+    m = efm_model_create(0, stream)
+    try:
+        efm_model_params(m, p)
+    except Exception:
+        efm_model_free(m)
+        raise
+    return m
+
+
 # --- conveniences ------------------------------------------------------------
 
 class Network:

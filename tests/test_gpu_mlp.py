@@ -208,3 +208,22 @@ def test_trained_model_reaches_k_sooner(efm):
     print(f"certified by both: {both}; plain {plain_ms:.1f} ms, learned {learned_ms:.1f} ms")
     assert both >= 4
     assert learned_ms < plain_ms
+
+
+def test_save_and_load_reproduce_the_scores(efm, tmp_path):
+    rng = np.random.default_rng(21)
+    X, y = _rows(rng, 700)
+    m = efm.efm_model_create(5)
+    try:
+        efm.efm_model_add_rows(m, X, y)
+        efm.efm_model_train(m, epochs=3, batch_tiles=2, lr=1e-3)
+        s1 = efm.efm_model_forward(m, X)
+        efm.save_model(m, tmp_path / "model.npy")
+    finally:
+        efm.efm_model_free(m)
+    m2 = efm.load_model(tmp_path / "model.npy")
+    try:
+        s2 = efm.efm_model_forward(m2, X)
+    finally:
+        efm.efm_model_free(m2)
+    assert np.array_equal(s1, s2)
