@@ -337,3 +337,81 @@ def type1(seed: int, n_int: int = 7, n_ext: int = 3, n_rxn: int = 14, n_rev: int
     if n_rev:
         rev[rng.choice(n_rxn, size=n_rev, replace=False)] = 1
     return Network.from_dense(S, rev, ext, list(range(n_int, n_met)), name=f"type1-{seed}", seed=seed)
+
+
+# largest |coefficient| the C-ABI loader accepts (EFM_MAX_COEF)
+MAX_COEF = 524287
+
+
+def maximal(seed: int = 4_000_000) -> Network:
+    """A network at the library's size limits: exactly 1024 internal
+    metabolites and 4096 split columns (support width 64 words), with
+    coefficients up to MAX_COEF.
+
+    Two parts that share no metabolite:
+
+    * a chain that reaches the length limit: target T is made by r_0 from
+      m_0, r_i (i = 1..62) makes m_{i-1} from m_i, and r_63 makes m_62 from
+      the uptake X, so {r_0..r_63} is one 64-column pathway.  Coefficients
+      are 1 except a few (MAX_COEF, 2, 3) that scale the flux along the
+      chain.  Side branches: an uptake X' makes m_10, m_20, m_30, m_40 and
+      m_50 (shorter pathways); r_30 is reversible (twin rule); a reaction
+      q turns m_44 into m_46, closing the cycle q, r_46, r_45 (secondary
+      steps and a non-elementary balanced support).
+    * a random filler of 961 internal and 8 external metabolites (uniform
+      degree, 2-6 metabolites per reaction, coefficients mostly 1-3 with 3%
+      drawn up to MAX_COEF, 800 of 3225 reactions reversible), whose first
+      external is a second target.
+
+    Targets: T, then the filler target."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n_chain, n_fill_int, n_fill_ext = 63, 961, 8
+    n_int = n_chain + n_fill_int
+    T, X, Xalt = n_int, n_int + 1, n_int + 2
+    fext0 = n_int + 3
+    n_met = fext0 + n_fill_ext
+    cols = []
+    rev = []
+
+    def add(entries, reversible=False):
+        c = np.zeros(n_met, dtype=np.int64)
+        for m, v in entries:
+            c[m] += v
+        cols.append(c)
+        rev.append(1 if reversible else 0)
+
+    a = {5: MAX_COEF, 12: 2, 33: 3}  # consumption coefficients of r_i on m_i
+    b = {20: MAX_COEF, 27: 3, 51: 2}  # production coefficients of r_i on m_{i-1}
+    add([(0, -1), (T, 1)])
+    for i in range(1, n_chain):
+        add([(i, -a.get(i, 1)), (i - 1, b.get(i, 1))], reversible=(i == 30))
+    add([(X, -1), (n_chain - 1, 1)])
+    for i in (10, 20, 30, 40, 50):
+        add([(Xalt, -1), (i, 1)])
+    add([(44, -1), (46, 1)])
+    n_fixed_cols = len(cols) + sum(rev)
+    n_fill_rev = 800
+    n_fill = 4096 - n_fixed_cols - n_fill_rev
+    fill_mets = np.concatenate([np.arange(n_chain, n_int), np.arange(fext0, n_met)])
+    big = 0
+    for r in range(n_fill):
+        sz = int(rng.integers(2, 7))
+        mets = rng.choice(fill_mets, size=sz, replace=False)
+        n_sub = int(rng.integers(1, sz))
+        ent = []
+        for j, m in enumerate(mets):
+            v = int(rng.integers(1, 4))
+            if rng.random() < 0.03:
+                v = MAX_COEF if big < 2 else int(rng.integers(4, MAX_COEF + 1))
+                big += 1
+            ent.append((int(m), -v if j < n_sub else v))
+        if r < 6 and fext0 not in mets:
+            ent.append((fext0, 1))  # producers of the filler target
+        add(ent)
+    S = np.stack(cols, axis=1)
+    reversible = np.asarray(rev, dtype=np.uint8)
+    fill_rev = rng.choice(np.arange(len(cols) - n_fill, len(cols)), size=n_fill_rev, replace=False)
+    reversible[fill_rev] = 1
+    ext = np.zeros(n_met, dtype=np.uint8)
+    ext[n_int:] = 1
+    return Network.from_dense(S, reversible, ext, [T, fext0], name=f"maximal-{seed}", seed=seed)

@@ -59,3 +59,33 @@ def test_rank_primes_are_prime_and_below_2_31():
     for c in cs:
         assert sympy.isprime(2**31 - c)
         assert c < 2**10
+
+
+def test_load_network_rejects_out_of_range_sizes_on_the_host(lib):
+    """The loader validates on the host, before any device call: one internal
+    metabolite, one split column or one unit of coefficient past the limits
+    of the maximal network is EFM_EINVAL."""
+    import numpy as np
+
+    from paper_1804_02867_gb300 import efmgraph, synth
+
+    net = synth.maximal()
+    assert net.split_columns() == 4096 and int((net.external == 0).sum()) == 1024
+
+    def load(n_met=net.n_met, n_rxn=net.n_rxn, coef=net.coef, reversible=net.reversible, external=net.external):
+        with pytest.raises(efmgraph.EfmError) as e:
+            efmgraph.efm_load_network(n_met, n_rxn, net.row_ptr, net.col_idx, coef, reversible, external, stream=0)
+        return e.value.code
+
+    ext = net.external.copy()
+    ext[net.targets[1]] = 0  # 1025 internal metabolites
+    assert load(external=ext) == -1
+    rev = net.reversible.copy()
+    rev[np.nonzero(rev == 0)[0][-1]] = 1  # 4097 split columns
+    assert load(reversible=rev) == -1
+    coef = net.coef.copy()
+    coef[np.argmax(np.abs(coef))] = -(synth.MAX_COEF + 1)
+    assert load(coef=coef) == -1
+    coef = net.coef.copy()
+    coef[0] = 0
+    assert load(coef=coef) == -1
