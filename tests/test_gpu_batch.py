@@ -64,3 +64,44 @@ def test_batch_autotuner_reports_choice(efm):
     _batch(efm, nets, 20, 2, 2**9)
     tune = efm.efm_batch_tuning()
     assert tune is not None and tune[0] >= 1 and tune[1] in (0, 1)
+
+
+def wide_member(i):
+    """A batched-call member with 129-256 internal metabolites (8 balance
+    entries per lane, the widest row the batched kernel takes)."""
+    rng = np.random.default_rng(6_000_000 + i)
+    n_int = int(rng.integers(129, 257))
+    n_rxn = int(rng.integers(2 * n_int, 3 * n_int))
+    return synth.generate(n_int=n_int, n_targets=3, n_hubs=4, n_substrates=2, n_rxn=n_rxn, n_rev=n_rxn // 5,
+                          size_range=(2, 6), coef_probs=synth.CORE_COEFS, gamma=2.2, hub_degree=(30, 80),
+                          seed=6_000_000 + i, name=f"wide-{i}")
+
+
+@pytest.mark.parametrize("budget", [2**10, 2**12])
+def test_batch_mixed_row_widths(oracle_lib, efm, budget):
+    """One launch over members of every row width it supports (1, 2, 4 and 8
+    entries per lane, supports of 1 to 14 words), interleaved."""
+    nets = []
+    for i in range(24):
+        nets += [wide_member(i), synth.batched_member(3000 + i)] + ([synth.tiny(100 + i)] if i % 3 == 0 else [])
+    got = _batch(efm, nets, 30, 4, budget)
+    widths = set()
+    for net, (sup, ctr) in zip(nets, got):
+        L = min(30, net.split_columns())
+        osup, octr = oracle_lib.enumerate_pathways(net, net.targets[0], oracle_lib.Limits(L, 4, 0, budget))
+        assert np.array_equal(sup, osup), net.name
+        assert ctr == octr, (net.name, ctr, octr)
+        need = max(1, -(-int((net.external == 0).sum()) // 32))
+        widths.add(min(e for e in (1, 2, 4, 8) if e >= need))
+    assert widths == {1, 2, 4, 8}
+
+
+def test_batch_rejects_wider_rows(efm):
+    """Members with more than 256 internal metabolites are refused
+    (EFM_EUNSUPPORTED) before anything is launched."""
+    wide = synth.generate(n_int=300, n_targets=3, n_hubs=4, n_substrates=2, n_rxn=700, n_rev=140,
+                          size_range=(2, 6), coef_probs=synth.CORE_COEFS, gamma=2.2, hub_degree=(30, 80),
+                          seed=6_100_000, name="too-wide")
+    with pytest.raises(efm.EfmError) as e:
+        _batch(efm, [synth.tiny(0), wide], 20, 2, 2**10)
+    assert e.value.code == -6
