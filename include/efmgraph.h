@@ -214,11 +214,13 @@ int efm_sample_pathways(efm_net *net, int32_t target, const efm_limits *limits, 
  * order or largest network first) by timing a sample of the jobs, and caches
  * the choice per (job count, row class, SM count).
  *  nets[n_jobs]     loaded networks (any mix; all on nets[0]'s stream and
- *                   device; at most 256 internal metabolites each)
+ *                   device; at most 256 internal metabolites each, else
+ *                   EFM_EUNSUPPORTED before anything is launched)
  *  targets[n_jobs]  target metabolite per job (or -1)
  *  limits           as efm_find_pathways; max_frontier must be > 0 (it sizes
  *                   each CTA's frontier arena); each job uses
  *                   min(max_len, its column count)
+ *  model            must be NULL (first-K and proposals are not batched)
  *  out              one job handle with n_jobs entries for efm_fetch_results
  * Per-job device errors (capacity, bounded waits) are reported by
  * efm_fetch_results for that entry.  Per job at most 2^15 distinct balanced
