@@ -97,10 +97,10 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def profile_traffic():
-    """Per-launch DRAM traffic of the expansion kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "expand_kernel_core.md")
+def profile_figure(name, key):
+    """A figure from a committed ncu summary under profiles/, if that summary
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", name)
     src = os.path.join(ROOT, "paper_1804_02867_gb300", "csrc", "efm_kernels.cu")
     try:
         text = open(path).read()
@@ -108,10 +108,16 @@ def profile_traffic():
     except OSError:
         return None
     m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
-    m_tr = re.search(r"dram_bytes_per_launch_full_scale:\s*([0-9.eE+]+)", text)
-    if not m_sha or not m_tr or m_sha.group(1) != sha:
+    m_val = re.search(re.escape(key) + r":\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_val or m_sha.group(1) != sha:
         return None
-    return float(m_tr.group(1))
+    return float(m_val.group(1))
+
+
+def profile_traffic():
+    """Per-launch DRAM traffic of the core network's expansion kernel at full
+    scale (ncu), or None."""
+    return profile_figure("expand_kernel_core.md", "dram_bytes_per_launch_full_scale")
 
 
 class ClockSampler:
@@ -352,7 +358,7 @@ def run_ours(args):
             "peak": float(peaks["hbm_gbs"]),
             "unit": "GB/s",
             "frac": achieved / float(peaks["hbm_gbs"]),
-            "traffic": (traffic * tot_el / max(tot_el, 1)) if traffic else None,
+            "traffic": traffic,
             "peak_kind": f"{peak_kind} HBM copy bandwidth",
             "launches": tot_el,
             "avg_launch_ms": tot_ems / max(tot_el, 1),
@@ -395,7 +401,7 @@ def run_genome(args):
 
     def step():
         job, _ = efmgraph.efm_find_pathways(nw.handle, targets, 40, MAX_SEC, 0, budget)
-        exp = res = 0
+        exp = res = el = 0
         eb = ems = 0.0
         for i in range(n_t):
             _, c, _ = efmgraph.efm_fetch_results(job, i, copy=False)
@@ -404,18 +410,19 @@ def run_genome(args):
             res += c["results"]
             eb += tm["expand_bytes"]
             ems += tm["expand_ms"]
+            el += tm["expand_launches"]
         efmgraph.efm_free_job(job)
-        return exp, res, eb, ems
+        return exp, res, eb, ems, el
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     tot_ms = eb = ems = 0.0
-    exp = res = 0
+    exp = res = el = 0
     for _ in range(args.steps):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        e, r, b, m = step()
+        e, r, b, m, n = step()
         ev1.record(stream)
         ev1.synchronize()
         tot_ms += ev0.elapsed_time(ev1)
@@ -423,9 +430,14 @@ def run_genome(args):
         res += r
         eb += b
         ems += m
+        el += n
     nw.close()
     peaks, kind = measured_peaks()
     achieved = eb / (ems * 1e-3) / 1e9 if ems else 0.0
+    # DRAM traffic: the ratio ncu measured on one launch of this kernel,
+    # applied to this run's algorithmic bytes per launch
+    ratio = profile_figure("expand_kernel_genome.md", "dram_to_algorithmic_ratio")
+    traffic = ratio * eb / el if ratio and el else None
     line = {
         "metric": METRIC, "value": exp / (tot_ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -435,7 +447,8 @@ def run_genome(args):
         "balanced_pathways_per_s": res / (tot_ms * 1e-3),
         "roofline": {"kernel": "expand_kernel<32,7>", "bound": "hbm", "achieved": achieved,
                      "peak": float(peaks["hbm_gbs"]), "unit": "GB/s", "frac": achieved / float(peaks["hbm_gbs"]),
-                     "traffic": None, "peak_kind": f"{kind} HBM copy bandwidth"},
+                     "traffic": traffic, "peak_kind": f"{kind} HBM copy bandwidth", "launches": el,
+                     "avg_launch_ms": ems / max(el, 1), "alg_bytes_per_launch": eb / max(el, 1)},
     }
     print(json.dumps(line), flush=True)
 

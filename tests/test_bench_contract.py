@@ -21,3 +21,21 @@ def test_reference_arm_line():
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     assert "workload" in line["config"]
+
+
+def test_profile_figures_follow_the_kernel_source(tmp_path):
+    """A figure from an ncu summary is used only while the summary names the
+    current kernel source's hash; otherwise the bench reports null."""
+    import hashlib
+
+    import bench
+
+    src = os.path.join(ROOT, "paper_1804_02867_gb300", "csrc", "efm_kernels.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    f = tmp_path / "summary.md"
+    f.write_text(f"kernel_source_sha256_16: {sha}\ndram_to_algorithmic_ratio: 1.25\n")
+    assert bench.profile_figure(str(f), "dram_to_algorithmic_ratio") == 1.25
+    assert bench.profile_figure(str(f), "dram_bytes_per_launch_full_scale") is None
+    f.write_text("kernel_source_sha256_16: 0123456789abcdef\ndram_to_algorithmic_ratio: 1.25\n")
+    assert bench.profile_figure(str(f), "dram_to_algorithmic_ratio") is None
+    assert bench.profile_figure(str(tmp_path / "absent.md"), "dram_to_algorithmic_ratio") is None
