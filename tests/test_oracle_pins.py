@@ -8,7 +8,9 @@
   cycles of the reaction digraph, enumerated by networkx;
 * tiny random networks: every result is an elementary flux mode (exact
   sympy null space), and results are a subset of the brute-force EFM set;
-* the overflow rule on a chain whose flux grows by 4 per step.
+* the overflow rule on a chain whose flux grows by 4 per step;
+* the maximal network (the library's size limits): its chain target's
+  pathways and flux vectors in closed form.
 """
 import json
 import os
@@ -432,3 +434,51 @@ def test_python_walks_agree_with_c_walks(oracle_lib):
             got = [tuple(k for k in range(64) if (U >> k) & 1) for U in res]
             assert got == oracle_lib.supports_to_lists(sup), (seed, t)
             assert ctr == rctr, (seed, t, ctr, rctr)
+
+
+def test_maximal_network_chain_in_closed_form(oracle_lib):
+    """At the library's size limits (1024 internal metabolites, 4096 split
+    columns, 64-word supports, coefficients up to 524287) the target T of
+    the maximal network ends a linear chain, so its pathways are known by
+    construction: r_0..r_i closed by the side uptake of m_i (i = 10, 20, 30,
+    40, 50), and the whole chain r_0..r_62 closed by the uptake r_63.  Along
+    a chain each intermediate m_{j-1} balances its producer r_j against its
+    consumer r_{j-1}, so v_j = v_{j-1} * |S[m_{j-1}, r_{j-1}]| / S[m_{j-1}, r_j]
+    (Def. 3), scaled to the primitive integer vector."""
+    from fractions import Fraction
+    from math import gcd, lcm
+
+    from oracle import bruteforce, flux
+
+    net = synth.maximal()
+    S = net.dense()
+    T = net.targets[0]
+    rx, d = oracle_lib.column_map(net)
+    col = {(int(r), int(s)): k for k, (r, s) in enumerate(zip(rx, d))}
+    side = {10: 64, 20: 65, 30: 66, 40: 67, 50: 68}  # reactions of the side uptakes
+    closes = [(i, side[i]) for i in (10, 20, 30, 40, 50)] + [(62, 63)]
+    want_sup, want_flux = [], []
+    for i, last in closes:
+        rxns = list(range(i + 1)) + [last]
+        v = {0: Fraction(1)}
+        for j in range(1, i + 1):
+            v[j] = v[j - 1] * -S[j - 1, j - 1] / S[j - 1, j]
+        v[last] = v[i] * -S[i, i] / S[i, last]
+        den = lcm(*(x.denominator for x in v.values()))
+        ints = {r: int(x * den) for r, x in v.items()}
+        g = 0
+        for x in ints.values():
+            g = gcd(g, x)
+        cols = sorted(col[(r, 1)] for r in rxns)
+        by_col = {col[(r, 1)]: ints[r] // g for r in rxns}
+        want_sup.append(tuple(cols))
+        want_flux.append([by_col[c] for c in cols])
+    sup, ctr = oracle_lib.enumerate_pathways(net, T, oracle_lib.Limits(64, 4, 0, 0))
+    got = oracle_lib.supports_to_lists(sup)
+    assert [tuple(c) for c in got] == want_sup
+    assert ctr["status"] == 0 and ctr["results"] == 6
+    S_int, _, _ = bruteforce.split(net)
+    for cols, w in zip(got, want_flux):
+        rows = np.nonzero(np.any(S_int[:, list(cols)] != 0, axis=1))[0]
+        assert flux.flux_vector(S_int[rows], cols) == w
+    assert max(want_flux[-1]) == 6 * synth.MAX_COEF
