@@ -182,6 +182,21 @@ int efm_dependent_reactions(efm_net *net, int32_t depth, uint64_t *dep_out, uint
 #define EFM_FLUX_COLUMNS 64
 int efm_flux_vectors(efm_net *net, const uint64_t *supports, int64_t n, int64_t *flux, int8_t *status);
 
+/* Failure detection, on demand.  Every device-side wait of the library (a
+ * hash slot claimed by another warp but not yet published, a bulk copy's
+ * mbarrier) polls a bounded number of times; at the bound the kernel sets
+ * a timeout bit in its error word and returns, and the call reports
+ * EFM_ETIMEOUT.  This call takes that path on purpose: one kernel waits on
+ * a device flag that nothing sets, gives up after 2^20 polls (each with a
+ * short sleep; about a second in all) and flags the timeout, which
+ * the host maps as it maps a traversal's error word.  Nothing faults or
+ * hangs, and the network and its stream stay usable afterwards.
+ *  polls      receives the number of polls made (may be NULL)
+ *  waited_ms  receives the kernel's device time (may be NULL)
+ * Returns EFM_ETIMEOUT (the expected outcome), or EFM_EINVAL, EFM_ENOMEM,
+ * EFM_ECUDA.  Synchronous on the network's stream. */
+int efm_check_bounded_wait(efm_net *net, int64_t *polls, double *waited_ms);
+
 /* Monte-Carlo mode: the paper's own method (Alg. 3 with its random
  * choices, Theorem 1), in the exact integer form of the traversal.  Walk w
  * (0 <= w < n_walks) starts at a random seed column of the target and takes

@@ -996,6 +996,36 @@ extern "C" int efm_flux_vectors(efm_net *net, const uint64_t *supports, int64_t 
     return rc;
 }
 
+extern "C" int efm_check_bounded_wait(efm_net *net, int64_t *polls, double *waited_ms)
+{
+    if (!net) return EFM_EINVAL;
+    cudaStream_t s = net->stream;
+    DevBuf dbuf;  // flag (never set), padding, error word, poll count
+    if (!dev_alloc(dbuf, 32, s)) return EFM_ENOMEM;
+    unsigned long long h[2] = {0, 0};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = EFM_OK;
+    auto *base = (unsigned long long *)dbuf.p;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+        cudaMemsetAsync(dbuf.p, 0, 32, s) != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess ||
+        launch_stalled_wait((const uint32_t *)dbuf.p, base + 2, base + 3, s) != cudaSuccess ||
+        cudaEventRecord(e1, s) != cudaSuccess ||
+        cudaMemcpyAsync(h, base + 2, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        rc = EFM_ECUDA;
+    } else {
+        float ms = 0.f;
+        if (waited_ms) *waited_ms = cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess ? (double)ms : -1.0;
+        if (polls) *polls = (int64_t)h[1];
+        rc = err_from_bits(h[0]);  // the mapping every traversal's error word goes through
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dev_free(dbuf, s);
+    return rc;
+}
+
 extern "C" int efm_sample_pathways(efm_net *net, int32_t target, const efm_limits *limits, uint64_t seed,
                                    int64_t n_walks, efm_job **out)
 {

@@ -20,6 +20,7 @@ constexpr int kStageLimitBytes = 72 * 1024;  // static network staged in smem up
 constexpr int64_t kFirstKChunkMin = 8192;     // first-K search: fewest parents per expansion launch
 constexpr int64_t kFirstKChunks = 32;         // first-K search: launches per level, at most
 constexpr int64_t kResultWindow = 256;        // first-K search: new results fetched with the counters
+constexpr int kWaitSpinLimit = 1 << 20;       // polls of a bounded device-side wait (with ~0.25 us sleeps)
 
 // device error bits (ctr[C_ERR])
 enum : unsigned { ERR_TIMEOUT = 1u, ERR_CAND_CAP = 2u, ERR_RES_CAP = 4u, ERR_TABLE_FULL = 8u,
@@ -194,6 +195,9 @@ cudaError_t launch_step_count(const NetView &nv, unsigned *r, cudaStream_t s);
 cudaError_t launch_or_words(uint64_t *a, const uint64_t *b, int64_t n, cudaStream_t s);
 cudaError_t launch_depthy(const NetView &nv, int L, unsigned r, unsigned long long n_paths, unsigned long long *dep_out,
                           unsigned long long *dep_in, int sm_count, cudaStream_t s);
+// one thread waits on `flag` for kWaitSpinLimit polls; ERR_TIMEOUT in *err if it stays 0
+cudaError_t launch_stalled_wait(const uint32_t *flag, unsigned long long *err, unsigned long long *polls,
+                                cudaStream_t s);
 cudaError_t launch_flux(const NetView &nv, const uint64_t *sup, int64_t n, int64_t *flux, int8_t *status, int sm_count,
                         cudaStream_t s);
 cudaError_t launch_walks(const NetView &nv, const LevelArgs &a, int target, uint64_t seed, int64_t n_walks, int sm_count,

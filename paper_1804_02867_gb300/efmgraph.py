@@ -24,7 +24,7 @@ EXPORTS = ("efm_load_network", "efm_network_shape", "efm_column_map", "efm_find_
            "efm_sort_supports_noalloc", "efm_find_pathways_batch", "efm_batch_tuning", "efm_model_create",
            "efm_model_params", "efm_model_add_rows", "efm_model_rows", "efm_model_clear_rows", "efm_model_forward",
            "efm_model_gradient", "efm_model_train", "efm_model_trace", "efm_model_free", "efm_sample_pathways",
-           "efm_flux_vectors", "efm_find_pathways_from", "efm_dependent_reactions")
+           "efm_flux_vectors", "efm_find_pathways_from", "efm_dependent_reactions", "efm_check_bounded_wait")
 EFM_NOALLOC_MAX_ROWS = 1 << 20
 EFM_MLP_FEATURES, EFM_MLP_HIDDEN = 128, 256
 EFM_MLP_PARAMS = 256 * 128 + 256 + 1
@@ -124,6 +124,8 @@ def load_library(path: str | None = None):
     lib.efm_sample_pathways.argtypes = [ctypes.c_void_p, ctypes.c_int32, _P(efm_limits), ctypes.c_uint64,
                                         ctypes.c_int64, _P(ctypes.c_void_p)]
     lib.efm_sample_pathways.restype = ctypes.c_int
+    lib.efm_check_bounded_wait.argtypes = [ctypes.c_void_p, _P(ctypes.c_int64), _P(ctypes.c_double)]
+    lib.efm_check_bounded_wait.restype = ctypes.c_int
     lib.efm_model_free.argtypes = [ctypes.c_void_p]
     lib.efm_model_free.restype = None
     _lib = lib
@@ -259,6 +261,18 @@ def efm_flux_vectors(net, supports):
     if rc != 0:
         raise EfmError(rc, "efm_flux_vectors")
     return flux[:n], st[:n]
+
+
+def efm_check_bounded_wait(net):
+    """Run the library's bounded-wait failure path once (a device wait on a
+    flag that nothing sets).  Returns (status, polls, waited_ms); the status
+    is EFM_ETIMEOUT (-4) when the wait gave up, as it should.  Other
+    errors raise EfmError."""
+    polls, ms = ctypes.c_int64(), ctypes.c_double()
+    rc = load_library().efm_check_bounded_wait(net, ctypes.byref(polls), ctypes.byref(ms))
+    if rc < 0 and rc != -4:
+        raise EfmError(rc, "efm_check_bounded_wait")
+    return rc, polls.value, ms.value
 
 
 def efm_sample_pathways(net, target, max_len, max_secondary, seed, n_walks):

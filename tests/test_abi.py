@@ -89,3 +89,18 @@ def test_load_network_rejects_out_of_range_sizes_on_the_host(lib):
     coef = net.coef.copy()
     coef[0] = 0
     assert load(coef=coef) == -1
+
+
+def test_wait_bounds_agree_and_null_handles_are_refused(lib):
+    """The traversal kernels' poll bound equals the one the failure-path
+    check runs (both 2^20), and the check refuses a null network on the host."""
+    from paper_1804_02867_gb300 import efmgraph
+
+    with open(os.path.join(ROOT, "paper_1804_02867_gb300", "csrc", "efm_kernels.cu")) as f:
+        kern = re.search(r"constexpr int kSpinLimit = ([^;]+);", f.read()).group(1)
+    with open(os.path.join(ROOT, "paper_1804_02867_gb300", "csrc", "efm_internal.cuh")) as f:
+        shared = re.search(r"constexpr int kWaitSpinLimit = ([^;]+);", f.read()).group(1)
+    assert kern.strip() == shared.strip() == "1 << 20"
+    with pytest.raises(efmgraph.EfmError) as e:
+        efmgraph.efm_check_bounded_wait(None)
+    assert e.value.code == -1
