@@ -20,7 +20,9 @@ def test_reference_arm_line():
     assert line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
-    assert "workload" in line["config"]
+    import bench
+
+    assert line["config"] == bench.workload_config(bench.BUDGET)  # the GPU arm's workload
 
 
 def test_profile_figures_follow_the_kernel_source(tmp_path):
