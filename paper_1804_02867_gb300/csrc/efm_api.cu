@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "efm_internal.cuh"
+#include "efm_topk.h"
 
 using namespace efm;
 
@@ -429,54 +430,7 @@ int err_from_bits(unsigned long long e)
 // The K smallest results found so far by a first-K search (output order:
 // |U|, then the ascending column list), kept on the host; the K-th is the
 // branch-and-bound of the next expansion launches.
-struct TopK {
-    int K = 0, W = 0;
-    std::vector<uint64_t> rows;  // at most K rows once K were found
-    int pc = 0;                  // |U| of the K-th (0 while fewer than K)
-    std::vector<uint64_t> kth;
 
-    static int popc(const uint64_t *r, int W)
-    {
-        int c = 0;
-        for (int w = 0; w < W; ++w) c += __builtin_popcountll(r[w]);
-        return c;
-    }
-    static bool less(const uint64_t *x, const uint64_t *y, int W)
-    {
-        const int cx = popc(x, W), cy = popc(y, W);
-        if (cx != cy) return cx < cy;
-        for (int w = 0; w < W; ++w) {
-            const uint64_t d = x[w] ^ y[w];
-            if (d) return (x[w] & (d & (~d + 1))) != 0;
-        }
-        return false;
-    }
-    void add(const uint64_t *r, int64_t n)
-    {
-        rows.insert(rows.end(), r, r + (size_t)n * W);
-        const int64_t have = (int64_t)(rows.size() / W);
-        if (have < K) return;
-        std::vector<int64_t> idx((size_t)have);
-        for (int64_t i = 0; i < have; ++i) idx[i] = i;
-        const uint64_t *base = rows.data();
-        const int Wl = W;
-        std::nth_element(idx.begin(), idx.begin() + (K - 1), idx.end(), [&](int64_t i, int64_t j) {
-            return less(base + i * Wl, base + j * Wl, Wl);
-        });
-        std::vector<uint64_t> keep((size_t)K * W);
-        for (int i = 0; i < K; ++i) std::copy(base + idx[i] * W, base + idx[i] * W + W, keep.begin() + (size_t)i * W);
-        kth.assign(base + idx[K - 1] * W, base + idx[K - 1] * W + W);
-        rows.swap(keep);
-        pc = popc(kth.data(), W);
-    }
-};
-
-// One (network, target) traversal.  Level 0 = seeds; level l expands F_{l-1}.
-// With limits.first_k = K > 0 the traversal is the same, with each level's
-// frontier expanded in chunks (in the order the proposal gives) and an exact
-// branch and bound between chunks: once K results are known, a child that
-// would follow the K-th of them in the output order is not generated, since
-// every descendant keeps or grows its support.
 // DEPTHy tags of the network for the model's features: the deepest walk
 // length (at most 3) whose enumeration stays under 2^26 walks per
 // metabolite; dep_out | dep_in per internal metabolite.  Computed once.
@@ -528,6 +482,12 @@ struct Trace {
 
 bool model_reserve_rows(efm_model *m, int64_t rows);
 
+// One (network, target) traversal.  Level 0 = seeds; level l expands F_{l-1}.
+// With limits.first_k = K > 0 the traversal is the same, with each level's
+// frontier expanded in chunks (in the order the proposal gives) and an exact
+// branch and bound between chunks: once K results are known, a child that
+// would follow the K-th of them in the output order is not generated, since
+// every descendant keeps or grows its support.
 // seedset (device, n_seedset columns): start from that one state instead of
 // the target's seeds (Prop. 1), at level n_seedset - 1.
 int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetOut &out,
