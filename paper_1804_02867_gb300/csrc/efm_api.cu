@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "efm_internal.cuh"
+#include "efm_netprep.h"
 #include "efm_topk.h"
 
 using namespace efm;
@@ -53,15 +54,6 @@ void dev_free(DevBuf &b, cudaStream_t s)
         cudaFreeAsync(b.p, s);
     b.p = nullptr;
     b.bytes = 0;
-}
-
-int pick_epl(int M)
-{
-    const int need = std::max(1, (M + 31) / 32);
-    const int opts[] = {1, 2, 4, 8, 16, 28, 32};
-    for (int o : opts)
-        if (o >= need) return o;
-    return -1;
 }
 
 uint64_t next_pow2(uint64_t x)
@@ -151,124 +143,37 @@ extern "C" int efm_load_network(int32_t n_met, int32_t n_rxn, const int32_t *row
 {
     if (!out) return EFM_EINVAL;
     *out = nullptr;
-    if (n_met <= 0 || n_rxn <= 0 || !row_ptr || !reversible || !external) return EFM_EINVAL;
-    if (row_ptr[0] != 0) return EFM_EINVAL;
-    const int64_t nnz = row_ptr[n_met];
-    if (nnz > 0 && (!col_idx || !coef)) return EFM_EINVAL;
-    std::vector<int32_t> mark(n_rxn, -1);
-    for (int m = 0; m < n_met; ++m) {
-        if (row_ptr[m + 1] < row_ptr[m]) return EFM_EINVAL;
-        for (int p = row_ptr[m]; p < row_ptr[m + 1]; ++p) {
-            const int j = col_idx[p];
-            if (j < 0 || j >= n_rxn) return EFM_EINVAL;
-            if (coef[p] == 0 || coef[p] > EFM_MAX_COEF || coef[p] < -EFM_MAX_COEF) return EFM_EINVAL;
-            if (mark[j] == m) return EFM_EINVAL;  // duplicate entry in a row
-            mark[j] = m;
-        }
-    }
+    NetPrep prep;
+    const int prc = prepare_network(n_met, n_rxn, row_ptr, col_idx, coef, reversible, external, prep);
+    if (prc != EFM_OK) return prc;
     auto *net = new (std::nothrow) efm_net();
     if (!net) return EFM_ENOMEM;
     net->n_met = n_met;
     net->n_rxn = n_rxn;
     net->stream = (cudaStream_t)cuda_stream;
-    // split columns (direction of Def. 6): forward, then reverse if reversible
-    std::vector<int> first_col(n_rxn);
-    int N = 0;
-    for (int j = 0; j < n_rxn; ++j) {
-        first_col[j] = N;
-        net->col_rxn.push_back(j);
-        net->col_dir.push_back(1);
-        ++N;
-        if (reversible[j]) {
-            net->col_rxn.push_back(j);
-            net->col_dir.push_back(-1);
-            ++N;
-        }
-    }
-    std::vector<int> int_row(n_met, -1);
-    int M = 0;
-    for (int m = 0; m < n_met; ++m)
-        if (!external[m]) int_row[m] = M++;
-    const int EPL = pick_epl(M);
-    if (N > EFM_MAX_COLUMNS || M > EFM_MAX_INTERNAL || EPL < 0) {
-        delete net;
-        return EFM_EINVAL;
-    }
-    // S_int by column (rows ascending) and by internal row (columns ascending)
-    std::vector<std::vector<std::pair<int, int32_t>>> col(N), cons(M), prod(M);
-    std::vector<std::vector<std::pair<int, int32_t>>> metrow(n_met);
-    for (int m = 0; m < n_met; ++m) {
-        for (int p = row_ptr[m]; p < row_ptr[m + 1]; ++p) {
-            const int j = col_idx[p];
-            const int f = first_col[j];
-            metrow[m].push_back({f, coef[p]});
-            if (reversible[j]) metrow[m].push_back({f + 1, -coef[p]});
-            if (int_row[m] < 0) continue;
-            col[f].push_back({int_row[m], coef[p]});
-            if (reversible[j]) col[f + 1].push_back({int_row[m], -coef[p]});
-        }
-    }
-    std::vector<uint32_t> hbits(N, 0);
-    for (int k = 0; k < N; ++k) {
-        std::sort(col[k].begin(), col[k].end());
-        uint64_t nsq = 0;
-        for (auto &e : col[k]) {
-            nsq += (uint64_t)((int64_t)e.second * e.second);
-            if (e.second < 0) cons[e.first].push_back({k, -e.second});
-            if (e.second > 0) prod[e.first].push_back({k, e.second});
-        }
-        hbits[k] = nsq <= 1 ? 0u : (uint32_t)(64 - __builtin_clzll(nsq - 1));
-    }
-    // blob assembly
-    std::vector<uint32_t> blob;
+    net->col_rxn = prep.col_rxn;
+    net->col_dir = prep.col_dir;
+    const std::vector<uint32_t> &blob = prep.blob;
+    const std::vector<int32_t> &mptr = prep.mptr;
+    const std::vector<uint32_t> &ment = prep.ment;
     NetView &nv = net->nv;
-    auto put_csr = [&](std::vector<std::vector<std::pair<int, int32_t>>> &lists, int &o_ptr, int &o_ent) {
-        o_ptr = (int)blob.size();
-        uint32_t acc = 0;
-        for (auto &l : lists) {
-            blob.push_back(acc);
-            acc += (uint32_t)l.size();
-        }
-        blob.push_back(acc);
-        o_ent = (int)blob.size();
-        for (auto &l : lists)
-            for (auto &e : l) blob.push_back(ent_pack(e.first, e.second));
-    };
-    put_csr(col, nv.o_colptr, nv.o_colent);
-    put_csr(cons, nv.o_consptr, nv.o_consent);
-    put_csr(prod, nv.o_prodptr, nv.o_prodent);
-    nv.o_twin = (int)blob.size();
-    for (int k = 0; k < N; ++k) {
-        int tw = -1;
-        if (k + 1 < N && net->col_rxn[k + 1] == net->col_rxn[k]) tw = k + 1;
-        if (k > 0 && net->col_rxn[k - 1] == net->col_rxn[k]) tw = k - 1;
-        blob.push_back((uint32_t)tw);
-    }
-    nv.o_keypos = (int)blob.size();
-    for (int r = 0; r < M; ++r) blob.push_back(((uint32_t)cons[r].size() << 16) | (uint32_t)r);
-    nv.o_keyneg = (int)blob.size();
-    for (int r = 0; r < M; ++r) blob.push_back(((uint32_t)prod[r].size() << 16) | (uint32_t)r);
-    nv.o_hbits = (int)blob.size();
-    for (int k = 0; k < N; ++k) blob.push_back(hbits[k]);
-    while (blob.size() % 4) blob.push_back(0);
-    // dense column-major copy of S_int (row k = column k over Mpad rows)
-    nv.o_dcols = (int)blob.size();
-    blob.resize(blob.size() + (size_t)N * 32 * EPL, 0u);
-    for (int k = 0; k < N; ++k)
-        for (auto &e : col[k]) blob[(size_t)nv.o_dcols + (size_t)k * 32 * EPL + e.first] = (uint32_t)e.second;
-    std::vector<int32_t> mptr(n_met + 1, 0);
-    std::vector<uint32_t> ment;
-    for (int m = 0; m < n_met; ++m) {
-        for (auto &e : metrow[m]) ment.push_back(ent_pack(e.first, e.second));
-        mptr[m + 1] = (int32_t)ment.size();
-    }
-    if (ment.empty()) ment.push_back(0);
+    nv.o_colptr = prep.o_colptr;
+    nv.o_colent = prep.o_colent;
+    nv.o_consptr = prep.o_consptr;
+    nv.o_consent = prep.o_consent;
+    nv.o_prodptr = prep.o_prodptr;
+    nv.o_prodent = prep.o_prodent;
+    nv.o_twin = prep.o_twin;
+    nv.o_keypos = prep.o_keypos;
+    nv.o_keyneg = prep.o_keyneg;
+    nv.o_hbits = prep.o_hbits;
+    nv.o_dcols = prep.o_dcols;
     nv.blob_words = (int)blob.size();
-    nv.M = M;
-    nv.N = N;
-    nv.W = (N + 63) / 64;
-    nv.EPL = EPL;
-    nv.Mpad = 32 * EPL;
+    nv.M = prep.M;
+    nv.N = prep.N;
+    nv.W = prep.W;
+    nv.EPL = prep.EPL;
+    nv.Mpad = prep.Mpad;
     nv.n_met = n_met;
     cudaStream_t s = net->stream;
     int rc = EFM_OK;

@@ -62,9 +62,6 @@ struct NetView {
 
 __host__ __device__ inline int ent_index(uint32_t e) { return (int)(e >> 20); }
 __host__ __device__ inline int32_t ent_coef(uint32_t e) { return ((int32_t)(e << 12)) >> 12; }
-__host__ inline uint32_t ent_pack(int idx, int32_t coef) {
-    return ((uint32_t)idx << 20) | ((uint32_t)coef & 0xFFFFFu);
-}
 
 // One arena of pathway states, structure of arrays.
 struct Arena {

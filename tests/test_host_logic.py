@@ -1,5 +1,13 @@
 """Host logic of the library, without a GPU.
 
+The loader's host work (csrc/efm_netprep.h) validates S and builds the
+static network the kernels read; compiled alone with g++, its decoded output
+must equal what the definitions give on seeded networks: split columns
+(forward, then reverse for a reversible reaction), S_int by column, the
+consumers and producers of each internal metabolite, twins, pivot keys,
+Hadamard bits, the dense copy and the full rows over split columns; and it
+must refuse every malformed input.
+
 The first-K search keeps, on the host, the K smallest results seen so far in
 the output order (|U|, then the ascending column list) and hands the K-th of
 them to the kernels as the bound (efm::TopK, csrc/efm_topk.h).  Here that
@@ -18,15 +26,128 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_1804_02867_gb300", "csrc")
 
 
-@pytest.fixture(scope="module")
-def driver(tmp_path_factory):
+def _compile(tmp_path_factory, name):
     gxx = shutil.which("g++")
     if gxx is None:
         pytest.skip("g++ not available")
-    exe = str(tmp_path_factory.mktemp("topk") / "topk_driver")
-    subprocess.run([gxx, "-std=c++17", "-O1", "-I", CSRC, os.path.join(ROOT, "tests", "host", "topk_driver.cpp"),
+    exe = str(tmp_path_factory.mktemp(name) / name)
+    subprocess.run([gxx, "-std=c++17", "-O1", "-I", CSRC, os.path.join(ROOT, "tests", "host", name + ".cpp"),
                     "-o", exe], check=True)
     return exe
+
+
+@pytest.fixture(scope="module")
+def driver(tmp_path_factory):
+    return _compile(tmp_path_factory, "topk_driver")
+
+
+@pytest.fixture(scope="module")
+def netprep(tmp_path_factory):
+    return _compile(tmp_path_factory, "netprep_driver")
+
+
+def run_netprep(exe, n_met, n_rxn, row_ptr, col_idx, coef, reversible, external):
+    vals = [n_met, n_rxn, *row_ptr, *col_idx, *coef, *reversible, *external]
+    out = subprocess.run([exe], input=" ".join(str(int(v)) for v in vals) + "\n", capture_output=True, text=True,
+                         check=True).stdout.splitlines()
+    status = int(out[0].split()[1])
+    items = {}
+    for ln in out[1:]:
+        f = ln.split()
+        items.setdefault(f[0], []).append(f[1:])
+    return status, items
+
+
+def expected_static(net):
+    """The static network by its definitions, from the dense S."""
+    S = net.dense()
+    cols, cmap = [], []
+    for j in range(net.n_rxn):
+        cols.append(S[:, j])
+        cmap.append((j, 1))
+        if net.reversible[j]:
+            cols.append(-S[:, j])
+            cmap.append((j, -1))
+    Ss = np.stack(cols, axis=1)
+    internal = [m for m in range(net.n_met) if not net.external[m]]
+    Si = Ss[internal]
+    M, N = Si.shape
+    epl = min(e for e in (1, 2, 4, 8, 16, 28, 32) if e >= max(1, -(-M // 32)))
+    exp = {"shape": [N, M, -(-N // 64), epl, 32 * epl], "colmap": cmap}
+    exp["col"] = [[(r, int(Si[r, k])) for r in range(M) if Si[r, k]] for k in range(N)]
+    exp["cons"] = [[(k, int(-Si[r, k])) for k in range(N) if Si[r, k] < 0] for r in range(M)]
+    exp["prod"] = [[(k, int(Si[r, k])) for k in range(N) if Si[r, k] > 0] for r in range(M)]
+    exp["twin"] = [next((q for q in (k - 1, k + 1) if 0 <= q < N and cmap[q][0] == cmap[k][0]), -1)
+                   for k in range(N)]
+    exp["key"] = [((len(exp["cons"][r]) << 16) | r, (len(exp["prod"][r]) << 16) | r) for r in range(M)]
+    nsq = [int(sum(int(x) ** 2 for x in Si[:, k])) for k in range(N)]
+    exp["hbits"] = [(q - 1).bit_length() if q > 1 else 0 for q in nsq]  # ceil(log2(q))
+    exp["dense"] = [list(Si[:, k]) + [0] * (32 * epl - M) for k in range(N)]
+    exp["met"] = [[(k, int(Ss[m, k])) for k in range(N) if Ss[m, k]] for m in range(net.n_met)]
+    return exp
+
+
+def _pairs(fields):
+    return [tuple(int(x) for x in f.split(":")) for f in fields]
+
+
+@pytest.mark.parametrize("which", ["tiny-0", "tiny-5", "core", "batched-7", "type1-3", "mid-40"])
+def test_network_preparation_matches_the_definitions(netprep, which):
+    from paper_1804_02867_gb300 import synth
+
+    net = {"tiny-0": lambda: synth.tiny(0), "tiny-5": lambda: synth.tiny(5), "core": synth.core,
+           "batched-7": lambda: synth.batched_member(7), "type1-3": lambda: synth.type1(3),
+           "mid-40": lambda: synth.generate(n_int=40, n_targets=3, n_hubs=2, n_substrates=1, n_rxn=70, n_rev=20,
+                                            coef_probs={1: 0.5, 3: 0.3, 524287: 0.2}, seed=7)}[which]()
+    status, got = run_netprep(netprep, net.n_met, net.n_rxn, net.row_ptr, net.col_idx, net.coef, net.reversible,
+                              net.external)
+    assert status == 0
+    exp = expected_static(net)
+    N, M = exp["shape"][0], exp["shape"][1]
+    assert [int(x) for x in got["shape"][0]] == exp["shape"]
+    assert [(int(f[1]), int(f[2])) for f in got["colmap"]] == exp["colmap"]
+    for name, n in (("col", N), ("cons", M), ("prod", M)):
+        rows = got.get(name, [])
+        assert [int(f[0]) for f in rows] == list(range(n))
+        assert [_pairs(f[1:]) for f in rows] == exp[name], name
+    assert [int(f[1]) for f in got["twin"]] == exp["twin"]
+    assert [(int(f[1]), int(f[2])) for f in got.get("key", [])] == exp["key"]
+    assert [int(f[1]) for f in got["hbits"]] == exp["hbits"]
+    assert got["dense_offset_mod4"] == [["0"]]
+    assert [[int(x) for x in f[1:]] for f in got["dense"]] == exp["dense"]
+    assert [_pairs(f[1:]) for f in got["met"]] == exp["met"]
+
+
+def test_network_preparation_refuses_malformed_input(netprep):
+    from paper_1804_02867_gb300 import synth
+
+    net = synth.tiny(1)
+    args = [net.n_met, net.n_rxn, net.row_ptr, net.col_idx, net.coef, net.reversible, net.external]
+
+    def status(**change):
+        a = dict(zip(("n_met", "n_rxn", "row_ptr", "col_idx", "coef", "reversible", "external"), args))
+        a.update(change)
+        return run_netprep(netprep, *a.values())[0]
+
+    assert status() == 0
+    coef = net.coef.copy()
+    coef[3] = 0
+    assert status(coef=coef) == -1  # explicit zero
+    coef[3] = 524288
+    assert status(coef=coef) == -1  # beyond the coefficient limit
+    col = net.col_idx.copy()
+    col[2] = net.n_rxn
+    assert status(col_idx=col) == -1  # reaction index out of range
+    col = net.col_idx.copy()
+    r0 = next(m for m in range(net.n_met) if net.row_ptr[m + 1] - net.row_ptr[m] >= 2)
+    col[net.row_ptr[r0] + 1] = col[net.row_ptr[r0]]
+    assert status(col_idx=col) == -1  # duplicate entry in a row
+    rp = net.row_ptr.copy()
+    rp[2], rp[3] = rp[3], rp[2]
+    assert status(row_ptr=rp) == -1 or rp[2] == rp[3]  # decreasing row pointer
+    rp = net.row_ptr.copy()
+    rp[0] = 1
+    assert status(row_ptr=rp) == -1  # row_ptr[0] != 0
 
 
 def columns(row):
