@@ -482,3 +482,46 @@ def test_maximal_network_chain_in_closed_form(oracle_lib):
         rows = np.nonzero(np.any(S_int[:, list(cols)] != 0, axis=1))[0]
         assert flux.flux_vector(S_int[rows], cols) == w
     assert max(want_flux[-1]) == 6 * synth.MAX_COEF
+
+
+def test_walks_choose_uniformly_among_valid_branches(oracle_lib):
+    """The Monte-Carlo mode takes one valid OR branch per step, each with the
+    same probability (Alg. 3's random input, Theorem 1).  On a chain with
+    side uptakes the probability of each result is a closed form: target T
+    is made from m_0 by r0; m_{i-1} from m_i by r_i (i = 1..5); m_5 from the
+    uptake X by r6; m_1 and m_3 each have one more producer (an uptake of Y),
+    m_4 two more.  A walk ends at m_1 with probability 1/2, at m_3 with 1/4,
+    and at m_4 with 1/12 for each of its three producers (two uptakes, and
+    r5 followed by the forced r6).  6000 walks, one generator key each, must
+    fit these probabilities (chi-square, 4 degrees of freedom, p > 1e-4)."""
+    n_int, T, X, Y = 6, 6, 7, 8
+    cols = []
+
+    def rxn(*entries):
+        c = np.zeros(9, dtype=np.int64)
+        for m, v in entries:
+            c[m] = v
+        cols.append(c)
+
+    rxn((0, -1), (T, 1))
+    for i in range(1, 6):
+        rxn((i, -1), (i - 1, 1))
+    rxn((X, -1), (5, 1))
+    for m in (1, 3, 4, 4):
+        rxn((Y, -1), (m, 1))
+    S = np.stack(cols, axis=1)
+    ext = np.zeros(9, dtype=np.uint8)
+    ext[n_int:] = 1
+    net = synth.Network.from_dense(S, np.zeros(S.shape[1], np.uint8), ext)
+    lists = {(0, 1, 7): 0, (0, 1, 2, 3, 8): 1, (0, 1, 2, 3, 4, 9): 2, (0, 1, 2, 3, 4, 10): 3,
+             (0, 1, 2, 3, 4, 5, 6): 4}
+    probs = np.array([1 / 2, 1 / 4, 1 / 12, 1 / 12, 1 / 12])
+    counts = np.zeros(5)
+    n = 6000
+    for seed in range(n):
+        sup, ctr = oracle_lib.sample_pathways(net, T, oracle_lib.Limits(20, 0), seed, 1)
+        assert ctr["balanced"] == 1 and len(sup) == 1
+        counts[lists[tuple(oracle_lib.supports_to_lists(sup)[0])]] += 1
+    expected = n * probs
+    chi2 = float(((counts - expected) ** 2 / expected).sum())
+    assert chi2 < 23.5, (counts, expected, chi2)  # 23.5 = chi-square(4) quantile at 1 - 1e-4
