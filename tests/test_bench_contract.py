@@ -25,6 +25,15 @@ def test_reference_arm_line():
     assert line["config"] == bench.workload_config(bench.BUDGET)  # the GPU arm's workload
 
 
+def test_reference_arm_other_ranks_exit_quietly():
+    """Under torchrun only rank 0 runs the reference arm and prints its line;
+    the other ranks exit 0 without work or output."""
+    env = dict(os.environ, RANK="1", LOCAL_RANK="1", WORLD_SIZE="2")
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1",
+                        "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=600, env=env)
+    assert r.returncode == 0 and r.stdout.strip() == ""
+
+
 def test_profile_figures_follow_the_kernel_source(tmp_path):
     """A figure from an ncu summary is used only while the summary names the
     current kernel source's hash; otherwise the bench reports null."""
