@@ -276,19 +276,21 @@ void efm_free_net(efm_net *net);
 /* Sort supports into the output order of efm_fetch_results (by |U|, then
  * ascending column list) WITHOUT allocating any memory.  The paper has no
  * counterpart; this is for callers that cannot allocate where they sort:
- * work recorded during CUDA stream capture (allocation is not allowed
- * there), code whose device memory is owned by another framework's
- * allocator, or loops that must never wait on an allocator.
+ * code whose device memory is owned by another framework's allocator (a
+ * private cudaMalloc would escape its accounting), or loops that must never
+ * wait on an allocator.
  *  supports_in   device pointer, n_rows x words_per_set uint64 (caller-owned)
- *  supports_out  device pointer, same size, must not alias supports_in
+ *  supports_out  device pointer, same size; its bytes must not overlap the
+ *                input's
  *  cuda_stream   stream the sort runs on (asynchronous; no host sync)
  * The only scratch, an index array, is a file-scope device array of
  * EFM_NOALLOC_MAX_ROWS entries (4 MiB) held by every GPU that loads the
  * library until exit.  All calls share it: calls whose GPU work overlaps
  * (unordered streams) race and may return wrong orders.  The first call on
- * a device looks up the array's address; make it before any stream capture.
+ * a device (and the first after its context changed) looks up the array's
+ * address in the current context; make it before any stream capture.
  * Errors: EFM_ECAPACITY if n_rows > EFM_NOALLOC_MAX_ROWS; EFM_EINVAL for
- * words_per_set outside 1..64, NULL or aliased buffers; EFM_ECUDA. */
+ * words_per_set outside 1..64, NULL or overlapping buffers; EFM_ECUDA. */
 #define EFM_NOALLOC_MAX_ROWS (1 << 20)
 int efm_sort_supports_noalloc(const uint64_t *supports_in, int64_t n_rows, int32_t words_per_set,
                               uint64_t *supports_out, uintptr_t cuda_stream);

@@ -29,7 +29,11 @@ COUNTER_FIELDS = ("levels", "seeds", "expansions", "overflow", "balanced", "cand
 
 class _Limits(ctypes.Structure):
     _fields_ = [("max_len", ctypes.c_int32), ("max_secondary", ctypes.c_int32),
-                ("max_results", ctypes.c_int64), ("max_frontier", ctypes.c_int64)]
+                ("max_results", ctypes.c_int64), ("max_frontier", ctypes.c_int64),
+                ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+NO_PRUNE = 1  # _Limits.flags: skip the superset rule (the plain definition)
 
 
 class _Counters(ctypes.Structure):
@@ -42,6 +46,11 @@ class Limits:
     max_secondary: int = 4
     max_results: int = 0
     max_frontier: int = 0
+    prune: bool = True  # False: no superset rule, the definition alone
+
+    def c_struct(self) -> "_Limits":
+        return _Limits(self.max_len, self.max_secondary, self.max_results, self.max_frontier,
+                       0 if self.prune else NO_PRUNE, 0)
 
 
 def build(force: bool = False) -> str:
@@ -104,7 +113,7 @@ def enumerate_pathways(net, target: int, limits: Limits):
     cf = np.ascontiguousarray(net.coef, dtype=np.int32)
     rv = np.ascontiguousarray(net.reversible, dtype=np.uint8)
     ex = np.ascontiguousarray(net.external, dtype=np.uint8)
-    lim = _Limits(limits.max_len, limits.max_secondary, limits.max_results, limits.max_frontier)
+    lim = limits.c_struct()
     out = ctypes.POINTER(ctypes.c_uint64)()
     n = ctypes.c_int64(0)
     W = ctypes.c_int32(0)
@@ -137,7 +146,7 @@ def enumerate_from(net, columns, limits: Limits):
     rv = np.ascontiguousarray(net.reversible, dtype=np.uint8)
     ex = np.ascontiguousarray(net.external, dtype=np.uint8)
     cols = np.ascontiguousarray(columns, dtype=np.int32)
-    lim = _Limits(limits.max_len, limits.max_secondary, limits.max_results, limits.max_frontier)
+    lim = limits.c_struct()
     out = ctypes.POINTER(ctypes.c_uint64)()
     n = ctypes.c_int64(0)
     W = ctypes.c_int32(0)
@@ -167,7 +176,7 @@ def sample_pathways(net, target: int, limits: Limits, seed: int, n_walks: int):
     cf = np.ascontiguousarray(net.coef, dtype=np.int32)
     rv = np.ascontiguousarray(net.reversible, dtype=np.uint8)
     ex = np.ascontiguousarray(net.external, dtype=np.uint8)
-    lim = _Limits(limits.max_len, limits.max_secondary, 0, 0)
+    lim = Limits(limits.max_len, limits.max_secondary, 0, 0).c_struct()
     out = ctypes.POINTER(ctypes.c_uint64)()
     n = ctypes.c_int64(0)
     W = ctypes.c_int32(0)

@@ -49,7 +49,10 @@
  *    - a non-balanced child whose new column k completes the support of a
  *      result accepted at a level < l (k in E, E contained in U + {k}) is
  *      pruned: any balanced descendant would contain that result, so it could
- *      not be minimal (secondary steps, k already in U, are never pruned);
+ *      not be minimal (secondary steps, k already in U, are never pruned).
+ *      The rule is an optimisation, not part of the definition (Def. 3 only
+ *      asks for nullity 1): with flags & OR_NO_PRUNE it is skipped, and the
+ *      result set must not change (pinned by the tests);
  *    - F_l = distinct (U, EF) among the remaining children (equal keys at
  *      one level have equal sec);
  *    - if |F_l| > max_frontier (> 0): status TRUNCATED, stop; results of
@@ -72,11 +75,16 @@
 #define OR_CAPPED 2
 #define OR_OVERFLOW_DROPPED 4
 
+/* or_limits.flags */
+#define OR_NO_PRUNE 1 /* the plain definition: no superset rule */
+
 typedef struct {
     int32_t max_len;
     int32_t max_secondary;
     int64_t max_results;
     int64_t max_frontier;
+    int32_t flags; /* OR_* bits above */
+    int32_t reserved;
 } or_limits;
 
 typedef struct {
@@ -896,7 +904,10 @@ static int enumerate_impl(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, 
                 if (!in_u && pc + 1 > lim->max_len) continue;
                 if (in_u && sec + 1 > lim->max_secondary) continue;
                 ctr->expansions++;
-                /* Eq. 3 in integers */
+                /* Eq. 3 in integers.  No int64 overflow: |EF[i]| <= 2^31 - 1
+                 * (normalise() drops wider rows), a <= |S_ik| <= 2^31 - 1 and
+                 * c <= |EF_i| (net_build() refuses INT32_MIN), so each product is
+                 * below 2^62 and the sum below 2^63. */
                 const uint64_t g0 = gcd_u64(abs_i64(ef_i), abs_i64(s_ik));
                 const int64_t a = (int64_t)(abs_i64(s_ik) / g0);
                 const int64_t c = (int64_t)(abs_i64(ef_i) / g0);
@@ -915,7 +926,7 @@ static int enumerate_impl(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, 
                     if ((rc = judge(&R, U2, level)) != OR_OK) goto done;
                     continue;
                 }
-                if (!in_u && completes_result(&R, U2, k, level)) {
+                if (!in_u && !(lim->flags & OR_NO_PRUNE) && completes_result(&R, U2, k, level)) {
                     ctr->pruned++;
                     continue;
                 }

@@ -76,11 +76,13 @@ def _normalise(ef):
     return tuple(x // g for x in ef), False
 
 
-def enumerate_reference(net, target, max_len=64, max_secondary=4, max_results=0, max_frontier=0, fluxes=None):
+def enumerate_reference(net, target, max_len=64, max_secondary=4, max_results=0, max_frontier=0, fluxes=None,
+                        prune=True):
     """The traversal in pure Python.  Returns (sorted result supports as
     int bitmasks, counters).  fluxes: optional dict, filled with support ->
     the flux vector {column: flux} of the first path reaching each balanced
-    support (S_int v = 0 there)."""
+    support (S_int v = 0 there).  prune=False skips the superset rule, which
+    leaves only the definition (Def. 3: nullity 1 decides)."""
     S_int, twin, full, cols = split_network(net)
     M = len(S_int)
     N = len(cols)
@@ -196,7 +198,7 @@ def enumerate_reference(net, target, max_len=64, max_secondary=4, max_results=0,
                     judge(U2, level)
                     continue
                 # the new column completes a result accepted at an earlier level
-                if not in_u and any((E >> k) & 1 and (E & ~U2) == 0 for E, lv in results if lv < level):
+                if prune and not in_u and any((E >> k) & 1 and (E & ~U2) == 0 for E, lv in results if lv < level):
                     ctr["pruned"] += 1
                     continue
                 key = (U2, nef)

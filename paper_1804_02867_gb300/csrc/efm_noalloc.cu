@@ -2,14 +2,13 @@
 // without allocating any memory.
 //
 // Who needs this: code that may not call cudaMalloc (or any allocator) at
-// the point where it orders pathway supports -- for example work recorded
-// while a stream is being captured into a CUDA graph (allocation calls are
-// not allowed there), code running under a fixed device-memory budget whose
-// allocator belongs to another framework, or a loop that must never block on
-// the allocator.  Such callers pass device buffers they already own for the
-// input and the output; the only other memory the sort needs, its index
-// array, lives in a file-scope device array reserved when the library is
-// loaded.
+// the point where it orders pathway supports -- code running under a fixed
+// device-memory budget whose allocator belongs to another framework (which
+// would not see, and could not account for, a private cudaMalloc), or a
+// loop that must never block on an allocator's synchronisation.  Such
+// callers pass device buffers they already own for the input and the
+// output; the only other memory the sort needs, its index array, lives in a
+// file-scope device array reserved when the library is loaded.
 //
 // Limits and sharing:
 //  - at most EFM_NOALLOC_MAX_ROWS rows (the index array holds the row count
@@ -20,8 +19,10 @@
 //    clearing, but two calls whose work overlaps on the GPU (different
 //    streams, no ordering between them) race on the array and may return
 //    wrong orders.
-//  - the first call on a device looks up the array's device address (no
-//    allocation); make that first call before any stream capture begins.
+//  - the first call on a device (and the first after that device's context
+//    changed, e.g. after cudaDeviceReset) looks up the array's device
+//    address in the current context (no allocation); make that first call
+//    before any stream capture begins.
 #include <mutex>
 
 #include "efm_internal.cuh"
@@ -36,10 +37,34 @@ static __device__ __align__(256) uint32_t g_sort_scratch[kNoallocMaxRows];
 
 std::mutex g_mu;
 uint32_t *g_scratch_ptr[kMaxDevices] = {};
+void *g_scratch_ctx[kMaxDevices] = {};  // the context each cached address belongs to
 
-// Device address of g_sort_scratch on the current device (looked up once
-// per device, with that device current).  Host code must not use the
-// symbol's name as an address: on the host it names a stand-in object.
+// The driver's current context (obtained through the runtime, so the
+// library needs no link against the driver library); nullptr if unknown.
+void *current_context()
+{
+    using get_fn = int (*)(void **);
+    static get_fn fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (get_fn)p;
+        else
+            cudaGetLastError();
+        looked = true;
+    }
+    void *ctx = nullptr;
+    if (fn && fn(&ctx) != 0) ctx = nullptr;
+    return ctx;
+}
+
+// Device address of g_sort_scratch in the current device's current context,
+// looked up once per device and again whenever that context changes.  Host
+// code must not use the symbol's name as an address: on the host it names a
+// stand-in object.
 cudaError_t scratch_ptr(uint32_t **out)
 {
     int dev = 0;
@@ -47,11 +72,13 @@ cudaError_t scratch_ptr(uint32_t **out)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    void *ctx = current_context();
+    if (!g_scratch_ptr[dev] || ctx == nullptr || ctx != g_scratch_ctx[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_sort_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_ptr[dev] = (uint32_t *)p;
+        g_scratch_ctx[dev] = current_context();  // the lookup may have created the primary context
     }
     *out = g_scratch_ptr[dev];
     return cudaSuccess;
@@ -65,7 +92,12 @@ extern "C" int efm_sort_supports_noalloc(const uint64_t *supports_in, int64_t n_
     if (n_rows < 0 || words_per_set < 1 || words_per_set > efm::kMaxW) return EFM_EINVAL;
     if (n_rows > kNoallocMaxRows) return EFM_ECAPACITY;
     if (n_rows == 0) return EFM_OK;
-    if (!supports_in || !supports_out || supports_in == supports_out) return EFM_EINVAL;
+    if (!supports_in || !supports_out) return EFM_EINVAL;
+    // the gather reads rows of the input while it writes the output: the two
+    // byte ranges must not overlap at all
+    const uintptr_t bytes = (uintptr_t)n_rows * (uintptr_t)words_per_set * 8u;
+    const uintptr_t a = (uintptr_t)supports_in, b = (uintptr_t)supports_out;
+    if (a < b + bytes && b < a + bytes) return EFM_EINVAL;
     uint32_t *scratch = nullptr;
     if (scratch_ptr(&scratch) != cudaSuccess) {
         cudaGetLastError();

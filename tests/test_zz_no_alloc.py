@@ -1,12 +1,12 @@
 """The allocation-free sort entry point (efm_sort_supports_noalloc).
 
-Callers that cannot allocate device memory where they work (inside CUDA
-stream capture, under another framework's allocator, in loops that must not
-wait on an allocator) sort supports with this entry point; its scratch lives
-in a fixed device array inside the library.  This test checks, through the
-C-ABI, that its output equals the order efm_fetch_results returns, on two
-calls in a row that reuse the same scratch.  The file is named so that pytest
-collects it last.
+Callers that cannot allocate device memory where they work (under another
+framework's allocator, in loops that must not wait on an allocator) sort
+supports with this entry point; its scratch lives in a fixed device array
+inside the library.  This test checks, through the C-ABI, that its output
+equals the order efm_fetch_results returns and the oracle's own sorted
+output, on two calls in a row that reuse the same scratch.  The file is
+named so that pytest collects it last.
 """
 import numpy as np
 import pytest
@@ -30,9 +30,14 @@ def efm():
 
 
 def _sorted_by_library(efm, net, target):
+    import oracle
+
     with efm.Network(net) as nw:
         (sup, ctr), = efm.enumerate_targets(nw, [target], 30, 4, 0, 2**17)
-    return sup
+    # the same order, written by the oracle's own sort
+    want, _ = oracle.enumerate_pathways(net, target, oracle.Limits(30, 4, 0, 2**17))
+    assert np.array_equal(sup, want)
+    return want
 
 
 def test_noalloc_sort_matches_fetch_order_twice(efm):
@@ -60,4 +65,10 @@ def test_noalloc_sort_rejects_oversize_and_aliasing(efm):
     buf = torch.zeros(4, 2, dtype=torch.int64, device="cuda")
     assert efm.efm_sort_supports_noalloc(buf.data_ptr(), efm.EFM_NOALLOC_MAX_ROWS + 1, 2, buf.data_ptr() + 64) == -3
     assert efm.efm_sort_supports_noalloc(buf.data_ptr(), 4, 2, buf.data_ptr()) == -1
+    # partly overlapping input and output (output 8 bytes past the input)
+    assert efm.efm_sort_supports_noalloc(buf.data_ptr(), 2, 2, buf.data_ptr() + 8) == -1
+    assert efm.efm_sort_supports_noalloc(buf.data_ptr() + 8, 2, 2, buf.data_ptr()) == -1
+    # adjacent, not overlapping: accepted
+    assert efm.efm_sort_supports_noalloc(buf.data_ptr(), 2, 2, buf.data_ptr() + 32) == 0
+    torch.cuda.synchronize()
     assert efm.efm_sort_supports_noalloc(buf.data_ptr(), 4, 65, buf.data_ptr() + 64) == -1
