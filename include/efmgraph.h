@@ -91,6 +91,8 @@ typedef struct {
     int64_t frontier;     /* sum over levels of distinct frontier states */
     int64_t frontier_max; /* largest level frontier */
     int64_t status;       /* EFM_TRUNCATED | EFM_CAPPED | EFM_OVERFLOW_DROPPED */
+    int64_t zero_flux;    /* EFM_SUBTRACTIVE only: children discarded because a subtractive
+                             step (Eq. 5) left a reaction with no positive flux (Prop. 3) */
 } efm_counters;
 
 /* Load a network (Alg. 1 "convert S to the MG graph and copy it to the GPU").

@@ -24,7 +24,7 @@ _SRC = os.path.join(_HERE, "efm_oracle.c")
 
 TRUNCATED, CAPPED, OVERFLOW_DROPPED = 1, 2, 4
 COUNTER_FIELDS = ("levels", "seeds", "expansions", "overflow", "balanced", "candidates", "results",
-                  "pruned", "frontier", "frontier_max", "status")
+                  "pruned", "frontier", "frontier_max", "status", "zero_flux")
 
 
 class _Limits(ctypes.Structure):
@@ -34,6 +34,7 @@ class _Limits(ctypes.Structure):
 
 
 NO_PRUNE = 1  # _Limits.flags: skip the superset rule (the plain definition)
+SUBTRACTIVE = 2  # _Limits.flags: Eq. 5 steps as well (states carry their flux vector)
 
 
 class _Counters(ctypes.Structure):
@@ -47,10 +48,11 @@ class Limits:
     max_results: int = 0
     max_frontier: int = 0
     prune: bool = True  # False: no superset rule, the definition alone
+    subtractive: bool = False  # True: Eq. 5 steps with the zero-flux discard of Prop. 3
 
     def c_struct(self) -> "_Limits":
-        return _Limits(self.max_len, self.max_secondary, self.max_results, self.max_frontier,
-                       0 if self.prune else NO_PRUNE, 0)
+        flags = (0 if self.prune else NO_PRUNE) | (SUBTRACTIVE if self.subtractive else 0)
+        return _Limits(self.max_len, self.max_secondary, self.max_results, self.max_frontier, flags, 0)
 
 
 def build(force: bool = False) -> str:

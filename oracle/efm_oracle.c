@@ -61,6 +61,20 @@
  *      return the max_results smallest;
  *    - stop when F_l is empty.
  *  Output: distinct supports sorted by (|U|, ascending column list).
+ *
+ *  Subtractive variant (flags & OR_SUBTRACTIVE; Eq. 5, Prop. 3): a state
+ *  also carries its flux vector v (integers, positive on U; EF = S_int v),
+ *  and (EF, v) are divided together by the gcd of all their entries, so a
+ *  state is the ray of v.  Besides the additive branches above, the acting
+ *  metabolite i may be balanced by taking flux away from a reaction k
+ *  already in U that moves i the same way as its imbalance (S_ik > 0 for a
+ *  surplus EF_i > 0, S_ik < 0 for a deficit): with g, a, c as in Eq. 3,
+ *      v' = a v - c e_k,   EF' = a EF - c S_int[:, k],
+ *  which zeroes EF_i (Eq. 5 in integers).  It keeps U, costs one secondary
+ *  step, and is discarded when the new flux on k is zero (Prop. 3) or
+ *  negative (the split columns carry non-negative flux); such children are
+ *  counted in zero_flux.  Additive steps update v as v' = a v + c e_k.
+ *  Distinct states are distinct (U, v).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -76,7 +90,8 @@
 #define OR_OVERFLOW_DROPPED 4
 
 /* or_limits.flags */
-#define OR_NO_PRUNE 1 /* the plain definition: no superset rule */
+#define OR_NO_PRUNE 1    /* the plain definition: no superset rule */
+#define OR_SUBTRACTIVE 2 /* Eq. 5 steps as well (states carry their flux vector) */
 
 typedef struct {
     int32_t max_len;
@@ -99,6 +114,7 @@ typedef struct {
     int64_t frontier;
     int64_t frontier_max;
     int64_t status;
+    int64_t zero_flux; /* Eq. 5 children discarded: a reaction's flux reached 0 or below (Prop. 3) */
 } or_counters;
 
 /* ------------------------------------------------------------------------ */
@@ -774,6 +790,33 @@ static int normalise(const int64_t *ef, int M, int32_t *out, int *zero)
     return ovf;
 }
 
+/* (EF, v) / gcd of all their entries (the subtractive variant's state ray);
+ * returns 1 when some entry leaves the int32 range.  *zero: EF == 0. */
+static int normalise2(const int64_t *ef, int M, const int64_t *v, int N, int32_t *ef_out, int32_t *v_out, int *zero)
+{
+    uint64_t g = 0;
+    int nz = 0;
+    for (int i = 0; i < M; ++i) {
+        g = gcd_u64(g, abs_i64(ef[i]));
+        nz |= ef[i] != 0;
+    }
+    for (int k = 0; k < N; ++k) g = gcd_u64(g, abs_i64(v[k]));
+    *zero = !nz;
+    if (g == 0) g = 1;
+    int ovf = 0;
+    for (int i = 0; i < M; ++i) {
+        int64_t x = ef[i] / (int64_t)g;
+        if (x > INT32_MAX || x < -(int64_t)INT32_MAX) ovf = 1;
+        ef_out[i] = (int32_t)x;
+    }
+    for (int k = 0; k < N; ++k) {
+        int64_t x = v[k] / (int64_t)g;
+        if (x > INT32_MAX || x < -(int64_t)INT32_MAX) ovf = 1;
+        v_out[k] = (int32_t)x;
+    }
+    return ovf;
+}
+
 /* The traversal from the seeds of a target (seedset == NULL), or from the
  * one state of a seed set R_in (Prop. 1): U = R_in with flux 1 on each of
  * its columns, EF = sum of their S_int columns / gcd, no secondary step,
@@ -817,8 +860,12 @@ static int enumerate_impl(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, 
     }
     *out_W = g.W;
     const int M = g.M, N = g.N, W = g.W;
+    const int sub = (lim->flags & OR_SUBTRACTIVE) != 0;
+    const int NV = sub ? N : 0; /* flux entries kept per state */
     const int64_t level0 = seedset ? n_seedset - 1 : 0;
-    const size_t key = sizeof(uint64_t) * (size_t)W + sizeof(int32_t) * (size_t)M;
+    /* record: U (W words), EF (M), v (NV), then sec; the key is all but sec */
+    const size_t off_v = sizeof(uint64_t) * (size_t)W + sizeof(int32_t) * (size_t)M;
+    const size_t key = off_v + sizeof(int32_t) * (size_t)NV;
     const size_t stride = key + sizeof(int32_t);
     or_run R;
     memset(&R, 0, sizeof(R));
@@ -831,27 +878,34 @@ static int enumerate_impl(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, 
     uint8_t *rec = (uint8_t *)calloc(1, stride);
     int64_t *ef = (int64_t *)malloc(sizeof(int64_t) * (size_t)(M > 0 ? M : 1));
     int32_t *efn = (int32_t *)malloc(sizeof(int32_t) * (size_t)(M > 0 ? M : 1));
-    if (!rec || !ef || !efn) { rc = OR_ENOMEM; goto done; }
+    int64_t *vv = (int64_t *)calloc((size_t)(NV > 0 ? NV : 1), sizeof(int64_t));
+    if (!rec || !ef || !efn || !vv) { rc = OR_ENOMEM; goto done; }
 
     /* level 0: seeds (INIT) -- or the one state of the seed set */
     for (int j = 0; j < (seedset ? 1 : N); ++j) {
         uint64_t *U = (uint64_t *)rec;
         memset(U, 0, sizeof(uint64_t) * (size_t)W);
+        for (int k = 0; k < NV; ++k) vv[k] = 0;
         if (seedset) {
             for (int i = 0; i < M; ++i) ef[i] = 0;
             for (int a = 0; a < n_seedset; ++a) {
                 const int k = seedset[a];
                 for (int i = 0; i < M; ++i) ef[i] += g.S[(size_t)i * N + k]; /* Eq. 2, flux 1 on each */
                 U[k >> 6] |= 1ull << (k & 63);
+                if (sub) vv[k] = 1;
             }
         } else {
             if (target >= 0 && full_coef(target, j, &g, row_ptr, col_idx, coef) <= 0) continue;
             for (int i = 0; i < M; ++i) ef[i] = g.S[(size_t)i * N + j]; /* Eq. 2 with flux 1 on j */
             U[j >> 6] |= 1ull << (j & 63);
+            if (sub) vv[j] = 1;
         }
         ctr->seeds++;
         int zero = 0;
-        if (normalise(ef, M, (int32_t *)(rec + sizeof(uint64_t) * W), &zero)) {
+        const int bad = sub ? normalise2(ef, M, vv, NV, (int32_t *)(rec + sizeof(uint64_t) * W),
+                                         (int32_t *)(rec + off_v), &zero)
+                            : normalise(ef, M, (int32_t *)(rec + sizeof(uint64_t) * W), &zero);
+        if (bad) {
             ctr->overflow++;
             continue;
         }
@@ -884,6 +938,7 @@ static int enumerate_impl(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, 
             const uint8_t *st = (const uint8_t *)vec_at(&F, s);
             const uint64_t *U = (const uint64_t *)st;
             const int32_t *EF = (const int32_t *)(st + sizeof(uint64_t) * W);
+            const int32_t *V = (const int32_t *)(st + off_v); /* flux vector (subtractive variant) */
             const int32_t sec = *(const int32_t *)(st + key);
             const int pc = popcount_words(U, W);
             /* acting metabolite: fewest reactions able to balance it, then index */
@@ -912,11 +967,16 @@ static int enumerate_impl(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, 
                 const int64_t a = (int64_t)(abs_i64(s_ik) / g0);
                 const int64_t c = (int64_t)(abs_i64(ef_i) / g0);
                 for (int i = 0; i < M; ++i) ef[i] = a * (int64_t)EF[i] + c * g.S[(size_t)i * N + k];
+                for (int x = 0; x < NV; ++x) vv[x] = a * (int64_t)V[x];
+                if (sub) vv[k] += c;
                 uint64_t *U2 = (uint64_t *)rec;
                 memcpy(U2, U, sizeof(uint64_t) * (size_t)W);
                 U2[k >> 6] |= 1ull << (k & 63);
                 int zero = 0;
-                if (normalise(ef, M, (int32_t *)(rec + sizeof(uint64_t) * W), &zero)) {
+                const int bad = sub ? normalise2(ef, M, vv, NV, (int32_t *)(rec + sizeof(uint64_t) * W),
+                                                 (int32_t *)(rec + off_v), &zero)
+                                    : normalise(ef, M, (int32_t *)(rec + sizeof(uint64_t) * W), &zero);
+                if (bad) {
                     ctr->overflow++;
                     continue;
                 }
@@ -935,8 +995,46 @@ static int enumerate_impl(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, 
                     goto done;
                 }
             }
+            /* Eq. 5: take flux away from a reaction k in U that moves the
+             * acting metabolite the same way as its imbalance */
+            for (int k = 0; k < N && sub; ++k) {
+                const int64_t s_ik = g.S[(size_t)piv * N + k];
+                if (!(ef_i > 0 ? s_ik > 0 : s_ik < 0)) continue;
+                if (!bit_test(U, k)) continue;
+                if (sec + 1 > lim->max_secondary) continue;
+                ctr->expansions++;
+                const uint64_t g0 = gcd_u64(abs_i64(ef_i), abs_i64(s_ik));
+                const int64_t a = (int64_t)(abs_i64(s_ik) / g0);
+                const int64_t c = (int64_t)(abs_i64(ef_i) / g0);
+                for (int i = 0; i < M; ++i) ef[i] = a * (int64_t)EF[i] - c * g.S[(size_t)i * N + k];
+                for (int x = 0; x < NV; ++x) vv[x] = a * (int64_t)V[x];
+                vv[k] -= c;
+                if (vv[k] <= 0) { /* Prop. 3: no flux left on k (or less than none) */
+                    ctr->zero_flux++;
+                    continue;
+                }
+                uint64_t *U2 = (uint64_t *)rec;
+                memcpy(U2, U, sizeof(uint64_t) * (size_t)W);
+                int zero = 0;
+                if (normalise2(ef, M, vv, NV, (int32_t *)(rec + sizeof(uint64_t) * W), (int32_t *)(rec + off_v),
+                               &zero)) {
+                    ctr->overflow++;
+                    continue;
+                }
+                *(int32_t *)(rec + key) = sec + 1;
+                if (zero) {
+                    ctr->balanced++;
+                    if ((rc = judge(&R, U2, level)) != OR_OK) goto done;
+                    continue;
+                }
+                if (vec_push(&C, rec)) {
+                    rc = OR_ENOMEM;
+                    goto done;
+                }
+            }
         }
-        /* F_level = distinct (U, EF) of the surviving children */
+        /* F_level = distinct (U, EF) of the surviving children (with v in
+         * the subtractive variant) */
         g_keylen = key;
         qsort(C.data, C.n, stride, cmp_state);
         size_t u = 0;
@@ -989,6 +1087,7 @@ done:
     free(rec);
     free(ef);
     free(efn);
+    free(vv);
     free(F.data);
     free(C.data);
     free(R.results.data);

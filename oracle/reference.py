@@ -89,7 +89,7 @@ def enumerate_reference(net, target, max_len=64, max_secondary=4, max_results=0,
     deg_out = [sum(1 for k in range(N) if S_int[i][k] < 0) for i in range(M)]
     deg_in = [sum(1 for k in range(N) if S_int[i][k] > 0) for i in range(M)]
     ctr = dict(levels=0, seeds=0, expansions=0, overflow=0, balanced=0, candidates=0, results=0,
-               pruned=0, frontier=0, frontier_max=0, status=0)
+               pruned=0, frontier=0, frontier_max=0, status=0, zero_flux=0)
     seen = set()
     results = []  # (U, level)
 
@@ -217,6 +217,135 @@ def enumerate_reference(net, target, max_len=64, max_secondary=4, max_results=0,
     return finish()
 
 
+def enumerate_subtractive(net, target, max_len=64, max_secondary=4, max_results=0, max_frontier=0, prune=True):
+    """The traversal with the subtractive steps of Eq. 5 as well, in pure
+    Python.  A state is (U, v): the support and its flux vector, a primitive
+    integer vector positive on U.  Its extra flux is recomputed from v at
+    every step, EF = S_int v (Eq. 2), instead of being updated.  Branches of
+    the acting metabolite i (fewest reactions able to fix it, then index):
+      * additive (Eq. 3 / Eq. 4): every k with S_ik of the opposite sign to
+        EF_i, twin not in U, v' = a v + c e_k;
+      * subtractive (Eq. 5): every k in U with S_ik of the same sign as EF_i,
+        v' = a v - c e_k, discarded when v'_k <= 0 (Prop. 3);
+    with g = gcd(|EF_i|, |S_ik|), a = |S_ik| / g, c = |EF_i| / g, so that
+    EF'_i = 0.  Secondary steps (k already in U, either kind) cost one unit of
+    max_secondary.  Returns (sorted result supports as int bitmasks, counters)
+    like enumerate_reference."""
+    S_int, twin, full, cols = split_network(net)
+    M = len(S_int)
+    N = len(cols)
+    deg_out = [sum(1 for k in range(N) if S_int[i][k] < 0) for i in range(M)]
+    deg_in = [sum(1 for k in range(N) if S_int[i][k] > 0) for i in range(M)]
+    ctr = dict(levels=0, seeds=0, expansions=0, overflow=0, balanced=0, candidates=0, results=0,
+               pruned=0, frontier=0, frontier_max=0, status=0, zero_flux=0)
+    seen = set()
+    results = []  # (U, level)
+
+    def extra_flux(v):
+        return [sum(S_int[i][k] * x for k, x in v) for i in range(M)]
+
+    def primitive(vd):
+        g = 0
+        for x in vd.values():
+            g = gcd(g, abs(x))
+        return tuple(sorted((k, x // g) for k, x in vd.items() if x != 0))
+
+    def judge(U, level):
+        if U in seen:
+            return
+        seen.add(U)
+        ctr["candidates"] += 1
+        if nullity_one(S_int, U, N):
+            results.append((U, level))
+            ctr["results"] += 1
+
+    def finish():
+        if ctr["overflow"]:
+            ctr["status"] |= OVERFLOW_DROPPED
+        res = sorted((U for U, _ in results), key=lambda U: (bin(U).count("1"),
+                                                             [k for k in range(N) if (U >> k) & 1]))
+        if max_results > 0:
+            res = res[:max_results]
+        return res, ctr
+
+    def child(U, v, level, sec, F, new_col=-1):
+        """Place the child state (U, v) (v primitive) at `level`; new_col: the
+        column an additive step added to the support (superset rule)."""
+        ef = extra_flux(v)
+        if any(abs(x) > INT32_MAX for x in ef) or any(abs(x) > INT32_MAX for _, x in v):
+            ctr["overflow"] += 1
+            return
+        if not any(ef):
+            ctr["balanced"] += 1
+            judge(U, level)
+            return
+        if prune and new_col >= 0 and any((E >> new_col) & 1 and (E & ~U) == 0 for E, lv in results if lv < level):
+            ctr["pruned"] += 1
+            return
+        key = (U, v)
+        if key not in F or F[key] > sec:
+            F[key] = sec
+
+    F = {}  # (U, v) -> sec
+    for j in range(N):
+        if target >= 0 and full[target][j] <= 0:
+            continue
+        ctr["seeds"] += 1
+        child(1 << j, ((j, 1),), 0, 0, F)
+    ctr["levels"] = 1
+    if max_frontier > 0 and len(F) > max_frontier:
+        ctr["status"] |= TRUNCATED
+        return finish()
+    ctr["frontier"] += len(F)
+    ctr["frontier_max"] = max(ctr["frontier_max"], len(F))
+    if max_results > 0 and ctr["results"] >= max_results:
+        ctr["status"] |= CAPPED
+        return finish()
+    level = 0
+    while F:
+        level += 1
+        C = {}
+        for (U, v), sec in F.items():
+            pc = bin(U).count("1")
+            ef = extra_flux(v)
+            _, piv = min((deg_out[i] if ef[i] > 0 else deg_in[i], i) for i in range(M) if ef[i] != 0)
+            e = ef[piv]
+            vd = dict(v)
+            for k in range(N):
+                s = S_int[piv][k]
+                in_u = (U >> k) & 1
+                add = (s < 0) if e > 0 else (s > 0)
+                take = bool(in_u) and ((s > 0) if e > 0 else (s < 0))
+                if not add and not take:
+                    continue
+                if add and twin[k] >= 0 and (U >> twin[k]) & 1:
+                    continue
+                if (in_u and sec + 1 > max_secondary) or (not in_u and pc + 1 > max_len):
+                    continue
+                ctr["expansions"] += 1
+                g = gcd(abs(e), abs(s))
+                a, c = abs(s) // g, abs(e) // g
+                nv = {kk: a * x for kk, x in vd.items()}
+                nv[k] = nv.get(k, 0) + (c if add else -c)
+                if take and nv[k] <= 0:
+                    ctr["zero_flux"] += 1
+                    continue
+                nvt = primitive(nv)
+                assert extra_flux(nvt)[piv] == 0  # Eq. 3 / Eq. 5 zero the acting metabolite
+                child(U | (1 << k), nvt, level, sec + in_u, C, k if not in_u else -1)
+        F = C
+        ctr["levels"] = level + 1
+        if max_frontier > 0 and len(F) > max_frontier:
+            ctr["status"] |= TRUNCATED
+            break
+        ctr["frontier"] += len(F)
+        ctr["frontier_max"] = max(ctr["frontier_max"], len(F))
+        if max_results > 0 and ctr["results"] >= max_results:
+            ctr["status"] |= CAPPED
+            break
+    return finish()
+
+
 def _splitmix_at(seed, c):
     """First output of SplitMix64 started from state seed + c * golden."""
     m = (1 << 64) - 1
@@ -236,7 +365,7 @@ def sample_reference(net, target, max_len, max_secondary, seed, n_walks):
     deg_out = [sum(1 for k in range(N) if S_int[i][k] < 0) for i in range(M)]
     deg_in = [sum(1 for k in range(N) if S_int[i][k] > 0) for i in range(M)]
     ctr = dict(levels=0, seeds=0, expansions=0, overflow=0, balanced=0, candidates=0, results=0,
-               pruned=0, frontier=0, frontier_max=0, status=0)
+               pruned=0, frontier=0, frontier_max=0, status=0, zero_flux=0)
     seeds = [j for j in range(N) if target < 0 or full[target][j] > 0]
     seen, results = set(), []
     for w in range(n_walks if seeds else 0):

@@ -251,49 +251,85 @@ namespace {
 
 // Device buffers of one traversal, reused across the targets of a job.
 struct Work {
-    DevBuf U[2], B[2], meta[2];
+    DevBuf U[2], B[2], meta[2], live[2];
     DevBuf slots, cslots, cand, res, bcnt, bfill, bptr, bres, ctr, sortidx, rcols;
+    DevBuf fp;         // fingerprints of one level's reserved child rows
     DevBuf perm, fkb;  // first-K search: parent order of a level, bound support
     DevBuf band;       // per column: intersection of the results containing it (W <= 2)
     DevBuf lx, lscore, lhist, lerr;  // learned order: features, scores, buckets, error flag
     int64_t lx_rows = 0;
+    int64_t rows[2] = {0, 0};  // capacity of each arena (rows)
     int64_t F_cap = 0, cand_cap = 0, res_cap = 0, bres_cap = 0;  // bres_cap in bucket entries
+    int64_t fp_cap = 0, perm_cap = 0;
     uint64_t slot_cap = 0, cslot_cap = 0, sort_cap = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
+void free_arena(Work &w, int i, cudaStream_t s)
+{
+    dev_free(w.U[i], s);
+    dev_free(w.B[i], s);
+    dev_free(w.meta[i], s);
+    dev_free(w.live[i], s);
+    w.rows[i] = 0;
+}
+
 void free_work(Work &w, cudaStream_t s)
 {
-    for (int i = 0; i < 2; ++i) {
-        dev_free(w.U[i], s);
-        dev_free(w.B[i], s);
-        dev_free(w.meta[i], s);
-    }
+    for (int i = 0; i < 2; ++i) free_arena(w, i, s);
     DevBuf *bufs[] = {&w.slots, &w.cslots, &w.cand, &w.res, &w.bcnt,    &w.bfill, &w.bptr,
                       &w.bres,  &w.ctr,    &w.sortidx, &w.rcols, &w.perm, &w.fkb,
-                      &w.lx,    &w.lscore, &w.lhist,   &w.lerr, &w.band};
+                      &w.lx,    &w.lscore, &w.lhist,   &w.lerr, &w.band, &w.fp};
     for (DevBuf *b : bufs) dev_free(*b, s);
     for (auto &e : w.ev)
         if (e) cudaEventDestroy(e);
+}
+
+// Arena i with room for `rows` states (contents are not kept).
+bool alloc_arena(Work &w, const NetView &nv, int i, int64_t rows, cudaStream_t s)
+{
+    free_arena(w, i, s);
+    const size_t F = (size_t)rows;
+    bool ok = dev_alloc(w.U[i], F * nv.W * 8, s) && dev_alloc(w.B[i], F * nv.Mpad * 4, s) &&
+              dev_alloc(w.meta[i], F * 4, s) && dev_alloc(w.live[i], F * 4, s);
+    if (ok) w.rows[i] = rows;
+    return ok;
+}
+
+// The level's fingerprint array and state hash table hold `reserved` rows.
+bool ensure_level_tables(Work &w, uint64_t reserved, cudaStream_t s)
+{
+    if ((int64_t)reserved > w.fp_cap) {
+        dev_free(w.fp, s);
+        const int64_t cap = std::max<int64_t>((int64_t)reserved, w.fp_cap + w.fp_cap / 2);
+        if (!dev_alloc(w.fp, (size_t)cap * 8, s)) return false;
+        w.fp_cap = cap;
+    }
+    const uint64_t need = next_pow2(2 * reserved + 64);
+    if (need > w.slot_cap) {
+        dev_free(w.slots, s);
+        if (!dev_alloc(w.slots, need * 8, s)) return false;
+        w.slot_cap = need;
+    }
+    return true;
 }
 
 int alloc_work(Work &w, const efm_net *net, const efm_limits &lim, int total_warps, cudaStream_t s)
 {
     const NetView &nv = net->nv;
     const int64_t default_cap = (int64_t)1 << 22;
+    // a level writes a row for every surviving child before deduplication,
+    // so an arena gets room for a budget-sized frontier plus duplicates and
+    // the rows warps reserve but leave unused; a level that needs more is
+    // run again with a larger arena
     w.F_cap = lim.max_frontier > 0 ? lim.max_frontier + 1 : default_cap;
+    const int64_t rows = w.F_cap + w.F_cap / 8 + 32 * (int64_t)total_warps;
     w.cand_cap = (int64_t)1 << 20;
     w.res_cap = w.cand_cap;
-    w.slot_cap = next_pow2(2 * (uint64_t)w.F_cap + 64 * (uint64_t)total_warps);
     w.cslot_cap = next_pow2(2 * (uint64_t)w.cand_cap);
-    const size_t W = (size_t)nv.W, Mpad = (size_t)nv.Mpad, F = (size_t)w.F_cap;
-    bool ok = true;
-    for (int i = 0; i < 2; ++i) {
-        ok = ok && dev_alloc(w.U[i], F * W * 8, s);
-        ok = ok && dev_alloc(w.B[i], F * Mpad * 4, s);
-        ok = ok && dev_alloc(w.meta[i], F * 4, s);
-    }
-    ok = ok && dev_alloc(w.slots, w.slot_cap * 8, s);
+    const size_t W = (size_t)nv.W;
+    bool ok = alloc_arena(w, nv, 0, rows, s) && alloc_arena(w, nv, 1, rows, s);
+    ok = ok && ensure_level_tables(w, 1024 + 32 * (uint64_t)total_warps, s);
     ok = ok && dev_alloc(w.cslots, w.cslot_cap * 8, s);
     ok = ok && dev_alloc(w.cand, (size_t)w.cand_cap * W * 8, s);
     ok = ok && dev_alloc(w.res, (size_t)w.res_cap * W * 8, s);
@@ -303,10 +339,7 @@ int alloc_work(Work &w, const efm_net *net, const efm_limits &lim, int total_war
     ok = ok && dev_alloc(w.ctr, C_COUNT * 8, s);
     if (nv.W > 2) ok = ok && dev_alloc(w.rcols, (size_t)w.res_cap * kRcolStride * 2, s);
     if (nv.W <= 2) ok = ok && dev_alloc(w.band, (size_t)nv.N * nv.W * 8, s);
-    if (lim.first_k > 0) {
-        ok = ok && dev_alloc(w.perm, F * 4, s);
-        ok = ok && dev_alloc(w.fkb, W * 8, s);
-    }
+    if (lim.first_k > 0) ok = ok && dev_alloc(w.fkb, W * 8, s);
     for (auto &e : w.ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -401,15 +434,15 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
 {
     const NetView &nv = net->nv;
     cudaStream_t s = net->stream;
-    const int grid = expand_grid(nv, net->sm_count);
+    const int grid = generate_grid(nv, net->sm_count);
     const int total_warps = grid * kExpandWarps;
+    const int NG = 32 / std::min(32, std::max(4, 4 * nv.EPL));  // children per warp round
     unsigned long long *ctr = (unsigned long long *)w.ctr.p;
     unsigned long long h[C_COUNT];
     efm_counters &c = out.ctr;
     memset(&c, 0, sizeof(c));
 
     LevelArgs a{};
-    a.slots = (unsigned long long *)w.slots.p;
     a.cslots = (unsigned long long *)w.cslots.p;
     a.cslot_mask = w.cslot_cap - 1;
     a.cand = (uint64_t *)w.cand.p;
@@ -428,7 +461,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
         r.U = (uint64_t *)w.U[i].p;
         r.B = (int32_t *)w.B[i].p;
         r.meta = (uint32_t *)w.meta[i].p;
-        r.cap = w.F_cap;
+        r.cap = w.rows[i];
         return r;
     };
 
@@ -437,7 +470,8 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
     CK(cudaMemsetAsync(w.bptr.p, 0, (size_t)(nv.N + 1) * 4, s));
     CK(cudaEventRecord(w.ev[0], s));
 
-    // level 0: seeds (or the seed set's one state, at level |R_in| - 1)
+    // level 0: seeds (or the seed set's one state, at level |R_in| - 1),
+    // written densely: the first level reads its parents in arena order
     int cur = 0;
     const int level0 = seedset ? n_seedset - 1 : 0;
     a.level = level0;
@@ -447,6 +481,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
     else
         CK(launch_seed(nv, a, target, s));
     out.kernel_launches += 1;
+    const uint32_t *par_map = nullptr;  // frontier position -> arena row (null: identity)
     AcceptArgs acc{};
     acc.cand = (const uint64_t *)w.cand.p;
     acc.res = (uint64_t *)w.res.p;
@@ -492,7 +527,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
     if (lim.max_frontier > 0 && n_front > lim.max_frontier) {
         status |= EFM_TRUNCATED;
         stop = true;
-    } else if (n_front > w.F_cap) {
+    } else if (n_front > w.rows[cur]) {
         return EFM_ECAPACITY;
     } else {
         c.frontier += n_front;
@@ -502,7 +537,6 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
             stop = true;
         }
     }
-    unsigned long long exp_before = 0;
     int64_t buckets_built_for = 0;
     float ms = 0.f;
     for (int level = level0 + 1; !stop && n_front > 0; ++level) {
@@ -525,16 +559,6 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
             out.kernel_launches += res_n > 0 ? 3 : 1;
             buckets_built_for = res_n;
         }
-        const uint64_t bound = std::min<uint64_t>(deg_sum, (uint64_t)w.F_cap);
-        const uint64_t nslots = std::min<uint64_t>(w.slot_cap, next_pow2(2 * bound + 64 * (uint64_t)total_warps));
-        CK(cudaMemsetAsync(w.slots.p, 0xFF, nslots * 8, s));
-        CK(cudaMemsetAsync(ctr + C_NEXT, 0, 2 * 8, s));
-        a.par = arena(cur);
-        a.child = arena(cur ^ 1);
-        a.slot_mask = nslots - 1;
-        a.level = level;
-        // first-K: the level's parents in proposal order, in chunks with the
-        // bound refreshed between them
         if (trace && n_front > 0) {
             // training rows: a strided sample of this frontier (level - 1)
             const int64_t stride = std::max<int64_t>(1, (n_front + trace->rows_per_level - 1) / trace->rows_per_level);
@@ -542,13 +566,16 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
             efm_model *m = trace->m;
             if (!model_reserve_rows(m, m->n_rows + cnt)) return EFM_ENOMEM;
             if ((rc = ensure_dep_tags(net))) return rc;
-            CK(launch_features(nv, arena(cur), 0, stride, cnt, level - 1, lim.max_len, lim.max_secondary,
+            CK(launch_features(nv, arena(cur), par_map, 0, stride, cnt, level - 1, lim.max_len, lim.max_secondary,
                                (const uint64_t *)net->dep.p, m->X.p, m->n_rows, s));
-            CK(launch_labels((const uint64_t *)w.U[cur].p, nv.W, 0, stride, cnt, trace->ans, trace->n_ans,
+            CK(launch_labels((const uint64_t *)w.U[cur].p, nv.W, par_map, 0, stride, cnt, trace->ans, trace->n_ans,
                              (float *)m->y.p, m->n_rows, s));
             m->n_rows += cnt;
         }
+        // first-K: the level's parents in proposal order (positions -> arena
+        // rows), expanded in chunks with the bound refreshed between them
         int64_t chunk = n_front;
+        const uint32_t *order = par_map;
         if (fk) {
             chunk = std::max<int64_t>(kFirstKChunkMin, (n_front + kFirstKChunks - 1) / kFirstKChunks);
             if (model && lim.proposal == EFM_LEARNED && n_front > chunk) {
@@ -563,90 +590,154 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
                         return EFM_ENOMEM;
                     w.lx_rows = cap;
                 }
+                if (n_front > w.perm_cap) {
+                    dev_free(w.perm, s);
+                    const int64_t cap = std::max<int64_t>(n_front, 2 * w.perm_cap);
+                    if (!dev_alloc(w.perm, (size_t)cap * 4, s)) return EFM_ENOMEM;
+                    w.perm_cap = cap;
+                }
                 if (!w.lhist.p) {
                     if (!dev_alloc(w.lhist, 4096 * 4, s) || !dev_alloc(w.lerr, 4, s)) return EFM_ENOMEM;
                     CK(cudaMemsetAsync(w.lerr.p, 0, 4, s));
                 }
                 if ((rc = ensure_dep_tags(net))) return rc;
-                CK(launch_features(nv, arena(cur), 0, 1, n_front, level - 1, lim.max_len, lim.max_secondary,
+                CK(launch_features(nv, arena(cur), par_map, 0, 1, n_front, level - 1, lim.max_len, lim.max_secondary,
                                    (const uint64_t *)net->dep.p, w.lx.p, 0, s));
                 CK(launch_mlp_score(w.lx.p, n_front, model->wb.p, (const float *)model->params.p,
                                     (float *)w.lscore.p, (unsigned *)w.lerr.p, s));
-                CK(launch_score_order((const float *)w.lscore.p, n_front, (unsigned *)w.lhist.p,
+                CK(launch_score_order((const float *)w.lscore.p, n_front, par_map, (unsigned *)w.lhist.p,
                                       (uint32_t *)w.perm.p, s));
+                order = (const uint32_t *)w.perm.p;
                 out.kernel_launches += 6;
-            } else {
+            } else if (!order && chunk < n_front) {
+                if (n_front > w.perm_cap) {
+                    dev_free(w.perm, s);
+                    const int64_t cap = std::max<int64_t>(n_front, 2 * w.perm_cap);
+                    if (!dev_alloc(w.perm, (size_t)cap * 4, s)) return EFM_ENOMEM;
+                    w.perm_cap = cap;
+                }
                 CK(launch_iota((uint32_t *)w.perm.p, n_front, s));
+                order = (const uint32_t *)w.perm.p;
                 out.kernel_launches += 1;
             }
         }
-        uint64_t next_before = 0;
-        for (int64_t c0 = 0; c0 < n_front; c0 += chunk) {
-            const int64_t cn = std::min<int64_t>(chunk, n_front - c0);
-            a.n_par = cn;
-            a.perm = fk ? (const uint32_t *)w.perm.p + c0 : nullptr;
-            a.cpw = (int)std::min<int64_t>(32, std::max<int64_t>(1, (cn + total_warps - 1) / total_warps));
-            a.fk_pc = fk ? top.pc : 0;
-            a.fk_sup = (const uint64_t *)w.fkb.p;
-            a.max_len = (fk && top.pc > 0) ? std::min(lim.max_len, top.pc) : lim.max_len;
-            CK(cudaEventRecord(w.ev[2], s));
-            CK(launch_expand(nv, a, grid, s));
-            CK(cudaEventRecord(w.ev[3], s));
-            // minimality test of the new candidates, range taken on the device
-            CK(launch_accept_new(nv, acc, net->sm_count, s));
-            // one round trip per chunk: the counters and, in a first-K search, a
-            // window of the results that follow the ones already seen
-            const int64_t win = fk ? std::min<int64_t>(kResultWindow, w.res_cap - res_n) : 0;
-            if (win > 0)
-                CK(cudaMemcpyAsync(window.data(), (const uint64_t *)w.res.p + (size_t)res_n * nv.W,
-                                   (size_t)win * nv.W * 8, cudaMemcpyDeviceToHost, s));
-            if ((rc = read_ctr())) return rc;
-            CK(cudaEventElapsedTime(&ms, w.ev[2], w.ev[3]));
-            out.expand_ms += ms;
-            out.expand_launches += 1;
-            out.kernel_launches += 3;
-            {
-                const double state_bytes = 8.0 * nv.W + 4.0 * nv.M + 4.0;
-                const uint64_t next_now = std::min<unsigned long long>(h[C_NEXT], (unsigned long long)w.F_cap);
-                const double n_new = (double)(next_now - next_before);
-                const double n_child = (double)(h[C_EXP] - exp_before);
-                out.expand_bytes += state_bytes * ((double)cn + n_new) + 16.0 * n_child;
-                if (getenv("EFM_DEBUG"))
-                    fprintf(stderr, "efm: level %d parents %lld items %llu children %.0f new %.0f bytes %.0f ms %.3f\n",
-                            level, (long long)cn, (unsigned long long)(c0 == 0 && chunk >= n_front ? deg_sum : 0),
-                            n_child, n_new, state_bytes * ((double)cn + n_new) + 16.0 * n_child, ms);
-                exp_before = h[C_EXP];
-                next_before = next_now;
-            }
-            const int64_t res_now = (int64_t)std::min<unsigned long long>(h[C_RES_N], (unsigned long long)w.res_cap);
-            if (fk && res_now > res_n) {
-                // the new results (beyond the window: fetched now) tighten the bound
-                const uint64_t *fresh = window.data();
-                std::vector<uint64_t> more;
-                if (res_now - res_n > win) {
-                    more.resize((size_t)(res_now - res_n) * nv.W);
-                    CK(cudaMemcpyAsync(more.data(), (const uint64_t *)w.res.p + (size_t)res_n * nv.W,
-                                       more.size() * 8, cudaMemcpyDeviceToHost, s));
-                    CK(cudaStreamSynchronize(s));
-                    fresh = more.data();
+        // rows one warp reserves at a time: few for small or chunked levels
+        // (a warp's unused reserved rows at the end of every launch are dead
+        // weight in the arena), 32 for large ones
+        const int64_t launches = (n_front + chunk - 1) / chunk;
+        const int blk = launches > 1 ? NG
+                                     : (int)std::min<uint64_t>(32, std::max<uint64_t>((uint64_t)NG,
+                                                                                     deg_sum / (64ull * total_warps)));
+        const uint64_t reserved = deg_sum + (uint64_t)launches * blk * total_warps + 64;
+        if (!ensure_level_tables(w, reserved, s)) return EFM_ENOMEM;
+        const uint64_t nslots = next_pow2(2 * reserved + 64);
+        unsigned long long snap[C_COUNT];
+        memcpy(snap, h, sizeof(h));
+        // the level, run again with a larger child arena if some children
+        // found no row and the fingerprints alone cannot show a truncation
+        for (int attempt = 0;; ++attempt) {
+            if (attempt > 4) return EFM_ECAPACITY;
+            CK(cudaMemsetAsync(w.slots.p, 0xFF, nslots * 8, s));
+            CK(cudaMemsetAsync(ctr + C_NEXT, 0, 2 * 8, s));
+            CK(cudaMemsetAsync(ctr + C_WRITTEN, 0, 3 * 8, s));
+            CK(cudaMemsetAsync(ctr + C_DEDUP_BEGIN, 0, 8, s));
+            a.par = arena(cur);
+            a.child = arena(cur ^ 1);
+            a.live = (uint32_t *)w.live[cur ^ 1].p;
+            a.slots = (unsigned long long *)w.slots.p;
+            a.slot_mask = nslots - 1;
+            a.fp = (uint64_t *)w.fp.p;
+            a.fp_cap = w.fp_cap;
+            a.blk = blk;
+            a.level = level;
+            unsigned long long exp_before = h[C_EXP];
+            uint64_t next_before = 0;
+            for (int64_t c0 = 0; c0 < n_front; c0 += chunk) {
+                const int64_t cn = std::min<int64_t>(chunk, n_front - c0);
+                a.n_par = cn;
+                a.perm = order ? order + c0 : nullptr;
+                a.cpw = (int)std::min<int64_t>(32, std::max<int64_t>(1, (cn + total_warps - 1) / total_warps));
+                a.fk_pc = fk ? top.pc : 0;
+                a.fk_sup = (const uint64_t *)w.fkb.p;
+                a.max_len = (fk && top.pc > 0) ? std::min(lim.max_len, top.pc) : lim.max_len;
+                CK(cudaEventRecord(w.ev[2], s));
+                CK(launch_generate(nv, a, grid, s));
+                CK(launch_dedup(a, nv.Mpad, nv.W, net->sm_count, s));
+                CK(cudaEventRecord(w.ev[3], s));
+                // minimality test of the new candidates, range taken on the device
+                CK(launch_accept_new(nv, acc, net->sm_count, s));
+                // one round trip per chunk: the counters and, in a first-K search, a
+                // window of the results that follow the ones already seen
+                const int64_t win = fk ? std::min<int64_t>(kResultWindow, w.res_cap - res_n) : 0;
+                if (win > 0)
+                    CK(cudaMemcpyAsync(window.data(), (const uint64_t *)w.res.p + (size_t)res_n * nv.W,
+                                       (size_t)win * nv.W * 8, cudaMemcpyDeviceToHost, s));
+                if ((rc = read_ctr())) return rc;
+                CK(cudaEventElapsedTime(&ms, w.ev[2], w.ev[3]));
+                out.expand_ms += ms;
+                out.expand_launches += 1;
+                out.kernel_launches += 5;
+                {
+                    const double state_bytes = 8.0 * nv.W + 4.0 * nv.M + 4.0;
+                    const uint64_t next_now = h[C_NEXT];
+                    const double n_new = (double)(next_now - next_before);
+                    const double n_child = (double)(h[C_EXP] - exp_before);
+                    out.expand_bytes += state_bytes * ((double)cn + n_new) + 16.0 * n_child;
+                    if (getenv("EFM_DEBUG"))
+                        fprintf(stderr,
+                                "efm: level %d parents %lld items %llu children %.0f new %.0f rows %llu bytes %.0f ms %.3f\n",
+                                level, (long long)cn, (unsigned long long)(c0 == 0 && chunk >= n_front ? deg_sum : 0),
+                                n_child, n_new, h[C_WRITTEN], state_bytes * ((double)cn + n_new) + 16.0 * n_child, ms);
+                    exp_before = h[C_EXP];
+                    next_before = next_now;
                 }
-                const int pc_before = top.pc;
-                const std::vector<uint64_t> kth_before = top.kth;
-                top.add(fresh, res_now - res_n);
-                if (top.pc > 0 && (top.pc != pc_before || top.kth != kth_before))
-                    CK(cudaMemcpyAsync(w.fkb.p, top.kth.data(), (size_t)nv.W * 8, cudaMemcpyHostToDevice, s));
+                const int64_t res_now = (int64_t)std::min<unsigned long long>(h[C_RES_N], (unsigned long long)w.res_cap);
+                if (fk && res_now > res_n) {
+                    // the new results (beyond the window: fetched now) tighten the bound
+                    const uint64_t *fresh = window.data();
+                    std::vector<uint64_t> more;
+                    if (res_now - res_n > win) {
+                        more.resize((size_t)(res_now - res_n) * nv.W);
+                        CK(cudaMemcpyAsync(more.data(), (const uint64_t *)w.res.p + (size_t)res_n * nv.W,
+                                           more.size() * 8, cudaMemcpyDeviceToHost, s));
+                        CK(cudaStreamSynchronize(s));
+                        fresh = more.data();
+                    }
+                    const int pc_before = top.pc;
+                    const std::vector<uint64_t> kth_before = top.kth;
+                    top.add(fresh, res_now - res_n);
+                    if (top.pc > 0 && (top.pc != pc_before || top.kth != kth_before))
+                        CK(cudaMemcpyAsync(w.fkb.p, top.kth.data(), (size_t)nv.W * 8, cudaMemcpyHostToDevice, s));
+                }
+                res_n = res_now;
             }
-            res_n = res_now;
+            if (h[C_UNWRITTEN] == 0) break;  // every child has its row: the level is exact
+            // some children found no row: their distinct fingerprints and the
+            // distinct written rows bound |F_l| from below
+            if (lim.max_frontier > 0 && (int64_t)(h[C_NEXT] + h[C_UNV]) > lim.max_frontier) break;
+            // not decided: grow the child arena to every reserved row and run
+            // the level again (its balanced supports are already judged, so
+            // only the per-child counters are rolled back)
+            if (!alloc_arena(w, nv, cur ^ 1, (int64_t)h[C_WRITTEN] + (int64_t)h[C_WRITTEN] / 8 + 1024, s))
+                return EFM_ENOMEM;
+            const int back[] = {C_EXP, C_OVF, C_BAL, C_PRUNED};
+            for (int i : back) {
+                h[i] = snap[i];
+                CK(cudaMemcpyAsync(ctr + i, &snap[i], 8, cudaMemcpyHostToDevice, s));
+            }
+            CK(cudaStreamSynchronize(s));
         }
-        n_front = (int64_t)h[C_NEXT];
+        const bool unwritten = h[C_UNWRITTEN] != 0;
+        n_front = unwritten ? (int64_t)(h[C_NEXT] + h[C_UNV]) : (int64_t)h[C_NEXT];
         deg_sum = h[C_DEGSUM];
         c.levels = level - level0 + 1;
         cur ^= 1;
+        par_map = (const uint32_t *)w.live[cur].p;
         if (lim.max_frontier > 0 && n_front > lim.max_frontier) {
             status |= EFM_TRUNCATED;
             break;
         }
-        if (n_front > w.F_cap) return EFM_ECAPACITY;
+        if (unwritten) return EFM_ECAPACITY;  // unreachable: the loop above runs such a level again
         c.frontier += n_front;
         c.frontier_max = std::max<int64_t>(c.frontier_max, n_front);
         if (lim.max_results > 0 && (int64_t)h[C_RES] >= lim.max_results) {
@@ -690,6 +781,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
     c.candidates = (int64_t)h[C_CAND_N];
     c.results = (int64_t)h[C_RES];
     c.pruned = (int64_t)h[C_PRUNED];
+    c.zero_flux = (int64_t)h[C_ZERO];
     if (c.overflow) status |= EFM_OVERFLOW_DROPPED;
     c.status = status;
     out.status = status;
@@ -720,7 +812,7 @@ extern "C" int efm_find_pathways(efm_net *net, const int32_t *targets, int32_t n
     job->net = net;
     job->out.resize(n_targets);
     Work w;
-    const int total_warps = expand_grid(net->nv, net->sm_count) * kExpandWarps;
+    const int total_warps = generate_grid(net->nv, net->sm_count) * kExpandWarps;
     int rc = alloc_work(w, net, lim, total_warps, net->stream);
     int flags = 0;
     for (int i = 0; rc == EFM_OK && i < n_targets; ++i) {
@@ -764,7 +856,7 @@ extern "C" int efm_find_pathways_from(efm_net *net, const int32_t *columns, int3
     cudaStream_t s = net->stream;
     Work w;
     DevBuf cols;
-    const int total_warps = expand_grid(net->nv, net->sm_count) * kExpandWarps;
+    const int total_warps = generate_grid(net->nv, net->sm_count) * kExpandWarps;
     int rc = alloc_work(w, net, lim, total_warps, s);
     if (rc == EFM_OK && !dev_alloc(cols, (size_t)n_columns * 4, s)) rc = EFM_ENOMEM;
     if (rc == EFM_OK && cudaMemcpyAsync(cols.p, columns, (size_t)n_columns * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -1611,7 +1703,7 @@ extern "C" int efm_model_trace(efm_model *m, efm_net *net, const int32_t *target
     for (int i = 0; i < n_targets; ++i)
         if (targets[i] < -1 || targets[i] >= net->n_met) return EFM_EINVAL;
     Work w;
-    const int total_warps = expand_grid(net->nv, net->sm_count) * kExpandWarps;
+    const int total_warps = generate_grid(net->nv, net->sm_count) * kExpandWarps;
     int rc = alloc_work(w, net, lim, total_warps, net->stream);
     for (int i = 0; rc == EFM_OK && i < n_targets; ++i) {
         TargetOut ans;

@@ -34,10 +34,15 @@ enum {
     C_CAND_N,     // candidate list length (cumulative)
     C_RES_N,      // result list length (cumulative)
     C_ERR,        // ERR_* bits
+    C_WRITTEN,    // generate/dedup split: child rows reserved so far in the level
+    C_UNWRITTEN,  // children whose row did not fit the child arena
+    C_UNV,        // distinct fingerprints among the children without a row
     C_OUT_N = 20, // batched traversal: rows written to the job's output
     C_DONE,       // batched traversal: job finished
     C_ACC_BEGIN,  // first candidate the next device-range minimality launch judges
+    C_DEDUP_BEGIN,  // first reserved row the next dedup launch examines
     C_DIAG = 24,  // first bounds/watchdog record: code, value, limit, level
+    C_ZERO = 28,  // subtractive steps discarded: no positive flux left on the reaction (Prop. 3)
     C_COUNT = 32
 };
 
@@ -94,7 +99,15 @@ struct LevelArgs {
     const uint32_t *perm;       // parent order: position -> arena index (null = arena order)
     int fk_pc;                  // bound: |U| of the K-th smallest result found so far (0 = no bound)
     const uint64_t *fk_sup;     // bound: its support (W words)
+    // generate/dedup split (single-job traversal): every surviving child gets
+    // a reserved row and a fingerprint; the dedup pass keeps one per state
+    uint64_t *fp;               // [fp_cap] fingerprint per reserved row (kDeadFp: unused)
+    int64_t fp_cap;
+    uint32_t *live;             // dedup output: arena rows of the distinct children
+    int blk;                    // rows a warp reserves at a time (NG..32)
 };
+
+constexpr unsigned long long kDeadFp = ~0ull;  // fingerprint of a reserved row left unused
 
 constexpr int kRcolStride = 65;  // column count + up to 64 columns per result
 
@@ -157,10 +170,12 @@ __host__ __device__ inline uint32_t mlp_blk_off(int row, int k)
 }
 
 // kernels (efm_mlp.cu)
-cudaError_t launch_features(const NetView &nv, const Arena &par, int64_t first, int64_t stride, int64_t n, int level,
-                            int max_len, int max_sec, const uint64_t *dep, void *X, int64_t row0, cudaStream_t s);
-cudaError_t launch_labels(const uint64_t *U, int W, int64_t first, int64_t stride, int64_t n, const uint64_t *ans,
-                          int64_t n_ans, float *y, int64_t row0, cudaStream_t s);
+// map: frontier position -> arena row (null: identity); rows r take positions first + r * stride
+cudaError_t launch_features(const NetView &nv, const Arena &par, const uint32_t *map, int64_t first, int64_t stride,
+                            int64_t n, int level, int max_len, int max_sec, const uint64_t *dep, void *X, int64_t row0,
+                            cudaStream_t s);
+cudaError_t launch_labels(const uint64_t *U, int W, const uint32_t *map, int64_t first, int64_t stride, int64_t n,
+                          const uint64_t *ans, int64_t n_ans, float *y, int64_t row0, cudaStream_t s);
 cudaError_t launch_mlp_score(const void *X, int64_t n_rows, const void *wb, const float *params, float *score,
                              unsigned *err, cudaStream_t s);
 cudaError_t launch_mlp_train(const void *X, const float *y, int64_t n_rows, const int32_t *tiles, int n_tiles,
@@ -168,7 +183,9 @@ cudaError_t launch_mlp_train(const void *X, const float *y, int64_t n_rows, cons
                              float *loss, unsigned *err, cudaStream_t s);
 cudaError_t launch_adam(float *params, float *grad, float *mom, float lr, int step, void *wb, cudaStream_t s);
 cudaError_t launch_pack_w(const float *params, void *wb, cudaStream_t s);
-cudaError_t launch_score_order(const float *score, int64_t n, unsigned *hist, uint32_t *perm, cudaStream_t s);
+// perm[i] = map[position of the i-th highest score] (map null: the position itself)
+cudaError_t launch_score_order(const float *score, int64_t n, const uint32_t *map, unsigned *hist, uint32_t *perm,
+                               cudaStream_t s);
 cudaError_t launch_pack_rows(const float *x, int64_t n, void *X, int64_t row0, cudaStream_t s);
 size_t mlp_score_smem();
 size_t mlp_train_smem();
@@ -176,6 +193,11 @@ size_t mlp_train_smem();
 // kernels (efm_kernels.cu)
 cudaError_t launch_seed(const NetView &nv, const LevelArgs &a, int target, cudaStream_t s);
 cudaError_t launch_expand(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s);
+// generate/dedup split of one expansion: children with rows and fingerprints,
+// then one pass that keeps the first row of every distinct state
+cudaError_t launch_generate(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_dedup(const LevelArgs &a, int Mpad, int W, int sm_count, cudaStream_t s);
+int generate_grid(const NetView &nv, int sm_count);
 cudaError_t launch_accept(const NetView &nv, const AcceptArgs &a, cudaStream_t s);
 // minimality test of the candidates appended since the last such launch (range read on the
 // device, so no host round trip is needed between expansion and test); then advance the range

@@ -1234,6 +1234,443 @@ __global__ void __launch_bounds__(kExpandWarps * 32, (CPL <= 2 ? 3 : 2)) expand_
 }
 
 // ---------------------------------------------------------------------------
+// a1-a5 as two passes (single-job traversal): generate, then deduplicate.
+//
+// Generate: the same per-item work as phase 1 above (branch selection, AND
+// update, balance test, superset rule, pivot key, fingerprint), but every
+// surviving unbalanced child is written straight from registers to a row of
+// the child arena that its warp reserved in advance (rows are reserved blk
+// at a time with one atomic), together with its 64-bit fingerprint.  Nothing
+// waits on another child: no hash-table probe, no publish/compare protocol.
+// Children whose reserved row lies past the arena's capacity keep only their
+// fingerprint (the level is then decided from fingerprints, or run again
+// with a larger arena).
+//
+// Dedup: one thread per reserved row inserts (tag, row) into the level's
+// hash table with a plain CAS.  Every row was written by the previous
+// launch, so a tag match is settled at once by comparing the two rows; the
+// first row of every distinct (U, EF) survives and is appended to the live
+// list, which the next level reads its parents through.
+// ---------------------------------------------------------------------------
+
+template <int G, int CPL>
+__device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint32_t *bl, int64_t worker,
+                               int64_t nworkers)
+{
+    constexpr int NG = 32 / G;    // children per warp round
+    constexpr int EPL = 4 * CPL;  // balance entries per lane
+    const int lane = threadIdx.x & 31;
+    const int gi = lane / G;  // group in the warp
+    const int gl = lane % G;  // lane in the group
+    const int lead = gi * G;  // group leader lane
+    const int W = nv.W;
+    const int Mpad = nv.Mpad;
+    const int4 *dcol = reinterpret_cast<const int4 *>(bl + nv.o_dcols);
+    const int64_t row_cap = a.child.cap;
+
+    unsigned long long n_exp = 0, n_ovf = 0, n_bal = 0, n_pruned = 0, n_unwritten = 0;
+    bool fatal = false;
+    // this warp's reserved rows: [pool_next, pool_next + pool_left)
+    uint64_t pool_next = 0;
+    int pool_left = 0;
+
+    const int cpw = a.cpw;
+    const int64_t wstride = nworkers * cpw;
+    for (int64_t p0 = worker * cpw; p0 < a.n_par; p0 += wstride) {
+        const int64_t pl = p0 + lane;
+        const bool pin = lane < cpw && pl < a.n_par;
+        const int64_t pid = pin ? (a.perm ? (int64_t)a.perm[pl] : pl) : 0;  // this lane's parent
+        const int64_t pn = pl + wstride;
+        if (lane < cpw && pn < a.n_par) {
+            const int64_t nid = a.perm ? (int64_t)a.perm[pn] : pn;
+            const char *rp = reinterpret_cast<const char *>(a.par.B + (size_t)nid * Mpad);
+            for (int off = 0; off < Mpad * 4; off += 128) prefetch_l2(rp + off);
+            prefetch_l2(a.par.U + (size_t)nid * W);
+            prefetch_l2(a.par.meta + nid);
+        }
+        const uint32_t mj = pin ? a.par.meta[pid] : 0u;
+        int dj = pin ? (int)((mj >> 10) & 0x1FFFu) : 0;
+        // first-K: a parent larger than the bound has no descendant among the K smallest
+        if (a.fk_pc > 0 && (int)((mj >> 23) & 0x7Fu) > a.fk_pc) dj = 0;
+        int incl = dj;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int x = __shfl_up_sync(FULL, incl, off);
+            if (lane >= off) incl += x;
+        }
+        const int prej = incl - dj;
+        const int T = __shfl_sync(FULL, incl, 31);
+        if (T > 32 * nv.N) {
+            if (lane == 0) record_diag(a.ctr, ERR_BOUNDS, 3, T, 32 * nv.N, a.level);
+            fatal = true;
+        }
+        for (int base = 0; base < T; base += 32) {
+            if (__any_sync(FULL, fatal)) break;
+            // --- branch selection: one (parent, branch) item per lane ---
+            const int c = base + lane;
+            int j = 0;  // largest j with pre_j <= c
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int v = __shfl_sync(FULL, prej, j + step);
+                if (v <= c) j += step;
+            }
+            const uint32_t pm = __shfl_sync(FULL, mj, j);
+            const int q = c - __shfl_sync(FULL, prej, j);
+            const int64_t pl_ = __shfl_sync(FULL, pid, j);
+            bool okl = c < T;
+            int kl = 0, pcl = 0;
+            bool inl = false;
+            int32_t Al = 0, Cl = 0;
+            if (okl) {
+                const int32_t *prow_l = a.par.B + (size_t)pl_ * Mpad;
+                const uint64_t *pu_l = a.par.U + (size_t)pl_ * W;
+                const int piv = (int)(pm & 0x3FFu);
+                pcl = (int)((pm >> 23) & 0x7Fu);
+                const int32_t bi = piv < nv.M ? prow_l[piv] : 0;
+                const bool fwd = bi > 0;  // forward flow: consume the surplus
+                const uint32_t abi = (uint32_t)(bi < 0 ? -bi : bi);
+                const int lptr = (fwd ? nv.o_consptr : nv.o_prodptr) + (piv < nv.M ? piv : 0);
+                const int lb = (int)bl[lptr];
+                const int le = (int)bl[lptr + 1];
+                if (piv >= nv.M || bi == 0 || lb + q >= le) {
+                    record_diag(a.ctr, ERR_BOUNDS, 1 + (piv >= nv.M ? 10 : 0) + (bi == 0 ? 100 : 0), (long long)q,
+                                (long long)(le - lb), a.level);
+                    fatal = true;
+                    okl = false;
+                } else {
+                    const uint32_t br = bl[(fwd ? nv.o_consent : nv.o_prodent) + lb + q];
+                    kl = ent_index(br);
+                    const uint32_t sik = (uint32_t)ent_coef(br);  // |S_ik|
+                    const int tw = (int)bl[nv.o_twin + kl];
+                    inl = bit_of(pu_l, kl);
+                    const int sec = a.level - pcl;
+                    okl = !(tw >= 0 && bit_of(pu_l, tw)) && (inl ? sec + 1 <= a.max_sec : pcl + 1 <= a.max_len);
+                    if (okl && a.fk_pc > 0) {
+                        const int pc2 = pcl + (inl ? 0 : 1);
+                        okl = pc2 < a.fk_pc || (pc2 == a.fk_pc && !child_after(pu_l, kl, a.fk_sup, W));
+                    }
+                    const uint32_t g0 = (abi == 1u || sik == 1u) ? 1u : gcd32(abi, sik);
+                    Al = (int32_t)(sik / g0);
+                    Cl = (int32_t)(abi / g0);
+                }
+            }
+            if (okl) ++n_exp;
+            const uint32_t infol = (uint32_t)kl | ((uint32_t)pcl << 12) | (inl ? 1u << 19 : 0u);
+            const uint32_t pl32 = (uint32_t)pl_;
+            // the groups take the valid items of this pass NG at a time, in order
+            unsigned vmask = __ballot_sync(FULL, okl);
+            while (vmask) {
+                if (__any_sync(FULL, fatal)) break;
+                const int src = gi < __popc(vmask) ? (int)__fns(vmask, 0, gi + 1) : -1;
+#pragma unroll
+                for (int t = 0; t < NG; ++t) vmask &= vmask - 1;
+                const int sl = src < 0 ? 0 : src;
+                const bool ok = src >= 0;
+                const uint32_t info_i = __shfl_sync(FULL, infol, sl);
+                const int k = (int)(info_i & 0xFFFu);
+                const int pc = (int)((info_i >> 12) & 0x7Fu);
+                const bool in_u = (info_i >> 19) & 1u;
+                const int32_t A = __shfl_sync(FULL, Al, sl);
+                const int32_t C = __shfl_sync(FULL, Cl, sl);
+                const int64_t p = (int64_t)__shfl_sync(FULL, pl32, sl);
+                const int32_t *prow = a.par.B + (size_t)p * Mpad;
+                const uint64_t *pu = a.par.U + (size_t)p * W;
+
+                // --- AND update (Eq. 3 / Eq. 4 in integers), group-parallel ---
+                int32_t t32[EPL];
+                uint32_t fl = 0;  // bit0 nonzero, bit1 some |t| == 1, bit2 some t outside int32
+                const int4 *prow4 = reinterpret_cast<const int4 *>(prow);
+                const int4 *col4 = dcol + (size_t)k * (Mpad >> 2);
+                if (ok) {
+#pragma unroll
+                    for (int i = 0; i < CPL; ++i) {
+                        const int4 v = prow4[gl + G * i];
+                        const int4 w = col4[gl + G * i];
+                        const int32_t pv[4] = {v.x, v.y, v.z, v.w}, cv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) {
+                            const int64_t tt = (int64_t)A * pv[jj] + (int64_t)C * cv[jj];
+                            const int32_t lo = (int32_t)tt;
+                            const bool fits = tt == (int64_t)lo && lo != INT32_MIN;
+                            t32[4 * i + jj] = lo;
+                            fl |= (tt != 0 ? 1u : 0u) | ((lo == 1 || lo == -1) ? 2u : 0u) | (fits ? 0u : 4u);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) t32[e] = 0;
+                }
+                fl = group_or<G>(fl);
+                const bool nz = fl & 1u;
+                // slow path: the gcd is needed (no unit entry), or an entry is
+                // outside int32 (then the raw entries are recomputed in 64 bits)
+                const bool slow = ok && nz && ((fl & 6u) != 2u);
+                const bool big = (fl & 4u) != 0u;
+                bool ovf = false;
+                if (__any_sync(FULL, slow)) {
+                    uint64_t gg = 0, amax = 0;
+                    if (slow && !big) {
+#pragma unroll
+                        for (int e = 0; e < EPL; ++e) {
+                            const uint32_t at = (uint32_t)(t32[e] < 0 ? -t32[e] : t32[e]);
+                            if (at != 0) gg = gg == 0 ? at : gcd32((uint32_t)gg, at);
+                        }
+                    } else if (slow) {
+                        const GcdMax gm = raw_gcd_max(prow4, col4, gl, G, CPL, A, C);
+                        gg = gm.g;
+                        amax = gm.m;
+                    }
+#pragma unroll
+                    for (int off = G / 2; off > 0; off >>= 1) {
+                        const uint64_t og = __shfl_xor_sync(FULL, gg, off);
+                        gg = og == 0 ? gg : (gg == 0 ? og : gcd64(gg, og));
+                        const uint64_t y = __shfl_xor_sync(FULL, amax, off);
+                        amax = y > amax ? y : amax;
+                    }
+                    if (slow) {
+                        ovf = big && amax / gg > 2147483647ull;
+                        if (!ovf && gg > 1) {
+                            const bool pow2 = (gg & (gg - 1)) == 0;
+                            const int sh = __ffsll((long long)gg) - 1;
+                            if (!big) {
+#pragma unroll
+                                for (int e = 0; e < EPL; ++e)
+                                    t32[e] = t32[e] == 0 ? 0 : (pow2 ? (t32[e] >> sh) : t32[e] / (int32_t)gg);
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < CPL; ++i) {
+                                    const int4 v = prow4[gl + G * i];
+                                    const int4 w = col4[gl + G * i];
+                                    const int32_t pv[4] = {v.x, v.y, v.z, v.w}, cv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                                    for (int jj = 0; jj < 4; ++jj) {
+                                        const int64_t tt = (int64_t)A * pv[jj] + (int64_t)C * cv[jj];
+                                        t32[4 * i + jj] = (int32_t)(tt / (int64_t)gg);
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+                const bool bal = ok && !nz;
+                const bool grown = ok && nz && !ovf;
+                if (ovf && gl == 0) ++n_ovf;
+                if (bal && gl == 0) {
+                    ++n_bal;  // all metabolites stable: to the arbiter
+                    if (insert_support(a, W, pu, k) < INS_DUP) fatal = true;
+                }
+                fatal = group_or<G>(fatal ? 1u : 0u) != 0;
+                // superset rule: the new column k completes a result accepted
+                // at an earlier level (the group's lanes split its bucket)
+                bool pr = false;
+                if (grown && !in_u) {
+                    const int64_t b1 = a.bptr[k];
+                    const int64_t n = a.bptr[k + 1] - b1;
+                    if (W <= 2) {
+                        const uint64_t u0 = child_word(pu, 0, k), u1 = W == 2 ? child_word(pu, 1, k) : 0ull;
+                        bool maybe = n > 0;
+                        if (maybe && a.band) {
+                            const uint64_t i0 = __ldg(a.band + (size_t)k * W), i1 = W == 2 ? __ldg(a.band + (size_t)k * W + 1) : 0ull;
+                            maybe = ((i0 & ~u0) | (i1 & ~u1)) == 0;
+                        }
+                        for (int64_t i = gl; i < n && !pr && maybe; i += G) {
+                            const uint64_t *E = a.bres + (size_t)(b1 + i) * W;
+                            const uint64_t e0 = __ldg(E), e1 = W == 2 ? __ldg(E + 1) : 0ull;
+                            pr = ((e0 & ~u0) | (e1 & ~u1)) == 0;
+                        }
+                    } else {
+                        for (int64_t i = gl; i < n && !pr; i += G) pr = result_inside_wide(a, pu, k, b1 + i);
+                    }
+                }
+                pr = group_or<G>(pr ? 1u : 0u) != 0;
+                if (pr && gl == 0) ++n_pruned;
+                const bool norm = grown && !pr;
+
+                // --- pivot key and fingerprint ---
+                uint32_t key = 0xFFFFFFFFu, hlo = 0, hhi = 0;
+                if (norm) {
+#pragma unroll
+                    for (int i = 0; i < CPL; ++i)
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) {
+                            const int m = 4 * (gl + G * i) + jj;
+                            const int32_t v = t32[4 * i + jj];
+                            if (v != 0) {
+                                const uint32_t kk = bl[(v > 0 ? nv.o_keypos : nv.o_keyneg) + m];
+                                key = kk < key ? kk : key;
+                            }
+                            hash_entry((uint32_t)m, (uint32_t)v, hlo, hhi);
+                        }
+                    for (int w = gl; w < W; w += G) {
+                        const uint64_t x = mix64(child_word(pu, w, k) ^ (0x2545f4914f6cdd1dull * (uint64_t)(w + 1)));
+                        hlo += (uint32_t)x;
+                        hhi ^= (uint32_t)(x >> 32);
+                    }
+                }
+                key = group_min<G>(key);
+                hlo = group_add<G>(hlo);
+                hhi = group_xor<G>(hhi);
+
+                // --- a reserved row for every surviving child of the round ---
+                const unsigned nm = __ballot_sync(FULL, norm && gl == 0);
+                const int cnt = __popc(nm);
+                if (cnt > 0) {
+                    const int rank = __popc(nm & ((1u << lead) - 1u));
+                    uint64_t fresh = 0;
+                    if (pool_left < cnt) {
+                        if (lane == 0) fresh = atomicAdd(&a.ctr[C_WRITTEN], (unsigned long long)a.blk);
+                        fresh = __shfl_sync(FULL, fresh, 0);
+                    }
+                    const uint64_t idx = rank < pool_left ? pool_next + (uint64_t)rank
+                                                          : fresh + (uint64_t)(rank - pool_left);
+                    if (pool_left < cnt) {
+                        pool_next = fresh + (uint64_t)(cnt - pool_left);
+                        pool_left = a.blk - (cnt - pool_left);
+                    } else {
+                        pool_next += (uint64_t)cnt;
+                        pool_left -= cnt;
+                    }
+                    if (norm) {
+                        if ((int64_t)idx < row_cap) {
+                            int4 *db = reinterpret_cast<int4 *>(a.child.B + (size_t)idx * Mpad);
+#pragma unroll
+                            for (int i = 0; i < CPL; ++i)
+                                db[gl + G * i] = make_int4(t32[4 * i + 0], t32[4 * i + 1], t32[4 * i + 2], t32[4 * i + 3]);
+                            uint64_t *du = a.child.U + (size_t)idx * W;
+                            for (int w = gl; w < W; w += G) du[w] = child_word(pu, w, k);
+                            if (gl == 0) a.child.meta[idx] = pack_meta(key, pc + (in_u ? 0 : 1));
+                        } else if (gl == 0) {
+                            ++n_unwritten;
+                        }
+                        if (gl == 0) {
+                            if ((int64_t)idx < a.fp_cap) {
+                                uint64_t f = ((uint64_t)hhi << 32) | hlo;
+                                if (f == kDeadFp) f = kDeadFp - 1;
+                                a.fp[idx] = f;
+                            } else {
+                                record_diag(a.ctr, ERR_BOUNDS, 7, (long long)idx, a.fp_cap, a.level);
+                                fatal = true;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (__any_sync(FULL, fatal)) break;
+    }
+    // rows reserved but not used: marked so that the dedup pass skips them
+    if (lane < pool_left && (int64_t)(pool_next + lane) < a.fp_cap) a.fp[pool_next + lane] = kDeadFp;
+    if (n_exp) atomicAdd(&a.ctr[C_EXP], n_exp);
+    if (n_ovf) atomicAdd(&a.ctr[C_OVF], n_ovf);
+    if (n_bal) atomicAdd(&a.ctr[C_BAL], n_bal);
+    if (n_pruned) atomicAdd(&a.ctr[C_PRUNED], n_pruned);
+    if (n_unwritten) atomicAdd(&a.ctr[C_UNWRITTEN], n_unwritten);
+}
+
+template <int G, int CPL>
+__global__ void __launch_bounds__(kExpandWarps * 32, (CPL <= 2 ? 3 : 2)) generate_kernel(NetView nv, LevelArgs a,
+                                                                                      int staged)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int wid = threadIdx.x >> 5;
+    const int blob_words = staged ? nv.blob_words : 0;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + blob_words);
+    const uint32_t *bl = stage_blob(nv, smem, mbar, staged != 0, a.ctr);
+    if (bl == nullptr) return;
+    generate_range<G, CPL>(nv, a, bl, (int64_t)blockIdx.x * kExpandWarps + wid, (int64_t)gridDim.x * kExpandWarps);
+}
+
+// Are reserved rows i and j the same state (support and extra-flux row)?
+__device__ __forceinline__ bool same_state(const Arena &ar, int Mpad, int W, uint64_t i, uint64_t j)
+{
+    const int4 *x = reinterpret_cast<const int4 *>(ar.B + (size_t)i * Mpad);
+    const int4 *y = reinterpret_cast<const int4 *>(ar.B + (size_t)j * Mpad);
+    bool eq = true;
+    for (int c = 0; c < (Mpad >> 2) && eq; ++c) {
+        const int4 u = __ldcg(x + c), v = __ldcg(y + c);
+        eq = u.x == v.x && u.y == v.y && u.z == v.z && u.w == v.w;
+    }
+    const uint64_t *ux = ar.U + (size_t)i * W, *uy = ar.U + (size_t)j * W;
+    for (int w = 0; w < W && eq; ++w) eq = __ldcg(ux + w) == __ldcg(uy + w);
+    return eq;
+}
+
+// One thread per reserved row in [ctr[C_DEDUP_BEGIN], ctr[C_WRITTEN]).
+__global__ void __launch_bounds__(256) dedup_kernel(LevelArgs a, int Mpad, int W)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t begin = a.ctr[C_DEDUP_BEGIN];
+    uint64_t end = a.ctr[C_WRITTEN];
+    end = end < (uint64_t)a.fp_cap ? end : (uint64_t)a.fp_cap;
+    const uint64_t row_cap = (uint64_t)a.child.cap;
+    unsigned long long deg = 0, n_unv = 0;
+    bool fatal = false;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    // warp-uniform trip count so that the ballots below see the whole warp
+    for (uint64_t i0 = begin + (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < end; i0 += stride) {
+        const uint64_t i = i0 + lane;
+        bool mine = i < end;
+        const uint64_t f = mine ? a.fp[i] : kDeadFp;
+        mine = mine && f != kDeadFp;
+        bool keep = false;  // distinct state with a row: survives into the next frontier
+        if (mine) {
+            uint64_t pos;
+            uint32_t tag;
+            slot_tag_pos(f, a.slot_mask, pos, tag);
+            const bool written = i < row_cap;
+            for (uint64_t probe = 0;; ++probe) {
+                if (probe > a.slot_mask) {
+                    record_diag(a.ctr, ERR_TABLE_FULL, 8, (long long)i, (long long)a.slot_mask, a.level);
+                    fatal = true;
+                    break;
+                }
+                const unsigned long long v = atomicCAS(&a.slots[pos], kEmpty, ((unsigned long long)tag << 32) | i);
+                if (v == kEmpty) {  // first of its state
+                    if (written)
+                        keep = true;
+                    else
+                        ++n_unv;
+                    break;
+                }
+                if ((uint32_t)(v >> 32) == tag) {
+                    const uint64_t jrow = (uint32_t)v;
+                    // a row without its state written cannot be compared: the
+                    // level is then decided from the lower bound, or run again
+                    if (!written || jrow >= row_cap) break;
+                    if (same_state(a.child, Mpad, W, i, jrow)) break;  // duplicate
+                }
+                pos = (pos + 1) & a.slot_mask;
+            }
+        }
+        const unsigned km = __ballot_sync(FULL, keep);
+        if (km) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&a.ctr[C_NEXT], (unsigned long long)__popc(km));
+            base = __shfl_sync(FULL, base, 0);
+            if (keep) {
+                const uint64_t slot = base + (uint64_t)__popc(km & ((1u << lane) - 1u));
+                if (slot < row_cap) {
+                    a.live[slot] = (uint32_t)i;
+                    deg += (a.child.meta[i] >> 10) & 0x1FFFu;
+                }
+            }
+        }
+        if (__any_sync(FULL, fatal)) break;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        deg += __shfl_xor_sync(FULL, deg, off);
+        n_unv += __shfl_xor_sync(FULL, n_unv, off);
+    }
+    if (lane == 0) {
+        if (deg) atomicAdd(&a.ctr[C_DEGSUM], deg);
+        if (n_unv) atomicAdd(&a.ctr[C_UNV], n_unv);
+    }
+}
+
+__global__ void dedup_advance_kernel(unsigned long long *ctr) { ctr[C_DEDUP_BEGIN] = ctr[C_WRITTEN]; }
+
+// ---------------------------------------------------------------------------
 // a7/a8: exact minimality test by elimination modulo primes, then append.
 // ---------------------------------------------------------------------------
 
@@ -1817,6 +2254,37 @@ cudaError_t launch_expand_t(const NetView &nv, const LevelArgs &a, int grid, cud
 }
 
 template <int G, int CPL>
+cudaError_t launch_generate_t(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s)
+{
+    const bool staged = nv.blob_words * 4 <= kStageLimitBytes;
+    const size_t sm = (size_t)(staged ? nv.blob_words : 0) * 4 + 16;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(generate_kernel<G, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kStageLimitBytes + 16);
+        attr_set = true;
+    }
+    generate_kernel<G, CPL><<<grid, kExpandWarps * 32, sm, s>>>(nv, a, staged ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <int G, int CPL>
+int generate_grid_t(const NetView &nv, int sm_count)
+{
+    const bool staged = nv.blob_words * 4 <= kStageLimitBytes;
+    const size_t sm = (size_t)(staged ? nv.blob_words : 0) * 4 + 16;
+    cudaFuncSetAttribute(generate_kernel<G, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageLimitBytes + 16);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, generate_kernel<G, CPL>, kExpandWarps * 32, sm) !=
+            cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return sm_count * per_sm;
+}
+
+template <int G, int CPL>
 int expand_grid_t(const NetView &nv, int sm_count)
 {
     const bool staged = nv.blob_words * 4 <= kStageLimitBytes;
@@ -1873,6 +2341,29 @@ cudaError_t launch_expand(const NetView &nv, const LevelArgs &a, int grid, cudaS
     EFM_GROUP_DISPATCH(nv.EPL, CALL_EXP)
 #undef CALL_EXP
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_generate(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s)
+{
+#define CALL_GEN(G, C) launch_generate_t<G, C>(nv, a, grid, s)
+    EFM_GROUP_DISPATCH(nv.EPL, CALL_GEN)
+#undef CALL_GEN
+    return cudaErrorInvalidValue;
+}
+
+int generate_grid(const NetView &nv, int sm_count)
+{
+#define CALL_GGRID(G, C) generate_grid_t<G, C>(nv, sm_count)
+    EFM_GROUP_DISPATCH(nv.EPL, CALL_GGRID)
+#undef CALL_GGRID
+    return sm_count;
+}
+
+cudaError_t launch_dedup(const LevelArgs &a, int Mpad, int W, int sm_count, cudaStream_t s)
+{
+    dedup_kernel<<<sm_count * 8, 256, 0, s>>>(a, Mpad, W);
+    dedup_advance_kernel<<<1, 1, 0, s>>>(a.ctr);
+    return cudaGetLastError();
 }
 
 int expand_grid(const NetView &nv, int sm_count)

@@ -163,15 +163,17 @@ __device__ __forceinline__ uint32_t col_hash(uint32_t k)
 // ---------------------------------------------------------------------------
 constexpr int kFeatWarps = 8;
 
-__global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(NetView nv, Arena par, int64_t first, int64_t stride,
-                                                                   int64_t n, int level, int max_len, int max_sec,
-                                                                   const uint64_t *dep, __nv_bfloat16 *X, int64_t row0)
+__global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(NetView nv, Arena par, const uint32_t *map,
+                                                                   int64_t first, int64_t stride, int64_t n, int level,
+                                                                   int max_len, int max_sec, const uint64_t *dep,
+                                                                   __nv_bfloat16 *X, int64_t row0)
 {
     __shared__ float emb[kFeatWarps][64];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int W = nv.W;
     for (int64_t r = (int64_t)blockIdx.x * kFeatWarps + wid; r < n; r += (int64_t)gridDim.x * kFeatWarps) {
-        const int64_t p = first + r * stride;
+        const int64_t pos = first + r * stride;
+        const int64_t p = map ? (int64_t)map[pos] : pos;
         const uint64_t *U = par.U + (size_t)p * W;
         const int32_t *B = par.B + (size_t)p * nv.Mpad;
         const uint32_t meta = par.meta[p];
@@ -290,13 +292,14 @@ __global__ void __launch_bounds__(kFeatWarps * 32) features_kernel(NetView nv, A
 
 // Training label of a sampled state: 1 when its support lies inside one of
 // the answer's supports (the state can still reach that answer).
-__global__ void labels_kernel(const uint64_t *Uar, int W, int64_t first, int64_t stride, int64_t n,
-                              const uint64_t *ans, int64_t n_ans, float *y, int64_t row0)
+__global__ void labels_kernel(const uint64_t *Uar, int W, const uint32_t *map, int64_t first, int64_t stride,
+                              int64_t n, const uint64_t *ans, int64_t n_ans, float *y, int64_t row0)
 {
     const int lane = threadIdx.x & 31;
     for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n;
          r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        const uint64_t *U = Uar + (size_t)(first + r * stride) * W;
+        const int64_t pos = first + r * stride;
+        const uint64_t *U = Uar + (size_t)(map ? (int64_t)map[pos] : pos) * W;
         bool in = false;
         for (int64_t a = lane; a < n_ans && !in; a += 32) {
             const uint64_t *A = ans + (size_t)a * W;
@@ -645,11 +648,12 @@ __global__ void score_scan_kernel(unsigned *hist)
     }
 }
 
-__global__ void score_scatter_kernel(const float *score, int64_t n, unsigned *offs, uint32_t *perm)
+__global__ void score_scatter_kernel(const float *score, int64_t n, const uint32_t *map, unsigned *offs,
+                                     uint32_t *perm)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const unsigned pos = atomicAdd(&offs[score_bucket(score[i])], 1u);
-        perm[pos] = (uint32_t)i;
+        perm[pos] = map ? map[i] : (uint32_t)i;
     }
 }
 
@@ -678,22 +682,24 @@ int sm_count_cached()
 
 }  // namespace
 
-cudaError_t launch_features(const NetView &nv, const Arena &par, int64_t first, int64_t stride, int64_t n, int level,
-                            int max_len, int max_sec, const uint64_t *dep, void *X, int64_t row0, cudaStream_t s)
+cudaError_t launch_features(const NetView &nv, const Arena &par, const uint32_t *map, int64_t first, int64_t stride,
+                            int64_t n, int level, int max_len, int max_sec, const uint64_t *dep, void *X, int64_t row0,
+                            cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     const int64_t blocks = std::min<int64_t>((n + kFeatWarps - 1) / kFeatWarps, (int64_t)sm_count_cached() * 16);
-    features_kernel<<<(unsigned)blocks, kFeatWarps * 32, 0, s>>>(nv, par, first, stride, n, level, max_len, max_sec,
-                                                                 dep, reinterpret_cast<__nv_bfloat16 *>(X), row0);
+    features_kernel<<<(unsigned)blocks, kFeatWarps * 32, 0, s>>>(nv, par, map, first, stride, n, level, max_len,
+                                                                 max_sec, dep, reinterpret_cast<__nv_bfloat16 *>(X),
+                                                                 row0);
     return cudaGetLastError();
 }
 
-cudaError_t launch_labels(const uint64_t *U, int W, int64_t first, int64_t stride, int64_t n, const uint64_t *ans,
-                          int64_t n_ans, float *y, int64_t row0, cudaStream_t s)
+cudaError_t launch_labels(const uint64_t *U, int W, const uint32_t *map, int64_t first, int64_t stride, int64_t n,
+                          const uint64_t *ans, int64_t n_ans, float *y, int64_t row0, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     const int64_t blocks = std::min<int64_t>((n + 7) / 8, (int64_t)sm_count_cached() * 16);
-    labels_kernel<<<(unsigned)blocks, 256, 0, s>>>(U, W, first, stride, n, ans, n_ans, y, row0);
+    labels_kernel<<<(unsigned)blocks, 256, 0, s>>>(U, W, map, first, stride, n, ans, n_ans, y, row0);
     return cudaGetLastError();
 }
 
@@ -737,7 +743,8 @@ cudaError_t launch_pack_w(const float *params, void *wb, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_score_order(const float *score, int64_t n, unsigned *hist, uint32_t *perm, cudaStream_t s)
+cudaError_t launch_score_order(const float *score, int64_t n, const uint32_t *map, unsigned *hist, uint32_t *perm,
+                               cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(hist, 0, kScoreBuckets * 4, s);
@@ -745,7 +752,7 @@ cudaError_t launch_score_order(const float *score, int64_t n, unsigned *hist, ui
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count_cached() * 8);
     score_hist_kernel<<<blocks, 256, 0, s>>>(score, n, hist);
     score_scan_kernel<<<1, 1024, 0, s>>>(hist);
-    score_scatter_kernel<<<blocks, 256, 0, s>>>(score, n, hist, perm);
+    score_scatter_kernel<<<blocks, 256, 0, s>>>(score, n, map, hist, perm);
     return cudaGetLastError();
 }
 

@@ -18,7 +18,7 @@ from . import build as _build
 
 EFM_TRUNCATED, EFM_CAPPED, EFM_OVERFLOW_DROPPED = 1, 2, 4
 COUNTER_FIELDS = ("levels", "seeds", "expansions", "overflow", "balanced", "candidates", "results", "pruned",
-                  "frontier", "frontier_max", "status")
+                  "frontier", "frontier_max", "status", "zero_flux")
 EXPORTS = ("efm_load_network", "efm_network_shape", "efm_column_map", "efm_find_pathways", "efm_fetch_results",
            "efm_job_timing", "efm_free_job", "efm_free_net", "efm_status_str", "efm_set_allocator",
            "efm_sort_supports_noalloc", "efm_find_pathways_batch", "efm_batch_tuning", "efm_model_create",

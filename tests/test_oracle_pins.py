@@ -31,7 +31,7 @@ def _handworked():
 @pytest.mark.parametrize("case", _handworked(), ids=lambda c: c["name"])
 def test_handworked(oracle_lib, case):
     net = synth.Network.from_dense(case["S"], case["reversible"], case["external"])
-    lim = oracle_lib.Limits(case["max_len"], case["max_secondary"], 0, 0)
+    lim = oracle_lib.Limits(case["max_len"], case["max_secondary"], 0, 0, subtractive=case.get("subtractive", False))
     sup, ctr = oracle_lib.enumerate_pathways(net, case["target"], lim)
     assert oracle_lib.supports_to_lists(sup) == [tuple(x) for x in case["expected"]]
     for k, v in case.get("counters", {}).items():
@@ -43,7 +43,8 @@ def test_handworked_python_reference_agrees(oracle_lib):
 
     for case in _handworked():
         net = synth.Network.from_dense(case["S"], case["reversible"], case["external"])
-        res, ctr = reference.enumerate_reference(net, case["target"], case["max_len"], case["max_secondary"])
+        run = reference.enumerate_subtractive if case.get("subtractive") else reference.enumerate_reference
+        res, ctr = run(net, case["target"], case["max_len"], case["max_secondary"])
         got = [tuple(k for k in range(64) if (U >> k) & 1) for U in res]
         assert got == [tuple(x) for x in case["expected"]], case["name"]
         for k, v in case.get("counters", {}).items():
@@ -277,7 +278,8 @@ def test_flux_vectors_hand_worked(oracle_lib):
             continue
         net = synth.Network.from_dense(case["S"], case["reversible"], case["external"])
         sup, _ = oracle_lib.enumerate_pathways(net, case["target"],
-                                               oracle_lib.Limits(case["max_len"], case["max_secondary"], 0, 0))
+                                               oracle_lib.Limits(case["max_len"], case["max_secondary"], 0, 0,
+                                                                 subtractive=case.get("subtractive", False)))
         assert flux.flux_vectors(net, sup) == case["flux"], case["name"]
 
 
