@@ -72,10 +72,25 @@ typedef struct {
     int32_t proposal;      /* order of a first-K search: EFM_PLAIN (arena order) or
                               EFM_LEARNED (scores of the model passed with the call); the
                               result set is the same either way */
+    int32_t variant;       /* EFM_ADDITIVE: flux is only ever added (Eq. 3, Eq. 4);
+                              EFM_SUBTRACTIVE: also Eq. 5 -- the acting metabolite may be
+                              balanced by taking flux away from a reaction already in the
+                              pathway that moves it the same way as its imbalance; a step
+                              that leaves that reaction with zero (or negative) flux is
+                              discarded (Prop. 3) and counted in zero_flux.  Such a step
+                              keeps the support and costs one secondary step.  States then
+                              carry their flux vector, so distinct states are distinct
+                              (support, flux ray); the network needs internal metabolites
+                              + split columns <= EFM_MAX_INTERNAL (else EFM_EUNSUPPORTED),
+                              and first_k must be 0.  efm_find_pathways and
+                              efm_find_pathways_from only (the batched call is additive). */
+    int32_t reserved;      /* must be 0 */
 } efm_limits;
 
 #define EFM_PLAIN 0
 #define EFM_LEARNED 1
+#define EFM_ADDITIVE 0
+#define EFM_SUBTRACTIVE 1
 
 /* Counters of one (network, target) traversal; the same definitions as the
  * CPU oracle's.  frontier / frontier_max exclude a truncated level. */

@@ -17,6 +17,9 @@
 #include "efm_netprep.h"
 #include "efm_topk.h"
 
+static_assert(efm::kNarrowKeyRanks == efm::kNarrowRows && efm::kColxWordsDev == efm::kColxWords,
+              "narrow-network table layout of the kernels and the loader");
+
 using namespace efm;
 
 namespace {
@@ -72,6 +75,11 @@ struct efm_net {
     std::vector<int8_t> col_dir;
     NetView nv{};
     DevBuf blob, metptr, metent;
+    // the subtractive traversal's view (rows of M + N entries: extra flux,
+    // then flux per column), when M + N fits a row
+    NetView nv_sub{};
+    DevBuf blob_sub;
+    bool has_sub = false;
     int sm_count = 0;
     DevBuf dep;             // DEPTHy tags (dep_out | dep_in) per internal metabolite, for the model's features
     bool dep_ready = false;
@@ -168,6 +176,11 @@ extern "C" int efm_load_network(int32_t n_met, int32_t n_rxn, const int32_t *row
     nv.o_keyneg = prep.o_keyneg;
     nv.o_hbits = prep.o_hbits;
     nv.o_dcols = prep.o_dcols;
+    nv.narrow = prep.narrow ? 1 : 0;
+    nv.o_rank = prep.o_rank;
+    nv.o_keyr = prep.o_keyr;
+    nv.o_hrow = prep.o_hrow;
+    nv.o_colx = prep.o_colx;
     nv.blob_words = (int)blob.size();
     nv.M = prep.M;
     nv.N = prep.N;
@@ -212,6 +225,33 @@ extern "C" int efm_load_network(int32_t n_met, int32_t n_rxn, const int32_t *row
     nv.blob = (const uint32_t *)net->blob.p;
     nv.metptr = (const int32_t *)net->metptr.p;
     nv.metent = (const uint32_t *)net->metent.p;
+    // the subtractive view: the same static network with a dense copy whose
+    // column k is S_int[:, k] followed by e_k
+    NetPrep sub;
+    if (prepare_network(n_met, n_rxn, row_ptr, col_idx, coef, reversible, external, sub, true) == EFM_OK) {
+        if (!dev_alloc(net->blob_sub, sub.blob.size() * 4, s) ||
+            cudaMemcpyAsync(net->blob_sub.p, sub.blob.data(), sub.blob.size() * 4, cudaMemcpyHostToDevice, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            dev_free(net->blob_sub, s);
+            dev_free(net->blob, s);
+            dev_free(net->metptr, s);
+            dev_free(net->metent, s);
+            delete net;
+            return EFM_ENOMEM;
+        }
+        NetView &vs = net->nv_sub;
+        vs = nv;
+        vs.blob = (const uint32_t *)net->blob_sub.p;
+        vs.blob_words = (int)sub.blob.size();
+        vs.o_dcols = sub.o_dcols;
+        vs.o_hbits = sub.o_hbits;
+        vs.EPL = sub.EPL;
+        vs.Mpad = sub.Mpad;
+        vs.narrow = 0;
+        net->has_sub = true;
+    }
     *out = net;
     return EFM_OK;
 }
@@ -240,6 +280,7 @@ extern "C" void efm_free_net(efm_net *net)
     if (!net) return;
     cudaStream_t s = net->stream;
     dev_free(net->blob, s);
+    dev_free(net->blob_sub, s);
     dev_free(net->metptr, s);
     dev_free(net->metent, s);
     dev_free(net->dep, s);
@@ -252,6 +293,7 @@ namespace {
 // Device buffers of one traversal, reused across the targets of a job.
 struct Work {
     DevBuf U[2], B[2], meta[2], live[2];
+    DevBuf sum[2], pmax[2];  // narrow networks: per-state summaries of the extra-flux row
     DevBuf slots, cslots, cand, res, bcnt, bfill, bptr, bres, ctr, sortidx, rcols;
     DevBuf fp;         // fingerprints of one level's reserved child rows
     DevBuf perm, fkb;  // first-K search: parent order of a level, bound support
@@ -271,6 +313,8 @@ void free_arena(Work &w, int i, cudaStream_t s)
     dev_free(w.B[i], s);
     dev_free(w.meta[i], s);
     dev_free(w.live[i], s);
+    dev_free(w.sum[i], s);
+    dev_free(w.pmax[i], s);
     w.rows[i] = 0;
 }
 
@@ -292,6 +336,7 @@ bool alloc_arena(Work &w, const NetView &nv, int i, int64_t rows, cudaStream_t s
     const size_t F = (size_t)rows;
     bool ok = dev_alloc(w.U[i], F * nv.W * 8, s) && dev_alloc(w.B[i], F * nv.Mpad * 4, s) &&
               dev_alloc(w.meta[i], F * 4, s) && dev_alloc(w.live[i], F * 4, s);
+    if (ok && nv.narrow) ok = dev_alloc(w.sum[i], F * 32, s) && dev_alloc(w.pmax[i], F * 4, s);
     if (ok) w.rows[i] = rows;
     return ok;
 }
@@ -314,9 +359,16 @@ bool ensure_level_tables(Work &w, uint64_t reserved, cudaStream_t s)
     return true;
 }
 
+// The static network a traversal reads: the subtractive variant's rows
+// carry the flux vector after the extra flux.
+const NetView &view_of(const efm_net *net, const efm_limits &lim)
+{
+    return lim.variant == EFM_SUBTRACTIVE ? net->nv_sub : net->nv;
+}
+
 int alloc_work(Work &w, const efm_net *net, const efm_limits &lim, int total_warps, cudaStream_t s)
 {
-    const NetView &nv = net->nv;
+    const NetView &nv = view_of(net, lim);
     const int64_t default_cap = (int64_t)1 << 22;
     // a level writes a row for every surviving child before deduplication,
     // so an arena gets room for a budget-sized frontier plus duplicates and
@@ -432,7 +484,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
                const efm_model *model = nullptr, Trace *trace = nullptr, const int32_t *seedset = nullptr,
                int n_seedset = 0)
 {
-    const NetView &nv = net->nv;
+    const NetView &nv = view_of(net, lim);
     cudaStream_t s = net->stream;
     const int grid = generate_grid(nv, net->sm_count);
     const int total_warps = grid * kExpandWarps;
@@ -456,12 +508,15 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
     a.max_len = lim.max_len;
     a.max_sec = lim.max_secondary;
     a.ctr = ctr;
+    a.sub = lim.variant == EFM_SUBTRACTIVE ? 1 : 0;
     auto arena = [&](int i) {
         Arena r;
         r.U = (uint64_t *)w.U[i].p;
         r.B = (int32_t *)w.B[i].p;
         r.meta = (uint32_t *)w.meta[i].p;
         r.cap = w.rows[i];
+        r.sum = (uint64_t *)w.sum[i].p;
+        r.pmax = (uint32_t *)w.pmax[i].p;
         return r;
     };
 
@@ -802,6 +857,9 @@ extern "C" int efm_find_pathways(efm_net *net, const int32_t *targets, int32_t n
         return EFM_EINVAL;
     if (lim.first_k > 0 && lim.max_results != 0) return EFM_EINVAL;
     if (lim.max_frontier > ((int64_t)1 << 31)) return EFM_EINVAL;  // arena indices are 32-bit
+    if ((lim.variant != EFM_ADDITIVE && lim.variant != EFM_SUBTRACTIVE) || lim.reserved != 0) return EFM_EINVAL;
+    if (lim.variant == EFM_SUBTRACTIVE && (lim.first_k != 0 || lim.proposal != EFM_PLAIN)) return EFM_EINVAL;
+    if (lim.variant == EFM_SUBTRACTIVE && !net->has_sub) return EFM_EUNSUPPORTED;
     // a model orders a first-K search and nothing else
     if ((lim.proposal == EFM_LEARNED) != (model != nullptr) || (model && lim.first_k <= 0)) return EFM_EINVAL;
     const efm_model *mdl = model;
@@ -812,7 +870,7 @@ extern "C" int efm_find_pathways(efm_net *net, const int32_t *targets, int32_t n
     job->net = net;
     job->out.resize(n_targets);
     Work w;
-    const int total_warps = generate_grid(net->nv, net->sm_count) * kExpandWarps;
+    const int total_warps = generate_grid(view_of(net, lim), net->sm_count) * kExpandWarps;
     int rc = alloc_work(w, net, lim, total_warps, net->stream);
     int flags = 0;
     for (int i = 0; rc == EFM_OK && i < n_targets; ++i) {
@@ -840,6 +898,9 @@ extern "C" int efm_find_pathways_from(efm_net *net, const int32_t *columns, int3
     if (lim.max_len < 1 || lim.max_len > EFM_MAX_LEN || lim.max_secondary < 0 || lim.first_k < 0 ||
         lim.proposal != EFM_PLAIN || (lim.first_k > 0 && lim.max_results != 0))
         return EFM_EINVAL;
+    if ((lim.variant != EFM_ADDITIVE && lim.variant != EFM_SUBTRACTIVE) || lim.reserved != 0) return EFM_EINVAL;
+    if (lim.variant == EFM_SUBTRACTIVE && lim.first_k != 0) return EFM_EINVAL;
+    if (lim.variant == EFM_SUBTRACTIVE && !net->has_sub) return EFM_EUNSUPPORTED;
     if (n_columns < 1 || n_columns > lim.max_len) return EFM_EINVAL;
     for (int i = 0; i < n_columns; ++i) {
         if (columns[i] < 0 || columns[i] >= net->nv.N) return EFM_EINVAL;
@@ -856,7 +917,7 @@ extern "C" int efm_find_pathways_from(efm_net *net, const int32_t *columns, int3
     cudaStream_t s = net->stream;
     Work w;
     DevBuf cols;
-    const int total_warps = generate_grid(net->nv, net->sm_count) * kExpandWarps;
+    const int total_warps = generate_grid(view_of(net, lim), net->sm_count) * kExpandWarps;
     int rc = alloc_work(w, net, lim, total_warps, s);
     if (rc == EFM_OK && !dev_alloc(cols, (size_t)n_columns * 4, s)) rc = EFM_ENOMEM;
     if (rc == EFM_OK && cudaMemcpyAsync(cols.p, columns, (size_t)n_columns * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -991,7 +1052,8 @@ extern "C" int efm_sample_pathways(efm_net *net, int32_t target, const efm_limit
     if (!net || !limits || n_walks < 0) return EFM_EINVAL;
     efm_limits lim = *limits;
     if (lim.max_len < 1 || lim.max_len > EFM_MAX_LEN || lim.max_secondary < 0 || lim.max_secondary > 63 ||
-        lim.first_k != 0 || lim.proposal != EFM_PLAIN || target < -1 || target >= net->n_met)
+        lim.first_k != 0 || lim.proposal != EFM_PLAIN || target < -1 || target >= net->n_met ||
+        lim.variant != EFM_ADDITIVE || lim.reserved != 0)
         return EFM_EINVAL;
     lim.max_frontier = 1;  // walks keep their state in registers: no arenas
     cudaStream_t s = net->stream;
@@ -1140,7 +1202,7 @@ extern "C" int efm_find_pathways_batch(efm_net *const *nets, const int32_t *targ
     if (!nets || !targets || n_jobs <= 0 || !limits || model) return EFM_EINVAL;
     const efm_limits lim = *limits;
     if (lim.max_len < 1 || lim.max_len > EFM_MAX_LEN || lim.max_secondary < 0 || lim.first_k != 0 ||
-        lim.proposal != 0 || lim.max_frontier <= 0)
+        lim.proposal != 0 || lim.max_frontier <= 0 || lim.variant != EFM_ADDITIVE || lim.reserved != 0)
         return EFM_EINVAL;
     int Wmax = 1, Mpad_max = 32, Nmax = 1, Lmax = 1, max_epl = 1;
     for (int i = 0; i < n_jobs; ++i) {
@@ -1698,7 +1760,7 @@ extern "C" int efm_model_trace(efm_model *m, efm_net *net, const int32_t *target
     efm_limits lim = *limits;
     lim.proposal = EFM_PLAIN;
     if (lim.max_len < 1 || lim.max_len > EFM_MAX_LEN || lim.max_secondary < 0 || lim.first_k <= 0 ||
-        lim.max_results != 0)
+        lim.max_results != 0 || lim.variant != EFM_ADDITIVE || lim.reserved != 0)
         return EFM_EINVAL;
     for (int i = 0; i < n_targets; ++i)
         if (targets[i] < -1 || targets[i] >= net->n_met) return EFM_EINVAL;

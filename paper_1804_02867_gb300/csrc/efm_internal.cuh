@@ -60,6 +60,12 @@ struct NetView {
     int o_keypos, o_keyneg;    // per internal row: (degree << 16) | row
     int o_hbits;               // per column: ceil(log2(|S_int[:,k]|^2))
     int o_dcols;               // dense S_int by column: N rows of Mpad int32 (16-byte aligned)
+    // narrow networks (M <= 64): state summary tables (see efm_netprep.h)
+    int narrow;
+    int o_rank;                // per row: rank in the positive key order | rank in the negative << 8
+    int o_keyr;                // per rank: positive key [64], then negative key [64]
+    int o_hrow;                // per row: 64-bit row hash constant R[m]
+    int o_colx;                // per column: suppP, suppN, suppR, HC (u64 each), smax, gcd1 (10 words)
     const int32_t *metptr;     // full S rows over split columns (seeds), [n_met + 1]
     const uint32_t *metent;    // packed (column, coefficient)
     int n_met;
@@ -74,6 +80,14 @@ struct Arena {
     int32_t *B;      // [cap][Mpad]
     uint32_t *meta;  // [cap]: pivot row | pivot degree << 10 | |U| << 23
     int64_t cap;
+    // narrow networks: per-state summaries of the extra-flux row EF
+    //   sum[4 s + 0] = sum_m EF_m R[m] (mod 2^64), the linear row hash
+    //   sum[4 s + 1] = positive entries, bit = rank of the row in the positive key order
+    //   sum[4 s + 2] = negative entries, bit = rank of the row in the negative key order
+    //   sum[4 s + 3] = rows with |EF_m| = 1
+    //   pmax[s]      = an upper bound of max_m |EF_m| (saturating at 2^31 - 1)
+    uint64_t *sum;
+    uint32_t *pmax;
 };
 
 struct LevelArgs {
@@ -105,11 +119,17 @@ struct LevelArgs {
     int64_t fp_cap;
     uint32_t *live;             // dedup output: arena rows of the distinct children
     int blk;                    // rows a warp reserves at a time (NG..32)
+    // subtractive variant (Eq. 5): rows hold the extra flux (M entries), then
+    // the flux of every column; a state's branches also take flux away from
+    // a column in U, and its meta degree counts both lists of the pivot
+    int sub;
 };
 
 constexpr unsigned long long kDeadFp = ~0ull;  // fingerprint of a reserved row left unused
 
 constexpr int kRcolStride = 65;  // column count + up to 64 columns per result
+constexpr int kNarrowKeyRanks = 64;  // narrow networks: keys per rank order (efm_netprep.h kNarrowRows)
+constexpr int kColxWordsDev = 10;    // narrow networks: per-column summary words (efm_netprep.h kColxWords)
 
 struct AcceptArgs {
     const uint64_t *cand;

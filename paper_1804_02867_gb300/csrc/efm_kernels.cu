@@ -298,13 +298,33 @@ __device__ __forceinline__ uint32_t pivot_key(const uint32_t *bl, const NetView 
     uint32_t kmin = 0xFFFFFFFFu;
 #pragma unroll
     for (int e = 0; e < EPL; ++e) {
-        if (t[e] != 0) {
-            const int m = lane + 32 * e;
+        const int m = lane + 32 * e;
+        if (t[e] != 0 && m < nv.M) {  // rows past M hold flux (subtractive variant) or padding
             const uint32_t k = t[e] > 0 ? bl[nv.o_keypos + m] : bl[nv.o_keyneg + m];
             kmin = k < kmin ? k : kmin;
         }
     }
     return __reduce_min_sync(FULL, kmin);
+}
+
+// The meta word's degree field counts the branches a state has: the list of
+// the pivot's side, plus (subtractive variant) the opposite list.
+__device__ __forceinline__ uint32_t branch_key(const uint32_t *bl, const NetView &nv, uint32_t key, int sub)
+{
+    if (!sub) return key;
+    const int m = (int)(key & 0xFFFFu);
+    const uint32_t deg = (bl[nv.o_consptr + m + 1] - bl[nv.o_consptr + m]) + (bl[nv.o_prodptr + m + 1] - bl[nv.o_prodptr + m]);
+    return (deg << 16) | (key & 0xFFFFu);
+}
+
+// warp-wide test: all balance rows (m < M) of a row held across the warp are 0
+template <int EPL>
+__device__ __forceinline__ bool balance_zero(const int32_t (&t)[EPL], int M, int lane)
+{
+    bool nz = false;
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) nz = nz || (t[e] != 0 && lane + 32 * e < M);
+    return !__any_sync(FULL, nz);
 }
 
 // warp-cooperative normalisation of a seed column (t64 in, t32 out)
@@ -323,6 +343,77 @@ __device__ __forceinline__ void normalise(int64_t (&t64)[EPL], int32_t (&t32)[EP
     for (int off = 16; off > 0; off >>= 1) g = gcd64(g, __shfl_xor_sync(FULL, g, off));
 #pragma unroll
     for (int e = 0; e < EPL; ++e) t32[e] = (int32_t)(g > 1 ? t64[e] / (int64_t)g : t64[e]);
+}
+
+// ---------------------------------------------------------------------------
+// narrow networks (at most 64 internal rows): per-state summaries of the
+// extra-flux row, see generate_narrow below
+// ---------------------------------------------------------------------------
+
+struct NarrowSum {
+    uint64_t rh, pm, nm, um;
+    uint32_t pmax;
+};
+
+__device__ __forceinline__ uint64_t blob_u64(const uint32_t *bl, int o)
+{
+    return (uint64_t)bl[o] | ((uint64_t)bl[o + 1] << 32);
+}
+
+// Summaries of a full row held across a warp (entry m = lane + 32 e).
+template <int EPL>
+__device__ NarrowSum warp_summary(const uint32_t *bl, const NetView &nv, const int32_t (&t)[EPL], int lane)
+{
+    NarrowSum r{0, 0, 0, 0, 0};
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+        const int m = lane + 32 * e;
+        const int32_t v = t[e];
+        if (m < nv.M && v != 0) {
+            const uint32_t rk = bl[nv.o_rank + m];
+            if (v > 0) r.pm |= 1ull << (rk & 0xFFu);
+            else r.nm |= 1ull << ((rk >> 8) & 0xFFu);
+            if (v == 1 || v == -1) r.um |= 1ull << m;
+            const uint32_t a = (uint32_t)(v < 0 ? -v : v);
+            r.pmax = a > r.pmax ? a : r.pmax;
+            r.rh += (uint64_t)(int64_t)v * blob_u64(bl, nv.o_hrow + 2 * m);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        r.pm |= __shfl_xor_sync(FULL, r.pm, off);
+        r.nm |= __shfl_xor_sync(FULL, r.nm, off);
+        r.um |= __shfl_xor_sync(FULL, r.um, off);
+        r.rh += __shfl_xor_sync(FULL, r.rh, off);
+        const uint32_t o = __shfl_xor_sync(FULL, r.pmax, off);
+        r.pmax = o > r.pmax ? o : r.pmax;
+    }
+    return r;
+}
+
+__device__ __forceinline__ void store_summary(const Arena &ar, uint64_t idx, const NarrowSum &s, int lane)
+{
+    // one 16-byte store per lane pair: lanes 0 and 1 write the record
+    uint64_t *d = ar.sum + (size_t)idx * 4;
+    if (lane == 0) *reinterpret_cast<ulonglong2 *>(d) = make_ulonglong2(s.rh, s.pm);
+    if (lane == 1) *reinterpret_cast<ulonglong2 *>(d + 2) = make_ulonglong2(s.nm, s.um);
+    if (lane == 2) ar.pmax[idx] = s.pmax;
+}
+
+// pivot key from the two masks (0xFFFFFFFF when balanced)
+__device__ __forceinline__ uint32_t mask_key(const uint32_t *bl, const NetView &nv, uint64_t pm, uint64_t nm)
+{
+    const uint32_t kp = pm ? bl[nv.o_keyr + __ffsll((long long)pm) - 1] : 0xFFFFFFFFu;
+    const uint32_t kn = nm ? bl[nv.o_keyr + kNarrowKeyRanks + __ffsll((long long)nm) - 1] : 0xFFFFFFFFu;
+    return kp < kn ? kp : kn;
+}
+
+// 64-bit hash of the support words (W words of U plus column k)
+__device__ __forceinline__ uint64_t support_hash(const uint64_t *pu, int W, int k)
+{
+    uint64_t h = 0;
+    for (int w = 0; w < W; ++w) h += mix64(child_word(pu, w, k) ^ (0x2545f4914f6cdd1dull * (uint64_t)(w + 1)));
+    return h;
 }
 
 // ---------------------------------------------------------------------------
@@ -346,19 +437,16 @@ __device__ void seed_range(const NetView &nv, const LevelArgs &a, int target, in
             k = ent_index(e);
         }
         ++n_seed;
+        // the seed's row: column k of the dense copy (S_int[:, k], then, in
+        // the subtractive variant's view, flux 1 on k)
+        const int32_t *dk = reinterpret_cast<const int32_t *>(bl + nv.o_dcols) + (size_t)k * nv.Mpad;
         int64_t t64[EPL];
 #pragma unroll
-        for (int e = 0; e < EPL; ++e) t64[e] = 0;
-        for (int q = (int)bl[nv.o_colptr + k]; q < (int)bl[nv.o_colptr + k + 1]; ++q) {
-            const uint32_t ent = bl[nv.o_colent + q];
-            const int row = ent_index(ent);
-#pragma unroll
-            for (int e = 0; e < EPL; ++e)
-                if (row == lane + 32 * e) t64[e] = ent_coef(ent);
-        }
+        for (int e = 0; e < EPL; ++e) t64[e] = dk[lane + 32 * e];
         int32_t t[EPL];
         bool zero;
         normalise<EPL>(t64, t, zero);
+        zero = balance_zero<EPL>(t, nv.M, lane);
         if (zero) {
             ++n_bal;
             if (lane == 0) insert_support(a, W, nullptr, k);
@@ -376,8 +464,13 @@ __device__ void seed_range(const NetView &nv, const LevelArgs &a, int target, in
             int32_t *db = a.child.B + (size_t)idx * nv.Mpad;
 #pragma unroll
             for (int e = 0; e < EPL; ++e) db[lane + 32 * e] = t[e];
-            if (lane == 0) a.child.meta[idx] = pack_meta(key, 1);
-            deg_sum += key >> 16;
+            const uint32_t bkey = branch_key(bl, nv, key, a.sub);
+            if (lane == 0) a.child.meta[idx] = pack_meta(bkey, 1);
+            deg_sum += bkey >> 16;
+        }
+        if (EPL <= 2 && nv.narrow && a.child.sum) {
+            const NarrowSum sm = warp_summary<EPL>(bl, nv, t, lane);
+            if ((int64_t)idx < a.child.cap) store_summary(a.child, idx, sm, lane);
         }
     }
     if (lane == 0) {
@@ -591,6 +684,7 @@ __global__ void __launch_bounds__(32) seedset_kernel(NetView nv, LevelArgs a, co
     int32_t t[EPL];
     bool zero, ovf;
     walk_normalise<EPL>(t64, t, zero, ovf);
+    zero = balance_zero<EPL>(t, nv.M, lane);
     if (lane == 0) atomicAdd(&a.ctr[C_SEEDS], 1ull);
     if (ovf) {
         if (lane == 0) atomicAdd(&a.ctr[C_OVF], 1ull);
@@ -605,13 +699,18 @@ __global__ void __launch_bounds__(32) seedset_kernel(NetView nv, LevelArgs a, co
     }
     const uint32_t key = pivot_key<EPL>(nv.blob, nv, t, lane);
     if (a.child.cap < 1) return;
+    if (EPL <= 2 && nv.narrow && a.child.sum) {
+        const NarrowSum sm = warp_summary<EPL>(nv.blob, nv, t, lane);
+        store_summary(a.child, 0, sm, lane);
+    }
     for (int x = lane; x < W; x += 32) a.child.U[x] = U[x];
 #pragma unroll
     for (int e = 0; e < EPL; ++e) a.child.B[lane + 32 * e] = t[e];
+    const uint32_t bkey = branch_key(nv.blob, nv, key, a.sub);
     if (lane == 0) {
-        a.child.meta[0] = pack_meta(key, n_cols);
+        a.child.meta[0] = pack_meta(bkey, n_cols);
         atomicAdd(&a.ctr[C_NEXT], 1ull);
-        atomicAdd(&a.ctr[C_DEGSUM], (unsigned long long)(key >> 16));
+        atomicAdd(&a.ctr[C_DEGSUM], (unsigned long long)(bkey >> 16));
     }
 }
 
@@ -1268,7 +1367,7 @@ __device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint
     const int4 *dcol = reinterpret_cast<const int4 *>(bl + nv.o_dcols);
     const int64_t row_cap = a.child.cap;
 
-    unsigned long long n_exp = 0, n_ovf = 0, n_bal = 0, n_pruned = 0, n_unwritten = 0;
+    unsigned long long n_exp = 0, n_ovf = 0, n_bal = 0, n_pruned = 0, n_unwritten = 0, n_zero = 0;
     bool fatal = false;
     // this warp's reserved rows: [pool_next, pool_next + pool_left)
     uint64_t pool_next = 0;
@@ -1319,7 +1418,7 @@ __device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint
             const int64_t pl_ = __shfl_sync(FULL, pid, j);
             bool okl = c < T;
             int kl = 0, pcl = 0;
-            bool inl = false;
+            bool inl = false, subl = false;
             int32_t Al = 0, Cl = 0;
             if (okl) {
                 const int32_t *prow_l = a.par.B + (size_t)pl_ * Mpad;
@@ -1329,14 +1428,29 @@ __device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint
                 const int32_t bi = piv < nv.M ? prow_l[piv] : 0;
                 const bool fwd = bi > 0;  // forward flow: consume the surplus
                 const uint32_t abi = (uint32_t)(bi < 0 ? -bi : bi);
-                const int lptr = (fwd ? nv.o_consptr : nv.o_prodptr) + (piv < nv.M ? piv : 0);
+                const int pv_ = piv < nv.M ? piv : 0;
+                const int lptr = (fwd ? nv.o_consptr : nv.o_prodptr) + pv_;
                 const int lb = (int)bl[lptr];
                 const int le = (int)bl[lptr + 1];
-                if (piv >= nv.M || bi == 0 || lb + q >= le) {
+                // subtractive variant: after the side list, the opposite list
+                // (Eq. 5: less flux on a column of U that moves i the same way)
+                const int optr = (fwd ? nv.o_prodptr : nv.o_consptr) + pv_;
+                const int on = a.sub ? (int)bl[optr + 1] - (int)bl[optr] : 0;
+                if (piv >= nv.M || bi == 0 || q >= (le - lb) + on) {
                     record_diag(a.ctr, ERR_BOUNDS, 1 + (piv >= nv.M ? 10 : 0) + (bi == 0 ? 100 : 0), (long long)q,
-                                (long long)(le - lb), a.level);
+                                (long long)(le - lb + on), a.level);
                     fatal = true;
                     okl = false;
+                } else if (q >= le - lb) {
+                    const uint32_t br = bl[(fwd ? nv.o_prodent : nv.o_consent) + (int)bl[optr] + (q - (le - lb))];
+                    kl = ent_index(br);
+                    const uint32_t sik = (uint32_t)ent_coef(br);  // |S_ik|
+                    inl = bit_of(pu_l, kl);
+                    okl = inl && (a.level - pcl) + 1 <= a.max_sec;
+                    subl = true;
+                    const uint32_t g0 = (abi == 1u || sik == 1u) ? 1u : gcd32(abi, sik);
+                    Al = (int32_t)(sik / g0);
+                    Cl = (int32_t)(abi / g0);
                 } else {
                     const uint32_t br = bl[(fwd ? nv.o_consent : nv.o_prodent) + lb + q];
                     kl = ent_index(br);
@@ -1355,7 +1469,7 @@ __device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint
                 }
             }
             if (okl) ++n_exp;
-            const uint32_t infol = (uint32_t)kl | ((uint32_t)pcl << 12) | (inl ? 1u << 19 : 0u);
+            const uint32_t infol = (uint32_t)kl | ((uint32_t)pcl << 12) | (inl ? 1u << 19 : 0u) | (subl ? 1u << 20 : 0u);
             const uint32_t pl32 = (uint32_t)pl_;
             // the groups take the valid items of this pass NG at a time, in order
             unsigned vmask = __ballot_sync(FULL, okl);
@@ -1370,11 +1484,17 @@ __device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint
                 const int k = (int)(info_i & 0xFFFu);
                 const int pc = (int)((info_i >> 12) & 0x7Fu);
                 const bool in_u = (info_i >> 19) & 1u;
+                const bool subi = (info_i >> 20) & 1u;  // Eq. 5: flux taken away from k
                 const int32_t A = __shfl_sync(FULL, Al, sl);
-                const int32_t C = __shfl_sync(FULL, Cl, sl);
+                const int32_t C0 = __shfl_sync(FULL, Cl, sl);
+                const int32_t C = subi ? -C0 : C0;
                 const int64_t p = (int64_t)__shfl_sync(FULL, pl32, sl);
                 const int32_t *prow = a.par.B + (size_t)p * Mpad;
                 const uint64_t *pu = a.par.U + (size_t)p * W;
+                // Prop. 3: a subtractive step must leave k with positive flux
+                // (the flux of column k sits at row M + k)
+                bool zflux = false;
+                if (ok && subi) zflux = (int64_t)A * prow[nv.M + k] - (int64_t)C0 <= 0;
 
                 // --- AND update (Eq. 3 / Eq. 4 in integers), group-parallel ---
                 int32_t t32[EPL];
@@ -1393,7 +1513,9 @@ __device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint
                             const int32_t lo = (int32_t)tt;
                             const bool fits = tt == (int64_t)lo && lo != INT32_MIN;
                             t32[4 * i + jj] = lo;
-                            fl |= (tt != 0 ? 1u : 0u) | ((lo == 1 || lo == -1) ? 2u : 0u) | (fits ? 0u : 4u);
+                            // bit0: a balance row (m < M; the rest is flux or padding) is nonzero
+                            const bool brow = 4 * (gl + G * i) + jj < nv.M;
+                            fl |= ((tt != 0 && brow) ? 1u : 0u) | ((lo == 1 || lo == -1) ? 2u : 0u) | (fits ? 0u : 4u);
                         }
                     }
                 } else {
@@ -1404,7 +1526,7 @@ __device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint
                 const bool nz = fl & 1u;
                 // slow path: the gcd is needed (no unit entry), or an entry is
                 // outside int32 (then the raw entries are recomputed in 64 bits)
-                const bool slow = ok && nz && ((fl & 6u) != 2u);
+                const bool slow = ok && !zflux && nz && ((fl & 6u) != 2u);
                 const bool big = (fl & 4u) != 0u;
                 bool ovf = false;
                 if (__any_sync(FULL, slow)) {
@@ -1452,9 +1574,10 @@ __device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint
                         }
                     }
                 }
-                const bool bal = ok && !nz;
-                const bool grown = ok && nz && !ovf;
-                if (ovf && gl == 0) ++n_ovf;
+                if (zflux && gl == 0) ++n_zero;
+                const bool bal = ok && !zflux && !nz;
+                const bool grown = ok && !zflux && nz && !ovf;
+                if (ovf && !zflux && gl == 0) ++n_ovf;
                 if (bal && gl == 0) {
                     ++n_bal;  // all metabolites stable: to the arbiter
                     if (insert_support(a, W, pu, k) < INS_DUP) fatal = true;
@@ -1495,7 +1618,7 @@ __device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint
                         for (int jj = 0; jj < 4; ++jj) {
                             const int m = 4 * (gl + G * i) + jj;
                             const int32_t v = t32[4 * i + jj];
-                            if (v != 0) {
+                            if (v != 0 && m < nv.M) {
                                 const uint32_t kk = bl[(v > 0 ? nv.o_keypos : nv.o_keyneg) + m];
                                 key = kk < key ? kk : key;
                             }
@@ -1538,7 +1661,7 @@ __device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint
                                 db[gl + G * i] = make_int4(t32[4 * i + 0], t32[4 * i + 1], t32[4 * i + 2], t32[4 * i + 3]);
                             uint64_t *du = a.child.U + (size_t)idx * W;
                             for (int w = gl; w < W; w += G) du[w] = child_word(pu, w, k);
-                            if (gl == 0) a.child.meta[idx] = pack_meta(key, pc + (in_u ? 0 : 1));
+                            if (gl == 0) a.child.meta[idx] = pack_meta(branch_key(bl, nv, key, a.sub), pc + (in_u ? 0 : 1));
                         } else if (gl == 0) {
                             ++n_unwritten;
                         }
@@ -1565,6 +1688,7 @@ __device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint
     if (n_bal) atomicAdd(&a.ctr[C_BAL], n_bal);
     if (n_pruned) atomicAdd(&a.ctr[C_PRUNED], n_pruned);
     if (n_unwritten) atomicAdd(&a.ctr[C_UNWRITTEN], n_unwritten);
+    if (n_zero) atomicAdd(&a.ctr[C_ZERO], n_zero);
 }
 
 template <int G, int CPL>
@@ -1578,6 +1702,472 @@ __global__ void __launch_bounds__(kExpandWarps * 32, (CPL <= 2 ? 3 : 2)) generat
     const uint32_t *bl = stage_blob(nv, smem, mbar, staged != 0, a.ctr);
     if (bl == nullptr) return;
     generate_range<G, CPL>(nv, a, bl, (int64_t)blockIdx.x * kExpandWarps + wid, (int64_t)gridDim.x * kExpandWarps);
+}
+
+// ---------------------------------------------------------------------------
+// Generate, narrow networks (at most 64 internal rows): incremental state
+// summaries.
+//
+// The AND update t = A p + C s changes the sign pattern of the extra-flux
+// row only on the rows of column k (A > 0), so a state carries summaries
+// that a child updates from those few rows instead of scanning the whole
+// row:
+//   * two 64-bit masks of its positive and negative entries, with each row
+//     at its rank in the positive / negative pivot-key order: the child's
+//     pivot is the lowest set bit of either mask (Alg. 3's acting metabolite
+//     under the fewest-reactions rule), and both masks empty means balanced;
+//   * a linear row hash sum_m t_m R[m] (mod 2^64): the child's is
+//     A h(p) + C h(S_int[:, k]);
+//   * the rows holding +-1: with gcd(A, C) = 1, if the parent has a +-1 on a
+//     row outside column k and either A = 1 or the entries of column k are
+//     coprime, then every prime dividing all of t would divide A and
+//     therefore, through the rows of column k, every entry of the column --
+//     or divide the +-1 entry times A -- so gcd(t) = 1 with no gcd at all;
+//   * a bound on max |t|: A pmax + C max|s| < 2^31 lets the update run in
+//     plain 32-bit multiply-adds with no overflow test.
+// A child without such a certificate, or with a possible overflow, takes the
+// full-row path (exact gcd, 64-bit entries) and recomputes what it must.
+//
+// Work is split by its shape: everything per child (branch rules, the
+// summaries from the rows of column k, balance test, superset rule, key,
+// fingerprint, support and summary stores) runs one item per lane, 32
+// children at once; only the dense extra-flux row (and a slow child's gcd)
+// runs on groups of G lanes, each lane holding two 16-byte chunks, so the
+// row's loads and stores are coalesced.
+// ---------------------------------------------------------------------------
+
+template <int G>
+__device__ void generate_narrow(const NetView &nv, const LevelArgs &a, const uint32_t *bl, int64_t worker,
+                                int64_t nworkers)
+{
+    constexpr int CPL = 2;
+    constexpr int NG = 32 / G;
+    constexpr int EPL = 4 * CPL;
+    const int lane = threadIdx.x & 31;
+    const int gi = lane / G;
+    const int gl = lane % G;
+    const int lead = gi * G;
+    const int W = nv.W;
+    const int Mpad = nv.Mpad;
+    const int4 *dcol = reinterpret_cast<const int4 *>(bl + nv.o_dcols);
+    const int64_t row_cap = a.child.cap;
+
+    unsigned long long n_exp = 0, n_ovf = 0, n_bal = 0, n_pruned = 0, n_unwritten = 0;
+    bool fatal = false;
+    uint64_t pool_next = 0;
+    int pool_left = 0;
+    // rows for cnt children of the warp (warp-uniform call); returns the
+    // first row of the calling lane's share given its rank among them
+    auto reserve = [&](int cnt, int rank) -> uint64_t {
+        uint64_t fresh = 0;
+        if (pool_left < cnt) {
+            const int want = cnt > a.blk ? cnt : a.blk;
+            if (lane == 0) fresh = atomicAdd(&a.ctr[C_WRITTEN], (unsigned long long)want);
+            fresh = __shfl_sync(FULL, fresh, 0);
+            const uint64_t idx = rank < pool_left ? pool_next + (uint64_t)rank : fresh + (uint64_t)(rank - pool_left);
+            pool_next = fresh + (uint64_t)(cnt - pool_left);
+            pool_left = want - (cnt - pool_left);
+            return idx;
+        }
+        const uint64_t idx = pool_next + (uint64_t)rank;
+        pool_next += (uint64_t)cnt;
+        pool_left -= cnt;
+        return idx;
+    };
+
+    const int cpw = a.cpw;
+    const int64_t wstride = nworkers * cpw;
+    for (int64_t p0 = worker * cpw; p0 < a.n_par; p0 += wstride) {
+        const int64_t pl = p0 + lane;
+        const bool pin = lane < cpw && pl < a.n_par;
+        const int64_t pid = pin ? (a.perm ? (int64_t)a.perm[pl] : pl) : 0;
+        const int64_t pn = pl + wstride;
+        if (lane < cpw && pn < a.n_par) {
+            const int64_t nid = a.perm ? (int64_t)a.perm[pn] : pn;
+            const char *rp = reinterpret_cast<const char *>(a.par.B + (size_t)nid * Mpad);
+            for (int off = 0; off < Mpad * 4; off += 128) prefetch_l2(rp + off);
+            prefetch_l2(a.par.U + (size_t)nid * W);
+            prefetch_l2(a.par.meta + nid);
+            prefetch_l2(a.par.sum + (size_t)nid * 4);
+        }
+        const uint32_t mj = pin ? a.par.meta[pid] : 0u;
+        int dj = pin ? (int)((mj >> 10) & 0x1FFFu) : 0;
+        if (a.fk_pc > 0 && (int)((mj >> 23) & 0x7Fu) > a.fk_pc) dj = 0;
+        int incl = dj;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int x = __shfl_up_sync(FULL, incl, off);
+            if (lane >= off) incl += x;
+        }
+        const int prej = incl - dj;
+        const int T = __shfl_sync(FULL, incl, 31);
+        if (T > 32 * nv.N) {
+            if (lane == 0) record_diag(a.ctr, ERR_BOUNDS, 3, T, 32 * nv.N, a.level);
+            fatal = true;
+        }
+        for (int base = 0; base < T; base += 32) {
+            if (__any_sync(FULL, fatal)) break;
+            // === phase A: one (parent, branch) item per lane.  Branch rules,
+            // then the child's summaries from the rows of column k only ===
+            const int c = base + lane;
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int v = __shfl_sync(FULL, prej, j + step);
+                if (v <= c) j += step;
+            }
+            const uint32_t pm = __shfl_sync(FULL, mj, j);
+            const int q = c - __shfl_sync(FULL, prej, j);
+            const int64_t pl_ = __shfl_sync(FULL, pid, j);
+            bool okl = c < T;
+            int kl = 0, pcl = 0;
+            bool inl = false;
+            int32_t Al = 0, Cl = 0;
+            const uint64_t *pu_l = a.par.U + (size_t)pl_ * W;
+            const int32_t *prow_l = a.par.B + (size_t)pl_ * Mpad;
+            if (okl) {
+                const int piv = (int)(pm & 0x3FFu);
+                pcl = (int)((pm >> 23) & 0x7Fu);
+                const int32_t bi = piv < nv.M ? prow_l[piv] : 0;
+                const bool fwd = bi > 0;
+                const uint32_t abi = (uint32_t)(bi < 0 ? -bi : bi);
+                const int lptr = (fwd ? nv.o_consptr : nv.o_prodptr) + (piv < nv.M ? piv : 0);
+                const int lb = (int)bl[lptr];
+                const int le = (int)bl[lptr + 1];
+                if (piv >= nv.M || bi == 0 || lb + q >= le) {
+                    record_diag(a.ctr, ERR_BOUNDS, 1 + (piv >= nv.M ? 10 : 0) + (bi == 0 ? 100 : 0), (long long)q,
+                                (long long)(le - lb), a.level);
+                    fatal = true;
+                    okl = false;
+                } else {
+                    const uint32_t br = bl[(fwd ? nv.o_consent : nv.o_prodent) + lb + q];
+                    kl = ent_index(br);
+                    const uint32_t sik = (uint32_t)ent_coef(br);
+                    const int tw = (int)bl[nv.o_twin + kl];
+                    inl = bit_of(pu_l, kl);
+                    const int sec = a.level - pcl;
+                    okl = !(tw >= 0 && bit_of(pu_l, tw)) && (inl ? sec + 1 <= a.max_sec : pcl + 1 <= a.max_len);
+                    if (okl && a.fk_pc > 0) {
+                        const int pc2 = pcl + (inl ? 0 : 1);
+                        okl = pc2 < a.fk_pc || (pc2 == a.fk_pc && !child_after(pu_l, kl, a.fk_sup, W));
+                    }
+                    const uint32_t g0 = (abi == 1u || sik == 1u) ? 1u : gcd32(abi, sik);
+                    Al = (int32_t)(sik / g0);
+                    Cl = (int32_t)(abi / g0);
+                }
+            }
+            if (okl) ++n_exp;
+            // summaries of the child (exact signs from 64-bit entries)
+            NarrowSum sm{0, 0, 0, 0, 0};
+            bool fast = false, cert = false;
+            if (okl) {
+                const uint64_t *ps = a.par.sum + (size_t)pl_ * 4;
+                const ulonglong2 s01 = *reinterpret_cast<const ulonglong2 *>(ps);
+                const ulonglong2 s23 = *reinterpret_cast<const ulonglong2 *>(ps + 2);
+                const uint32_t pmaxp = a.par.pmax[pl_];
+                const int ox = nv.o_colx + kColxWordsDev * kl;
+                const uint64_t suppP = blob_u64(bl, ox), suppN = blob_u64(bl, ox + 2), suppR = blob_u64(bl, ox + 4);
+                const uint32_t smax = bl[ox + 8], gcd1 = bl[ox + 9];
+                fast = (uint64_t)Al * pmaxp + (uint64_t)Cl * smax <= 2147483647ull;
+                uint64_t newp = 0, newn = 0, newu = 0, tmax = 0;
+                for (int qq = (int)bl[nv.o_colptr + kl]; qq < (int)bl[nv.o_colptr + kl + 1]; ++qq) {
+                    const uint32_t e = bl[nv.o_colent + qq];
+                    const int m = ent_index(e);
+                    const int64_t tm = (int64_t)Al * prow_l[m] + (int64_t)Cl * ent_coef(e);
+                    const uint32_t rk = bl[nv.o_rank + m];
+                    newp |= (tm > 0 ? 1ull : 0ull) << (rk & 0xFFu);
+                    newn |= (tm < 0 ? 1ull : 0ull) << ((rk >> 8) & 0xFFu);
+                    newu |= ((tm == 1 || tm == -1) ? 1ull : 0ull) << m;
+                    const uint64_t am = (uint64_t)(tm < 0 ? -tm : tm);
+                    tmax = am > tmax ? am : tmax;
+                }
+                sm.pm = (s01.y & ~suppP) | newp;
+                sm.nm = (s23.x & ~suppN) | newn;
+                const uint64_t uout = s23.y & ~suppR;  // parent's +-1 rows outside column k
+                sm.um = (Al == 1 ? uout : 0ull) | newu;
+                sm.rh = (uint64_t)(int64_t)Al * s01.x + (uint64_t)(int64_t)Cl * blob_u64(bl, ox + 6);
+                const uint64_t bound = (uint64_t)Al * pmaxp > tmax ? (uint64_t)Al * pmaxp : tmax;
+                sm.pmax = bound > 2147483647ull ? 2147483647u : (uint32_t)bound;
+                // gcd(t) = 1 without computing it: a +-1 entry in the child, or
+                // a parent +-1 outside column k with A = 1 or a coprime column
+                cert = sm.um != 0 || (uout != 0 && (Al == 1 || gcd1 != 0));
+            }
+            const bool nzl = (sm.pm | sm.nm) != 0;
+            const bool ball = okl && !nzl;
+            if (ball) {
+                ++n_bal;  // all metabolites stable: to the arbiter
+                if (insert_support(a, W, pu_l, kl) < INS_DUP) fatal = true;
+            }
+            // ready: the child is final (no overflow possible, gcd 1): prune
+            // test, key and fingerprint here; slow: settled by its lane group
+            bool ready = okl && nzl && fast && cert;
+            const bool slowl = okl && nzl && !(fast && cert);
+            if (ready && !inl) {
+                const int64_t b1 = a.bptr[kl];
+                const int64_t n = a.bptr[kl + 1] - b1;
+                bool pr = false;
+                if (n > 0) {
+                    if (W <= 2) {
+                        const uint64_t u0 = child_word(pu_l, 0, kl), u1 = W == 2 ? child_word(pu_l, 1, kl) : 0ull;
+                        bool maybe = true;
+                        if (a.band) {
+                            const uint64_t i0 = __ldg(a.band + (size_t)kl * W), i1 = W == 2 ? __ldg(a.band + (size_t)kl * W + 1) : 0ull;
+                            maybe = ((i0 & ~u0) | (i1 & ~u1)) == 0;
+                        }
+                        for (int64_t i = 0; i < n && !pr && maybe; ++i) {
+                            const uint64_t *E = a.bres + (size_t)(b1 + i) * W;
+                            const uint64_t e0 = __ldg(E), e1 = W == 2 ? __ldg(E + 1) : 0ull;
+                            pr = ((e0 & ~u0) | (e1 & ~u1)) == 0;
+                        }
+                    } else {
+                        for (int64_t i = 0; i < n && !pr; ++i) pr = result_inside_wide(a, pu_l, kl, b1 + i);
+                    }
+                }
+                if (pr) {
+                    ++n_pruned;
+                    ready = false;
+                }
+            }
+            // rows for the ready children of the pass, written per lane
+            // except the extra-flux row (phase B, coalesced by lane groups)
+            const unsigned rmask = __ballot_sync(FULL, ready);
+            uint64_t myidx = 0;
+            if (rmask) {
+                myidx = reserve(__popc(rmask), __popc(rmask & ((1u << lane) - 1u)));
+                if (ready) {
+                    if ((int64_t)myidx < row_cap) {
+                        uint64_t *du = a.child.U + (size_t)myidx * W;
+                        for (int w = 0; w < W; ++w) du[w] = child_word(pu_l, w, kl);
+                        a.child.meta[myidx] = pack_meta(mask_key(bl, nv, sm.pm, sm.nm), pcl + (inl ? 0 : 1));
+                        uint64_t *d = a.child.sum + (size_t)myidx * 4;
+                        *reinterpret_cast<ulonglong2 *>(d) = make_ulonglong2(sm.rh, sm.pm);
+                        *reinterpret_cast<ulonglong2 *>(d + 2) = make_ulonglong2(sm.nm, sm.um);
+                        a.child.pmax[myidx] = sm.pmax;
+                    } else {
+                        ++n_unwritten;
+                    }
+                    if ((int64_t)myidx < a.fp_cap) {
+                        uint64_t f = sm.rh ^ mix64(support_hash(pu_l, W, kl) + 0x632BE59BD9B4E019ull);
+                        if (f == kDeadFp) f = kDeadFp - 1;
+                        a.fp[myidx] = f;
+                    } else {
+                        record_diag(a.ctr, ERR_BOUNDS, 7, (long long)myidx, a.fp_cap, a.level);
+                        fatal = true;
+                    }
+                }
+            }
+            // === phase B: lane groups take the ready and slow children NG at
+            // a time: the extra-flux row t = A p + C s, coalesced ===
+            const uint32_t infol = (uint32_t)kl | ((uint32_t)pcl << 12) | (inl ? 1u << 19 : 0u) |
+                                   (slowl ? 1u << 20 : 0u) | (fast ? 1u << 21 : 0u);
+            const uint32_t pl32 = (uint32_t)pl_;
+            unsigned vmask = __ballot_sync(FULL, ready || slowl);
+            while (vmask) {
+                if (__any_sync(FULL, fatal)) break;
+                const int src = gi < __popc(vmask) ? (int)__fns(vmask, 0, gi + 1) : -1;
+#pragma unroll
+                for (int t = 0; t < NG; ++t) vmask &= vmask - 1;
+                const int sl = src < 0 ? 0 : src;
+                const bool ok = src >= 0;
+                const uint32_t info_i = __shfl_sync(FULL, infol, sl);
+                const int k = (int)(info_i & 0xFFFu);
+                const int pc = (int)((info_i >> 12) & 0x7Fu);
+                const bool in_u = (info_i >> 19) & 1u;
+                const bool slow = ok && ((info_i >> 20) & 1u);
+                const bool fst = (info_i >> 21) & 1u;
+                const int32_t A = __shfl_sync(FULL, Al, sl);
+                const int32_t C = __shfl_sync(FULL, Cl, sl);
+                const int64_t p = (int64_t)__shfl_sync(FULL, pl32, sl);
+                const uint64_t ridx = __shfl_sync(FULL, myidx, sl);
+                const int4 *prow4 = reinterpret_cast<const int4 *>(a.par.B + (size_t)p * Mpad);
+                const int4 *col4 = dcol + (size_t)k * (Mpad >> 2);
+                int32_t t32[EPL];
+                bool big = false;
+                if (ok && fst) {
+#pragma unroll
+                    for (int i = 0; i < CPL; ++i) {
+                        const int4 v = prow4[gl + G * i];
+                        const int4 w = col4[gl + G * i];
+                        t32[4 * i + 0] = A * v.x + C * w.x;
+                        t32[4 * i + 1] = A * v.y + C * w.y;
+                        t32[4 * i + 2] = A * v.z + C * w.z;
+                        t32[4 * i + 3] = A * v.w + C * w.w;
+                    }
+                } else if (ok) {
+#pragma unroll
+                    for (int i = 0; i < CPL; ++i) {
+                        const int4 v = prow4[gl + G * i];
+                        const int4 w = col4[gl + G * i];
+                        const int32_t pv[4] = {v.x, v.y, v.z, v.w}, cv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) {
+                            const int64_t tt = (int64_t)A * pv[jj] + (int64_t)C * cv[jj];
+                            const int32_t lo = (int32_t)tt;
+                            big = big || tt != (int64_t)lo || lo == INT32_MIN;
+                            t32[4 * i + jj] = lo;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) t32[e] = 0;
+                }
+                if (__any_sync(FULL, slow)) {
+                    // a slow child: exact gcd and int32 range over the whole row,
+                    // then the superset rule, and its row's summaries
+                    uint64_t gg = 0, amax = 0;
+                    if (slow && !big) {
+#pragma unroll
+                        for (int e = 0; e < EPL; ++e) {
+                            const uint32_t at = (uint32_t)(t32[e] < 0 ? -t32[e] : t32[e]);
+                            if (at != 0) gg = gg == 0 ? at : gcd32((uint32_t)gg, at);
+                            amax = at > amax ? at : amax;
+                        }
+                    } else if (slow) {
+                        const GcdMax gmx = raw_gcd_max(prow4, col4, gl, G, CPL, A, C);
+                        gg = gmx.g;
+                        amax = gmx.m;
+                    }
+#pragma unroll
+                    for (int off = G / 2; off > 0; off >>= 1) {
+                        const uint64_t og = __shfl_xor_sync(FULL, gg, off);
+                        gg = og == 0 ? gg : (gg == 0 ? og : gcd64(gg, og));
+                        const uint64_t y = __shfl_xor_sync(FULL, amax, off);
+                        amax = y > amax ? y : amax;
+                    }
+                    if (gg == 0) gg = 1;
+                    const bool ovf = slow && amax / gg > 2147483647ull;
+                    if (slow && !ovf && gg > 1) {
+                        if (!big) {
+#pragma unroll
+                            for (int e = 0; e < EPL; ++e) t32[e] = t32[e] / (int32_t)gg;
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < CPL; ++i) {
+                                const int4 v = prow4[gl + G * i];
+                                const int4 w = col4[gl + G * i];
+                                const int32_t pv[4] = {v.x, v.y, v.z, v.w}, cv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                                for (int jj = 0; jj < 4; ++jj) {
+                                    const int64_t tt = (int64_t)A * pv[jj] + (int64_t)C * cv[jj];
+                                    t32[4 * i + jj] = (int32_t)(tt / (int64_t)gg);
+                                }
+                            }
+                        }
+                    }
+                    if (ovf && gl == 0) ++n_ovf;
+                    const uint64_t *pu = a.par.U + (size_t)p * W;
+                    bool pr = false;
+                    const bool cand = slow && !ovf;
+                    if (cand && !in_u) {
+                        const int64_t b1 = a.bptr[k];
+                        const int64_t n = a.bptr[k + 1] - b1;
+                        if (W <= 2) {
+                            const uint64_t u0 = child_word(pu, 0, k), u1 = W == 2 ? child_word(pu, 1, k) : 0ull;
+                            bool maybe = n > 0;
+                            if (maybe && a.band) {
+                                const uint64_t i0 = __ldg(a.band + (size_t)k * W), i1 = W == 2 ? __ldg(a.band + (size_t)k * W + 1) : 0ull;
+                                maybe = ((i0 & ~u0) | (i1 & ~u1)) == 0;
+                            }
+                            for (int64_t i = gl; i < n && !pr && maybe; i += G) {
+                                const uint64_t *E = a.bres + (size_t)(b1 + i) * W;
+                                const uint64_t e0 = __ldg(E), e1 = W == 2 ? __ldg(E + 1) : 0ull;
+                                pr = ((e0 & ~u0) | (e1 & ~u1)) == 0;
+                            }
+                        } else {
+                            for (int64_t i = gl; i < n && !pr; i += G) pr = result_inside_wide(a, pu, k, b1 + i);
+                        }
+                    }
+                    pr = group_or<G>(pr ? 1u : 0u) != 0;
+                    if (pr && gl == 0) ++n_pruned;
+                    const bool keep = cand && !pr;
+                    // summaries of the settled row: signs from phase A (a
+                    // positive scale keeps them), the rest over the row
+                    uint64_t um = 0, rh = 0;
+                    if (keep) {
+#pragma unroll
+                        for (int i = 0; i < CPL; ++i)
+#pragma unroll
+                            for (int jj = 0; jj < 4; ++jj) {
+                                const int m = 4 * (gl + G * i) + jj;
+                                const int32_t v = t32[4 * i + jj];
+                                if (m < nv.M && v != 0) {
+                                    if (v == 1 || v == -1) um |= 1ull << m;
+                                    rh += (uint64_t)(int64_t)v * blob_u64(bl, nv.o_hrow + 2 * m);
+                                }
+                            }
+                    }
+#pragma unroll
+                    for (int off = G / 2; off > 0; off >>= 1) {
+                        um |= __shfl_xor_sync(FULL, um, off);
+                        rh += __shfl_xor_sync(FULL, rh, off);
+                    }
+                    // the slow child's lane (sl) holds its phase-A sign masks
+                    const uint64_t spm = __shfl_sync(FULL, sm.pm, sl);
+                    const uint64_t snm = __shfl_sync(FULL, sm.nm, sl);
+                    const unsigned km = __ballot_sync(FULL, keep && gl == 0);
+                    if (km) {
+                        const uint64_t idx = reserve(__popc(km), __popc(km & ((1u << lead) - 1u)));
+                        if (keep) {
+                            if ((int64_t)idx < row_cap) {
+                                int4 *db = reinterpret_cast<int4 *>(a.child.B + (size_t)idx * Mpad);
+#pragma unroll
+                                for (int i = 0; i < CPL; ++i)
+                                    db[gl + G * i] = make_int4(t32[4 * i + 0], t32[4 * i + 1], t32[4 * i + 2], t32[4 * i + 3]);
+                                uint64_t *du = a.child.U + (size_t)idx * W;
+                                for (int w = gl; w < W; w += G) du[w] = child_word(pu, w, k);
+                                if (gl == 0) {
+                                    a.child.meta[idx] = pack_meta(mask_key(bl, nv, spm, snm), pc + (in_u ? 0 : 1));
+                                    uint64_t *d = a.child.sum + (size_t)idx * 4;
+                                    *reinterpret_cast<ulonglong2 *>(d) = make_ulonglong2(rh, spm);
+                                    *reinterpret_cast<ulonglong2 *>(d + 2) = make_ulonglong2(snm, um);
+                                    a.child.pmax[idx] = (uint32_t)(amax / gg);
+                                }
+                            } else if (gl == 0) {
+                                ++n_unwritten;
+                            }
+                            if (gl == 0) {
+                                if ((int64_t)idx < a.fp_cap) {
+                                    uint64_t f = rh ^ mix64(support_hash(pu, W, k) + 0x632BE59BD9B4E019ull);
+                                    if (f == kDeadFp) f = kDeadFp - 1;
+                                    a.fp[idx] = f;
+                                } else {
+                                    record_diag(a.ctr, ERR_BOUNDS, 7, (long long)idx, a.fp_cap, a.level);
+                                    fatal = true;
+                                }
+                            }
+                        }
+                    }
+                    fatal = group_or<G>(fatal ? 1u : 0u) != 0;
+                }
+                // a ready child: its row (phase A wrote the rest)
+                if (ok && !slow && (int64_t)ridx < row_cap) {
+                    int4 *db = reinterpret_cast<int4 *>(a.child.B + (size_t)ridx * Mpad);
+#pragma unroll
+                    for (int i = 0; i < CPL; ++i)
+                        db[gl + G * i] = make_int4(t32[4 * i + 0], t32[4 * i + 1], t32[4 * i + 2], t32[4 * i + 3]);
+                }
+            }
+        }
+        if (__any_sync(FULL, fatal)) break;
+    }
+    if (lane < pool_left && (int64_t)(pool_next + lane) < a.fp_cap) a.fp[pool_next + lane] = kDeadFp;
+    if (n_exp) atomicAdd(&a.ctr[C_EXP], n_exp);
+    if (n_ovf) atomicAdd(&a.ctr[C_OVF], n_ovf);
+    if (n_bal) atomicAdd(&a.ctr[C_BAL], n_bal);
+    if (n_pruned) atomicAdd(&a.ctr[C_PRUNED], n_pruned);
+    if (n_unwritten) atomicAdd(&a.ctr[C_UNWRITTEN], n_unwritten);
+}
+
+template <int G>
+__global__ void __launch_bounds__(kExpandWarps * 32, 3) generate_narrow_kernel(NetView nv, LevelArgs a, int staged)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int wid = threadIdx.x >> 5;
+    const int blob_words = staged ? nv.blob_words : 0;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + blob_words);
+    const uint32_t *bl = stage_blob(nv, smem, mbar, staged != 0, a.ctr);
+    if (bl == nullptr) return;
+    generate_narrow<G>(nv, a, bl, (int64_t)blockIdx.x * kExpandWarps + wid, (int64_t)gridDim.x * kExpandWarps);
 }
 
 // Are reserved rows i and j the same state (support and extra-flux row)?
@@ -2253,6 +2843,37 @@ cudaError_t launch_expand_t(const NetView &nv, const LevelArgs &a, int grid, cud
     return cudaGetLastError();
 }
 
+template <int G>
+cudaError_t launch_generate_narrow_t(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s)
+{
+    const bool staged = nv.blob_words * 4 <= kStageLimitBytes;
+    const size_t sm = (size_t)(staged ? nv.blob_words : 0) * 4 + 16;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(generate_narrow_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kStageLimitBytes + 16);
+        attr_set = true;
+    }
+    generate_narrow_kernel<G><<<grid, kExpandWarps * 32, sm, s>>>(nv, a, staged ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <int G>
+int generate_narrow_grid_t(const NetView &nv, int sm_count)
+{
+    const bool staged = nv.blob_words * 4 <= kStageLimitBytes;
+    const size_t sm = (size_t)(staged ? nv.blob_words : 0) * 4 + 16;
+    cudaFuncSetAttribute(generate_narrow_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageLimitBytes + 16);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, generate_narrow_kernel<G>, kExpandWarps * 32, sm) !=
+            cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return sm_count * per_sm;
+}
+
 template <int G, int CPL>
 cudaError_t launch_generate_t(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s)
 {
@@ -2345,6 +2966,11 @@ cudaError_t launch_expand(const NetView &nv, const LevelArgs &a, int grid, cudaS
 
 cudaError_t launch_generate(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s)
 {
+    // narrow networks: incremental summaries (needs the arenas' summary arrays)
+    if (nv.narrow && a.par.sum && a.child.sum) {
+        if (nv.EPL == 1) return launch_generate_narrow_t<4>(nv, a, grid, s);
+        if (nv.EPL == 2) return launch_generate_narrow_t<8>(nv, a, grid, s);
+    }
 #define CALL_GEN(G, C) launch_generate_t<G, C>(nv, a, grid, s)
     EFM_GROUP_DISPATCH(nv.EPL, CALL_GEN)
 #undef CALL_GEN
@@ -2353,6 +2979,8 @@ cudaError_t launch_generate(const NetView &nv, const LevelArgs &a, int grid, cud
 
 int generate_grid(const NetView &nv, int sm_count)
 {
+    if (nv.narrow && nv.EPL == 1) return generate_narrow_grid_t<4>(nv, sm_count);
+    if (nv.narrow && nv.EPL == 2) return generate_narrow_grid_t<8>(nv, sm_count);
 #define CALL_GGRID(G, C) generate_grid_t<G, C>(nv, sm_count)
     EFM_GROUP_DISPATCH(nv.EPL, CALL_GGRID)
 #undef CALL_GGRID

@@ -16,6 +16,13 @@
 //    (producers << 16 | row);
 //  - per column, ceil(log2(|S_int[:, k]|^2)) (for the Hadamard bound of the
 //    minimality test);
+//  - networks with at most 64 internal rows ("narrow"), for the expansion's
+//    incremental state summaries: per internal row its rank in the order of
+//    the positive and of the negative pivot keys; per rank the key; per row
+//    a 64-bit constant R[m] of the linear row hash sum_m EF_m R[m] (mod 2^64);
+//    per column the rank-space masks of its rows (positive and negative
+//    orders), its row-space mask, sum_m S_int[m][k] R[m], max |S_int[m][k]|
+//    and whether the gcd of its entries is 1;
 //  - a dense column-major copy of S_int: N rows of Mpad = 32 EPL int32,
 //    16-byte aligned.
 // Entries are packed as (index << 20) | (coefficient & 0xFFFFF).
@@ -31,6 +38,19 @@
 namespace efm {
 
 inline uint32_t ent_pack(int idx, int32_t coef) { return ((uint32_t)idx << 20) | ((uint32_t)coef & 0xFFFFFu); }
+
+constexpr int kNarrowRows = 64;  // internal rows of a network with state summaries
+constexpr int kColxWords = 10;   // per-column summary words (narrow networks)
+
+// Constant of internal row m in the linear row hash: the SplitMix64
+// finaliser (Steele, Lea, Flood 2014) of 0x9E3779B97F4A7C15 * (m + 1).
+inline uint64_t row_hash_constant(int m)
+{
+    uint64_t z = 0x9E3779B97F4A7C15ull * (uint64_t)(m + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
 
 // balance entries per lane for M internal rows (a row holds 32 EPL entries),
 // -1 beyond EFM_MAX_INTERNAL
@@ -50,6 +70,8 @@ struct NetPrep {
     std::vector<uint32_t> blob;
     int o_colptr = 0, o_colent = 0, o_consptr = 0, o_consent = 0, o_prodptr = 0, o_prodent = 0;
     int o_twin = 0, o_keypos = 0, o_keyneg = 0, o_hbits = 0, o_dcols = 0;
+    bool narrow = false;                            // M <= kNarrowRows: the sections below exist
+    int o_rank = 0, o_keyr = 0, o_hrow = 0, o_colx = 0;
     std::vector<int32_t> mptr;  // full S rows over split columns (seeds): [n_met + 1]
     std::vector<uint32_t> ment;  // packed (column, coefficient)
 };
@@ -58,8 +80,13 @@ struct NetPrep {
 // Returns EFM_OK or EFM_EINVAL (malformed CSR, index out of range, duplicate
 // entry in a row, zero or out-of-range coefficient, more than
 // EFM_MAX_COLUMNS split columns or EFM_MAX_INTERNAL internal metabolites).
+// flux_rows: the view of the subtractive traversal (Eq. 5), whose states
+// carry their flux vector after the extra flux: a row holds M + N entries
+// and the dense copy of column k is S_int[:, k] followed by the unit vector
+// e_k (flux 1 on k); EFM_EUNSUPPORTED when M + N exceeds EFM_MAX_INTERNAL.
 inline int prepare_network(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, const int32_t *col_idx,
-                           const int32_t *coef, const uint8_t *reversible, const uint8_t *external, NetPrep &out)
+                           const int32_t *coef, const uint8_t *reversible, const uint8_t *external, NetPrep &out,
+                           bool flux_rows = false)
 {
     if (n_met <= 0 || n_rxn <= 0 || !row_ptr || !reversible || !external) return EFM_EINVAL;
     if (row_ptr[0] != 0) return EFM_EINVAL;
@@ -96,8 +123,9 @@ inline int prepare_network(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr,
     int M = 0;
     for (int m = 0; m < n_met; ++m)
         if (!external[m]) int_row[m] = M++;
-    const int EPL = pick_epl(M);
-    if (N > EFM_MAX_COLUMNS || M > EFM_MAX_INTERNAL || EPL < 0) return EFM_EINVAL;
+    if (N > EFM_MAX_COLUMNS || M > EFM_MAX_INTERNAL || pick_epl(M) < 0) return EFM_EINVAL;
+    const int EPL = flux_rows ? pick_epl(M + N) : pick_epl(M);
+    if (EPL < 0) return EFM_EUNSUPPORTED;
     // S_int by column (rows ascending) and by internal row (columns ascending)
     std::vector<std::vector<std::pair<int, int32_t>>> col(N), cons(M), prod(M);
     std::vector<std::vector<std::pair<int, int32_t>>> metrow(n_met);
@@ -154,12 +182,71 @@ inline int prepare_network(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr,
     for (int r = 0; r < M; ++r) blob.push_back(((uint32_t)prod[r].size() << 16) | (uint32_t)r);
     out.o_hbits = (int)blob.size();
     for (int k = 0; k < N; ++k) blob.push_back(hbits[k]);
+    out.narrow = M <= kNarrowRows && !flux_rows;
+    out.o_rank = out.o_keyr = out.o_hrow = out.o_colx = 0;
+    if (out.narrow) {
+        // ranks of the rows in the positive / negative key orders
+        std::vector<std::pair<uint32_t, int>> kp, kn;
+        for (int r = 0; r < M; ++r) {
+            kp.push_back({((uint32_t)cons[r].size() << 16) | (uint32_t)r, r});
+            kn.push_back({((uint32_t)prod[r].size() << 16) | (uint32_t)r, r});
+        }
+        std::sort(kp.begin(), kp.end());
+        std::sort(kn.begin(), kn.end());
+        std::vector<int> rp(M), rn(M);
+        for (int i = 0; i < M; ++i) {
+            rp[kp[i].second] = i;
+            rn[kn[i].second] = i;
+        }
+        out.o_rank = (int)blob.size();
+        for (int r = 0; r < M; ++r) blob.push_back((uint32_t)rp[r] | ((uint32_t)rn[r] << 8));
+        out.o_keyr = (int)blob.size();
+        for (int i = 0; i < kNarrowRows; ++i) blob.push_back(i < M ? kp[i].first : 0xFFFFFFFFu);
+        for (int i = 0; i < kNarrowRows; ++i) blob.push_back(i < M ? kn[i].first : 0xFFFFFFFFu);
+        while (blob.size() % 2) blob.push_back(0);
+        out.o_hrow = (int)blob.size();
+        std::vector<uint64_t> R(M);
+        for (int r = 0; r < M; ++r) {
+            R[r] = row_hash_constant(r);
+            blob.push_back((uint32_t)R[r]);
+            blob.push_back((uint32_t)(R[r] >> 32));
+        }
+        out.o_colx = (int)blob.size();
+        for (int k = 0; k < N; ++k) {
+            uint64_t sp = 0, sn = 0, sr = 0, hc = 0;
+            uint32_t smax = 0, g = 0;
+            for (auto &e : col[k]) {
+                sp |= 1ull << rp[e.first];
+                sn |= 1ull << rn[e.first];
+                sr |= 1ull << e.first;
+                hc += (uint64_t)(int64_t)e.second * R[e.first];
+                const uint32_t a = (uint32_t)(e.second < 0 ? -e.second : e.second);
+                smax = std::max(smax, a);
+                uint32_t x = g, y = a;
+                while (y) {
+                    const uint32_t t = x % y;
+                    x = y;
+                    y = t;
+                }
+                g = x;
+            }
+            const uint64_t w[4] = {sp, sn, sr, hc};
+            for (uint64_t v : w) {
+                blob.push_back((uint32_t)v);
+                blob.push_back((uint32_t)(v >> 32));
+            }
+            blob.push_back(smax);
+            blob.push_back(g == 1 ? 1u : 0u);
+        }
+    }
     while (blob.size() % 4) blob.push_back(0);
     // dense column-major copy of S_int (row k = column k over Mpad rows)
     out.o_dcols = (int)blob.size();
     blob.resize(blob.size() + (size_t)N * 32 * EPL, 0u);
-    for (int k = 0; k < N; ++k)
+    for (int k = 0; k < N; ++k) {
         for (auto &e : col[k]) blob[(size_t)out.o_dcols + (size_t)k * 32 * EPL + e.first] = (uint32_t)e.second;
+        if (flux_rows) blob[(size_t)out.o_dcols + (size_t)k * 32 * EPL + M + k] = 1u;
+    }
     out.mptr.assign(n_met + 1, 0);
     out.ment.clear();
     for (int m = 0; m < n_met; ++m) {

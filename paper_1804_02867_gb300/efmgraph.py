@@ -32,7 +32,8 @@ EFM_MLP_PARAMS = 256 * 128 + 256 + 1
 
 class efm_limits(ctypes.Structure):
     _fields_ = [("max_len", ctypes.c_int32), ("max_secondary", ctypes.c_int32), ("max_results", ctypes.c_int64),
-                ("max_frontier", ctypes.c_int64), ("first_k", ctypes.c_int32), ("proposal", ctypes.c_int32)]
+                ("max_frontier", ctypes.c_int64), ("first_k", ctypes.c_int32), ("proposal", ctypes.c_int32),
+                ("variant", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class efm_counters(ctypes.Structure):
@@ -187,15 +188,17 @@ def efm_column_map(net):
 
 
 EFM_PLAIN, EFM_LEARNED = 0, 1
+EFM_ADDITIVE, EFM_SUBTRACTIVE = 0, 1
 
 
 def efm_find_pathways(net, targets, max_len, max_secondary, max_results=0, max_frontier=0, first_k=0,
-                      proposal=EFM_PLAIN, model=None):
+                      proposal=EFM_PLAIN, model=None, variant=EFM_ADDITIVE):
     """Returns (job handle, warning flags).  first_k > 0 asks for exactly the
-    K smallest results; proposal / model set the order of that search."""
+    K smallest results; proposal / model set the order of that search;
+    variant EFM_SUBTRACTIVE adds the Eq. 5 steps."""
     tg, ptg = _arr(targets, np.int32, ctypes.c_int32)
     lim = efm_limits(int(max_len), int(max_secondary), int(max_results), int(max_frontier), int(first_k),
-                     int(proposal))
+                     int(proposal), int(variant), 0)
     job = ctypes.c_void_p()
     rc = load_library().efm_find_pathways(net, ptg, len(tg), ctypes.byref(lim), model, ctypes.byref(job))
     if rc < 0:
@@ -203,10 +206,12 @@ def efm_find_pathways(net, targets, max_len, max_secondary, max_results=0, max_f
     return job.value, rc
 
 
-def efm_find_pathways_from(net, columns, max_len, max_secondary, max_results=0, max_frontier=0, first_k=0):
+def efm_find_pathways_from(net, columns, max_len, max_secondary, max_results=0, max_frontier=0, first_k=0,
+                           variant=EFM_ADDITIVE):
     """Traversal from a seed set of split columns.  Returns (job, flags)."""
     cols, pc = _arr(columns, np.int32, ctypes.c_int32)
-    lim = efm_limits(int(max_len), int(max_secondary), int(max_results), int(max_frontier), int(first_k), EFM_PLAIN)
+    lim = efm_limits(int(max_len), int(max_secondary), int(max_results), int(max_frontier), int(first_k), EFM_PLAIN,
+                     int(variant), 0)
     job = ctypes.c_void_p()
     rc = load_library().efm_find_pathways_from(net, pc, len(cols), ctypes.byref(lim), ctypes.byref(job))
     if rc < 0:
@@ -214,10 +219,11 @@ def efm_find_pathways_from(net, columns, max_len, max_secondary, max_results=0, 
     return job.value, rc
 
 
-def enumerate_from(network, columns, max_len, max_secondary, max_results=0, max_frontier=0, first_k=0):
+def enumerate_from(network, columns, max_len, max_secondary, max_results=0, max_frontier=0, first_k=0,
+                   variant=EFM_ADDITIVE):
     """efm_find_pathways_from + fetch: (supports, counters)."""
     job, _ = efm_find_pathways_from(network.handle, columns, max_len, max_secondary, max_results, max_frontier,
-                                    first_k)
+                                    first_k, variant)
     try:
         sup, ctr, _ = efm_fetch_results(job, 0)
         return sup, ctr
@@ -530,11 +536,11 @@ class Network:
 
 
 def enumerate_targets(network: Network, targets, max_len, max_secondary, max_results=0, max_frontier=0,
-                      timing=False, first_k=0, proposal=EFM_PLAIN, model=None):
+                      timing=False, first_k=0, proposal=EFM_PLAIN, model=None, variant=EFM_ADDITIVE):
     """Run efm_find_pathways over `targets` and fetch every target's result.
     Returns a list of (supports, counters[, timing dict])."""
     job, _ = efm_find_pathways(network.handle, list(targets), max_len, max_secondary, max_results, max_frontier,
-                               first_k, proposal, model)
+                               first_k, proposal, model, variant)
     try:
         out = []
         for i in range(len(targets)):

@@ -58,6 +58,21 @@ int main()
     for (int k = 0; k < p.N; ++k) std::printf("twin %d %d\n", k, (int)(int32_t)p.blob[p.o_twin + k]);
     for (int r = 0; r < p.M; ++r) std::printf("key %d %u %u\n", r, p.blob[p.o_keypos + r], p.blob[p.o_keyneg + r]);
     for (int k = 0; k < p.N; ++k) std::printf("hbits %d %u\n", k, p.blob[p.o_hbits + k]);
+    std::printf("narrow %d\n", p.narrow ? 1 : 0);
+    if (p.narrow) {
+        auto u64 = [&](int o) { return (unsigned long long)p.blob[o] | ((unsigned long long)p.blob[o + 1] << 32); };
+        for (int r = 0; r < p.M; ++r)
+            std::printf("rank %d %u %u\n", r, p.blob[p.o_rank + r] & 0xFFu, (p.blob[p.o_rank + r] >> 8) & 0xFFu);
+        for (int i = 0; i < efm::kNarrowRows; ++i)
+            std::printf("keyr %d %u %u\n", i, p.blob[p.o_keyr + i], p.blob[p.o_keyr + efm::kNarrowRows + i]);
+        for (int r = 0; r < p.M; ++r) std::printf("hrow %d %llu\n", r, u64(p.o_hrow + 2 * r));
+        for (int k = 0; k < p.N; ++k) {
+            const int o = p.o_colx + efm::kColxWords * k;
+            std::printf("colx %d %llu %llu %llu %llu %u %u\n", k, u64(o), u64(o + 2), u64(o + 4), u64(o + 6),
+                        p.blob[o + 8], p.blob[o + 9]);
+        }
+        std::printf("align64 %d %d\n", p.o_hrow % 2, p.o_colx % 2);
+    }
     std::printf("dense_offset_mod4 %d\n", p.o_dcols % 4);
     for (int k = 0; k < p.N; ++k) {
         std::printf("dense %d", k);

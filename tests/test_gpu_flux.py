@@ -47,8 +47,10 @@ def test_hand_worked(efm):
         if "flux" not in case:
             continue
         net = synth.Network.from_dense(case["S"], case["reversible"], case["external"])
+        variant = efm.EFM_SUBTRACTIVE if case.get("subtractive") else efm.EFM_ADDITIVE
         with efm.Network(net) as nw:
-            (sup, _), = efm.enumerate_targets(nw, [case["target"]], case["max_len"], case["max_secondary"])
+            (sup, _), = efm.enumerate_targets(nw, [case["target"]], case["max_len"], case["max_secondary"],
+                                              variant=variant)
             got, st = efm.efm_flux_vectors(nw.handle, sup)
         for i, w in enumerate(case["flux"]):
             assert st[i] == 1 and list(got[i, :len(w)]) == w, case["name"]

@@ -84,6 +84,37 @@ def expected_static(net):
     exp["hbits"] = [(q - 1).bit_length() if q > 1 else 0 for q in nsq]  # ceil(log2(q))
     exp["dense"] = [list(Si[:, k]) + [0] * (32 * epl - M) for k in range(N)]
     exp["met"] = [[(k, int(Ss[m, k])) for k in range(N) if Ss[m, k]] for m in range(net.n_met)]
+    if M <= 64:
+        # narrow networks: ranks in the key orders, keys by rank, row hash
+        # constants (SplitMix64 finaliser of 0x9E3779B97F4A7C15 (m + 1)), and
+        # per column: rank-space and row-space masks, sum S R, max |S|, gcd == 1
+        import math
+
+        mask = (1 << 64) - 1
+
+        def splitmix_fin(z):
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9 & mask
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EB & mask
+            return z ^ (z >> 31)
+
+        kp = sorted((exp["key"][r][0], r) for r in range(M))
+        kn = sorted((exp["key"][r][1], r) for r in range(M))
+        rp = {r: i for i, (_, r) in enumerate(kp)}
+        rn = {r: i for i, (_, r) in enumerate(kn)}
+        exp["rank"] = [(rp[r], rn[r]) for r in range(M)]
+        big = 0xFFFFFFFF
+        exp["keyr"] = [(kp[i][0] if i < M else big, kn[i][0] if i < M else big) for i in range(64)]
+        R = [splitmix_fin(0x9E3779B97F4A7C15 * (r + 1) & mask) for r in range(M)]
+        exp["hrow"] = R
+        exp["colx"] = []
+        for k in range(N):
+            rows = [r for r in range(M) if Si[r, k]]
+            g = 0
+            for r in rows:
+                g = math.gcd(g, abs(int(Si[r, k])))
+            exp["colx"].append((sum(1 << rp[r] for r in rows), sum(1 << rn[r] for r in rows), sum(1 << r for r in rows),
+                                sum(int(Si[r, k]) * R[r] for r in rows) & mask,
+                                max((abs(int(Si[r, k])) for r in rows), default=0), 1 if g == 1 else 0))
     return exp
 
 
@@ -114,6 +145,13 @@ def test_network_preparation_matches_the_definitions(netprep, which):
     assert [(int(f[1]), int(f[2])) for f in got.get("key", [])] == exp["key"]
     assert [int(f[1]) for f in got["hbits"]] == exp["hbits"]
     assert got["dense_offset_mod4"] == [["0"]]
+    assert got["narrow"] == [["1" if M <= 64 else "0"]]
+    if M <= 64:
+        assert [(int(f[1]), int(f[2])) for f in got["rank"]] == exp["rank"]
+        assert [(int(f[1]), int(f[2])) for f in got["keyr"]] == exp["keyr"]
+        assert [int(f[1]) for f in got["hrow"]] == exp["hrow"]
+        assert [tuple(int(x) for x in f[1:]) for f in got["colx"]] == exp["colx"]
+        assert got["align64"] == [["0", "0"]]
     assert [[int(x) for x in f[1:]] for f in got["dense"]] == exp["dense"]
     assert [_pairs(f[1:]) for f in got["met"]] == exp["met"]
 
