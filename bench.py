@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--budget", type=int, default=BUDGET)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the batched, genome and first-K summaries of the default run")
     ap.add_argument("--workload", choices=["core", "batched", "genome", "firstk", "sample"], default="core",
                     help="core: the headline line; batched: 4096 uneven networks in one persistent launch; "
                          "genome: the genome-shaped network; firstk: first-K queries, learned vs plain order")
@@ -167,18 +169,30 @@ class ClockSampler:
 
 
 def oracle_sample(net, budget, threads):
-    """Run the CPU oracle over the 8 targets on `threads` host threads."""
+    """Run the CPU oracle over the 8 targets on `threads` host threads; with
+    more threads than targets every target is run ceil(threads / 8) times,
+    so that all of them have work (each run is one independent job)."""
     import oracle
 
     oracle.build()
     lim = oracle.Limits(MAX_LEN, MAX_SEC, 0, budget)
+    reps = max(1, -(-threads // len(net.targets)))
+    jobs = list(net.targets) * reps
     t0 = time.perf_counter()
     with cf.ThreadPoolExecutor(max_workers=threads) as ex:
-        outs = list(ex.map(lambda t: oracle.enumerate_pathways(net, t, lim), net.targets))
+        outs = list(ex.map(lambda t: oracle.enumerate_pathways(net, t, lim), jobs))
     dt = time.perf_counter() - t0
     exp = sum(c["expansions"] for _, c in outs)
     res = sum(len(s) for s, _ in outs)
     return exp, res, dt
+
+
+def host_threads():
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def run_reference(args):
@@ -189,7 +203,7 @@ def run_reference(args):
     from paper_1804_02867_gb300 import synth
 
     net = synth.core()
-    threads = min(os.cpu_count() or 1, len(net.targets))
+    threads = host_threads()
     for _ in range(args.warmup):
         oracle_sample(net, REF_STEP_BUDGET, threads)
     tot_exp, tot_res, tot_t, times = 0, 0, 0.0, []
@@ -200,8 +214,9 @@ def run_reference(args):
         tot_t += dt
         times.append(dt)
     value = tot_exp / tot_t
-    sample = (f"core-72x95, 8 targets, max_len {MAX_LEN}, max_secondary {MAX_SEC}, frontier budget "
-              f"{REF_STEP_BUDGET} per step (the workload's own budget is {args.budget})")
+    sample = (f"core-72x95, the 8 targets x {max(1, -(-threads // 8))} jobs on {threads} threads, max_len {MAX_LEN}, "
+              f"max_secondary {MAX_SEC}, frontier budget {REF_STEP_BUDGET} per step (the workload's own budget is "
+              f"{args.budget})")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
@@ -241,11 +256,12 @@ def run_ours(args):
     # CPU baseline first, before heavy GPU use (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        threads = min(os.cpu_count() or 1, len(targets))
+        threads = host_threads()
         e, r, dt = oracle_sample(net, CPU_SAMPLE_BUDGET, threads)
         cpu = {"value": e / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"core-72x95, 8 targets in parallel, max_len {MAX_LEN}, max_secondary {MAX_SEC}, "
-                         f"frontier budget {CPU_SAMPLE_BUDGET} (GPU: {budget}); {e} expansions in {dt:.1f} s",
+               "sample": f"core-72x95, the 8 targets x {max(1, -(-threads // 8))} independent jobs on {threads} "
+                         f"threads, max_len {MAX_LEN}, max_secondary {MAX_SEC}, frontier budget {CPU_SAMPLE_BUDGET} "
+                         f"(GPU: {budget}); {e} expansions in {dt:.1f} s",
                "balanced_pathways_per_s": r / dt}
 
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
@@ -325,6 +341,11 @@ def run_ours(args):
         e2e_t += time.perf_counter() - t0
         d2h = step_d2h
 
+    # the other workloads, compact, after the headline's timed region (rank 0, N = 1)
+    secondary = None
+    if rank == 0 and ws == 1 and not args.no_secondary:
+        secondary = run_secondary(args)
+
     # max over ranks of the device time; sum of work over ranks
     if ws > 1:
         (tot_ms, e2e_t), (tot_exp, tot_res, e2e_exp) = reduce_over_ranks([tot_ms, e2e_t], [tot_exp, tot_res, e2e_exp],
@@ -370,6 +391,7 @@ def run_ours(args):
         "e2e": {"value": e2e_exp / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": tot_kl,
         "clocks": clk,
+        "secondary": secondary,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -378,6 +400,27 @@ def run_ours(args):
 
 BATCH_BUDGET = 2**12
 GENOME_BUDGET = 2**22
+
+
+def run_secondary(args):
+    """Compact runs of the batched, genome and first-K workloads for the
+    default line (each measured on its own, after the headline)."""
+    from types import SimpleNamespace
+
+    out = {}
+    b = run_batched(SimpleNamespace(steps=2, warmup=1, jobs=4096))
+    out["batched"] = {"jobs": 4096, "ms_per_launch": b["ms_per_step"], "expansions_per_s": b["value"],
+                      "sequential_ms": b["sequential"]["ms"], "speedup_vs_sequential": b["speedup_vs_sequential"],
+                      "autotuner": b["autotuner"]}
+    g = run_genome(SimpleNamespace(steps=1, warmup=1, jobs=32, budget=BUDGET))
+    out["genome"] = {"targets": 32, "max_frontier": GENOME_BUDGET, "expansions_per_s": g["value"],
+                     "ms_per_step": g["ms_per_step"], "roofline_frac": g["roofline"]["frac"],
+                     "status_counts": g["status_counts"]}
+    f = run_firstk(SimpleNamespace(steps=1, warmup=1, jobs=192))
+    out["firstk"] = {"k": FIRSTK_K, "held_out_targets": 192, "plain_over_learned_time": f["value"],
+                     **{k: f["first_k"][k] for k in ("certified_both", "certified_plain_only",
+                                                      "certified_learned_only", "identical_sets")}}
+    return out
 
 
 def run_genome(args):
@@ -400,12 +443,17 @@ def run_genome(args):
     budget = args.budget if args.budget != BUDGET else GENOME_BUDGET
     nw = efmgraph.Network(net, stream)
 
+    status_counts = {}
+
     def step():
         job, _ = efmgraph.efm_find_pathways(nw.handle, targets, 40, MAX_SEC, 0, budget)
         exp = res = el = 0
         eb = ems = 0.0
         for i in range(n_t):
             _, c, _ = efmgraph.efm_fetch_results(job, i, copy=False)
+            key = "+".join(n for n, b in (("truncated", 1), ("capped", 2), ("overflow_dropped", 4))
+                           if c["status"] & b) or "complete"
+            status_counts[key] = status_counts.get(key, 0) + 1
             tm = efmgraph.efm_job_timing(job, i)
             exp += c["expansions"]
             res += c["results"]
@@ -418,6 +466,7 @@ def run_genome(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    status_counts.clear()
     tot_ms = eb = ems = 0.0
     exp = res = el = 0
     for _ in range(args.steps):
@@ -450,8 +499,9 @@ def run_genome(args):
                      "peak": float(peaks["hbm_gbs"]), "unit": "GB/s", "frac": achieved / float(peaks["hbm_gbs"]),
                      "traffic": traffic, "peak_kind": f"{kind} HBM copy bandwidth", "launches": el,
                      "avg_launch_ms": ems / max(el, 1), "alg_bytes_per_launch": eb / max(el, 1)},
+        "status_counts": status_counts,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_batched(args):
@@ -528,7 +578,7 @@ def run_batched(args):
         "speedup_vs_sequential": (seq_ms / (tot_ms / args.steps)),
         "autotuner": {"ctas_per_sm": tune[0], "largest_first": bool(tune[1])} if tune else None,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 FIRSTK_K = 1000
@@ -624,7 +674,7 @@ def run_firstk(args):
         "training": {"rows": n_rows, "positives": n_pos, "pos_weight": pos_weight, "epochs": 20,
                      "final_loss": loss, "trace_s": trace_s, "train_s": train_s},
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 SAMPLE_WALKS = 2**20
@@ -700,7 +750,7 @@ def run_sample(args):
         "coverage": {"target": COVERAGE_TARGET, "max_len": COVERAGE_LEN, "results_exhaustive": n_all,
                      "uniform_coupon_walks_to_all": n_all * h_n, "curve": coverage},
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
@@ -708,13 +758,13 @@ def main():
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":
-        run_batched(args)
+        print(json.dumps(run_batched(args)), flush=True)
     elif args.workload == "genome":
-        run_genome(args)
+        print(json.dumps(run_genome(args)), flush=True)
     elif args.workload == "firstk":
-        run_firstk(args)
+        print(json.dumps(run_firstk(args)), flush=True)
     elif args.workload == "sample":
-        run_sample(args)
+        print(json.dumps(run_sample(args)), flush=True)
     else:
         run_ours(args)
 

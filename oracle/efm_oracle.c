@@ -817,6 +817,47 @@ static int normalise2(const int64_t *ef, int M, const int64_t *v, int N, int32_t
     return ovf;
 }
 
+/* Sort the child list and keep one record per key (the smallest sec). */
+static void compact_children(vec *C, size_t key, size_t stride)
+{
+    g_keylen = key;
+    qsort(C->data, C->n, stride, cmp_state);
+    size_t u = 0;
+    for (size_t i = 0; i < C->n; ++i) {
+        uint8_t *ci = (uint8_t *)vec_at(C, i);
+        if (u > 0) {
+            uint8_t *cu = (uint8_t *)vec_at(C, u - 1);
+            if (memcmp(cu, ci, key) == 0) {
+                int32_t *su = (int32_t *)(cu + key), *si = (int32_t *)(ci + key);
+                if (*si < *su) *su = *si;
+                continue;
+            }
+        }
+        if (u != i) memcpy(vec_at(C, u), ci, stride);
+        ++u;
+    }
+    C->n = u;
+}
+
+/* Store a surviving child of a level.  With a frontier budget the list is
+ * compacted (deduplicated) whenever it reaches 1.5 budgets; once it holds
+ * more distinct states than the budget the level is truncated whatever
+ * follows, so later children are no longer stored (*over; they are still
+ * counted and judged by the caller).  This bounds the host memory of a
+ * truncating level and changes no result or counter. */
+static int push_child(vec *C, const uint8_t *rec, size_t key, size_t stride, const or_limits *lim, int *over)
+{
+    if (*over) return 0;
+    if (lim->max_frontier > 0 && (int64_t)C->n >= lim->max_frontier + lim->max_frontier / 2 + 16) {
+        compact_children(C, key, stride);
+        if ((int64_t)C->n > lim->max_frontier) {
+            *over = 1;
+            return 0;
+        }
+    }
+    return vec_push(C, rec);
+}
+
 /* The traversal from the seeds of a target (seedset == NULL), or from the
  * one state of a seed set R_in (Prop. 1): U = R_in with flux 1 on each of
  * its columns, EF = sum of their S_int columns / gcd, no secondary step,
@@ -934,6 +975,7 @@ static int enumerate_impl(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, 
 
     for (int64_t level = level0 + 1; F.n > 0; ++level) {
         C.n = 0;
+        int over = 0; /* the level already holds more distinct states than the budget */
         for (size_t s = 0; s < F.n; ++s) {
             const uint8_t *st = (const uint8_t *)vec_at(&F, s);
             const uint64_t *U = (const uint64_t *)st;
@@ -990,7 +1032,7 @@ static int enumerate_impl(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, 
                     ctr->pruned++;
                     continue;
                 }
-                if (vec_push(&C, rec)) {
+                if (push_child(&C, rec, key, stride, lim, &over)) {
                     rc = OR_ENOMEM;
                     goto done;
                 }
@@ -1027,7 +1069,7 @@ static int enumerate_impl(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, 
                     if ((rc = judge(&R, U2, level)) != OR_OK) goto done;
                     continue;
                 }
-                if (vec_push(&C, rec)) {
+                if (push_child(&C, rec, key, stride, lim, &over)) {
                     rc = OR_ENOMEM;
                     goto done;
                 }
@@ -1035,28 +1077,12 @@ static int enumerate_impl(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr, 
         }
         /* F_level = distinct (U, EF) of the surviving children (with v in
          * the subtractive variant) */
-        g_keylen = key;
-        qsort(C.data, C.n, stride, cmp_state);
-        size_t u = 0;
-        for (size_t i = 0; i < C.n; ++i) {
-            uint8_t *ci = (uint8_t *)vec_at(&C, i);
-            if (u > 0) {
-                uint8_t *cu = (uint8_t *)vec_at(&C, u - 1);
-                if (memcmp(cu, ci, key) == 0) {
-                    int32_t *su = (int32_t *)(cu + key), *si = (int32_t *)(ci + key);
-                    if (*si < *su) *su = *si;
-                    continue;
-                }
-            }
-            if (u != i) memcpy(vec_at(&C, u), ci, stride);
-            ++u;
-        }
-        C.n = u;
+        compact_children(&C, key, stride);
         vec t = F;
         F = C;
         C = t;
         ctr->levels = level - level0 + 1;
-        if (lim->max_frontier > 0 && (int64_t)F.n > lim->max_frontier) {
+        if (over || (lim->max_frontier > 0 && (int64_t)F.n > lim->max_frontier)) {
             ctr->status |= OR_TRUNCATED;
             break;
         }

@@ -293,9 +293,11 @@ namespace {
 // Device buffers of one traversal, reused across the targets of a job.
 struct Work {
     DevBuf U[2], B[2], meta[2], live[2];
-    DevBuf sum[2], pmax[2];  // narrow networks: per-state summaries of the extra-flux row
+    DevBuf sum[2];  // narrow networks: per-state summaries of the extra-flux row
     DevBuf slots, cslots, cand, res, bcnt, bfill, bptr, bres, ctr, sortidx, rcols;
     DevBuf fp;         // fingerprints of one level's reserved child rows
+    DevBuf slow;       // narrow networks: records of the children the settle pass decides
+    int64_t slow_cap = 0;
     DevBuf perm, fkb;  // first-K search: parent order of a level, bound support
     DevBuf band;       // per column: intersection of the results containing it (W <= 2)
     DevBuf lx, lscore, lhist, lerr;  // learned order: features, scores, buckets, error flag
@@ -314,7 +316,6 @@ void free_arena(Work &w, int i, cudaStream_t s)
     dev_free(w.meta[i], s);
     dev_free(w.live[i], s);
     dev_free(w.sum[i], s);
-    dev_free(w.pmax[i], s);
     w.rows[i] = 0;
 }
 
@@ -323,7 +324,7 @@ void free_work(Work &w, cudaStream_t s)
     for (int i = 0; i < 2; ++i) free_arena(w, i, s);
     DevBuf *bufs[] = {&w.slots, &w.cslots, &w.cand, &w.res, &w.bcnt,    &w.bfill, &w.bptr,
                       &w.bres,  &w.ctr,    &w.sortidx, &w.rcols, &w.perm, &w.fkb,
-                      &w.lx,    &w.lscore, &w.lhist,   &w.lerr, &w.band, &w.fp};
+                      &w.lx,    &w.lscore, &w.lhist,   &w.lerr, &w.band, &w.fp, &w.slow};
     for (DevBuf *b : bufs) dev_free(*b, s);
     for (auto &e : w.ev)
         if (e) cudaEventDestroy(e);
@@ -336,7 +337,7 @@ bool alloc_arena(Work &w, const NetView &nv, int i, int64_t rows, cudaStream_t s
     const size_t F = (size_t)rows;
     bool ok = dev_alloc(w.U[i], F * nv.W * 8, s) && dev_alloc(w.B[i], F * nv.Mpad * 4, s) &&
               dev_alloc(w.meta[i], F * 4, s) && dev_alloc(w.live[i], F * 4, s);
-    if (ok && nv.narrow) ok = dev_alloc(w.sum[i], F * 32, s) && dev_alloc(w.pmax[i], F * 4, s);
+    if (ok && nv.narrow) ok = dev_alloc(w.sum[i], F * kSumWords * 8, s);
     if (ok) w.rows[i] = rows;
     return ok;
 }
@@ -516,7 +517,6 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
         r.meta = (uint32_t *)w.meta[i].p;
         r.cap = w.rows[i];
         r.sum = (uint64_t *)w.sum[i].p;
-        r.pmax = (uint32_t *)w.pmax[i].p;
         return r;
     };
 
@@ -685,6 +685,13 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
                                                                                      deg_sum / (64ull * total_warps)));
         const uint64_t reserved = deg_sum + (uint64_t)launches * blk * total_warps + 64;
         if (!ensure_level_tables(w, reserved, s)) return EFM_ENOMEM;
+        // narrow networks: room for every child of a launch in the settle list
+        if (nv.narrow && (int64_t)deg_sum + 64 > w.slow_cap) {
+            dev_free(w.slow, s);
+            const int64_t cap = std::max<int64_t>((int64_t)deg_sum + 64, w.slow_cap + w.slow_cap / 2);
+            if (!dev_alloc(w.slow, (size_t)cap * kSlowWords * 8, s)) return EFM_ENOMEM;
+            w.slow_cap = cap;
+        }
         const uint64_t nslots = next_pow2(2 * reserved + 64);
         unsigned long long snap[C_COUNT];
         memcpy(snap, h, sizeof(h));
@@ -704,6 +711,8 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
             a.fp = (uint64_t *)w.fp.p;
             a.fp_cap = w.fp_cap;
             a.blk = blk;
+            a.slow = nv.narrow ? (uint64_t *)w.slow.p : nullptr;
+            a.slow_cap = nv.narrow ? w.slow_cap : 0;
             a.level = level;
             unsigned long long exp_before = h[C_EXP];
             uint64_t next_before = 0;
@@ -716,7 +725,9 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
                 a.fk_sup = (const uint64_t *)w.fkb.p;
                 a.max_len = (fk && top.pc > 0) ? std::min(lim.max_len, top.pc) : lim.max_len;
                 CK(cudaEventRecord(w.ev[2], s));
+                CK(cudaMemsetAsync(ctr + C_SLOW, 0, 8, s));
                 CK(launch_generate(nv, a, grid, s));
+                CK(launch_settle(nv, a, net->sm_count, s));
                 CK(launch_dedup(a, nv.Mpad, nv.W, net->sm_count, s));
                 CK(cudaEventRecord(w.ev[3], s));
                 // minimality test of the new candidates, range taken on the device
@@ -731,7 +742,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
                 CK(cudaEventElapsedTime(&ms, w.ev[2], w.ev[3]));
                 out.expand_ms += ms;
                 out.expand_launches += 1;
-                out.kernel_launches += 5;
+                out.kernel_launches += nv.narrow ? 6 : 5;
                 {
                     const double state_bytes = 8.0 * nv.W + 4.0 * nv.M + 4.0;
                     const uint64_t next_now = h[C_NEXT];

@@ -43,6 +43,7 @@ enum {
     C_DEDUP_BEGIN,  // first reserved row the next dedup launch examines
     C_DIAG = 24,  // first bounds/watchdog record: code, value, limit, level
     C_ZERO = 28,  // subtractive steps discarded: no positive flux left on the reaction (Prop. 3)
+    C_SLOW,       // narrow networks: children handed to the settle pass in this launch
     C_COUNT = 32
 };
 
@@ -80,15 +81,17 @@ struct Arena {
     int32_t *B;      // [cap][Mpad]
     uint32_t *meta;  // [cap]: pivot row | pivot degree << 10 | |U| << 23
     int64_t cap;
-    // narrow networks: per-state summaries of the extra-flux row EF
-    //   sum[4 s + 0] = sum_m EF_m R[m] (mod 2^64), the linear row hash
-    //   sum[4 s + 1] = positive entries, bit = rank of the row in the positive key order
-    //   sum[4 s + 2] = negative entries, bit = rank of the row in the negative key order
-    //   sum[4 s + 3] = rows with |EF_m| = 1
-    //   pmax[s]      = an upper bound of max_m |EF_m| (saturating at 2^31 - 1)
+    // narrow networks: per-state summaries of the extra-flux row EF, kSumWords each
+    //   sum[6 s + 0] = sum_m EF_m R[m] (mod 2^64), the linear row hash
+    //   sum[6 s + 1] = positive entries, bit = rank of the row in the positive key order
+    //   sum[6 s + 2] = negative entries, bit = rank of the row in the negative key order
+    //   sum[6 s + 3] = rows with |EF_m| = 1
+    //   sum[6 s + 4] = rows with odd EF_m
+    //   sum[6 s + 5] = an upper bound of max_m |EF_m| (saturating at 2^31 - 1)
     uint64_t *sum;
-    uint32_t *pmax;
 };
+
+constexpr int kSumWords = 6;
 
 struct LevelArgs {
     Arena par;
@@ -123,7 +126,13 @@ struct LevelArgs {
     // the flux of every column; a state's branches also take flux away from
     // a column in U, and its meta degree counts both lists of the pivot
     int sub;
+    // narrow networks: children whose gcd or int32 range is not settled by
+    // the summaries, kSlowWords words each, for the settle pass
+    uint64_t *slow;
+    int64_t slow_cap;
 };
+
+constexpr int kSlowWords = 8;
 
 constexpr unsigned long long kDeadFp = ~0ull;  // fingerprint of a reserved row left unused
 
@@ -217,6 +226,9 @@ cudaError_t launch_expand(const NetView &nv, const LevelArgs &a, int grid, cudaS
 // then one pass that keeps the first row of every distinct state
 cudaError_t launch_generate(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_dedup(const LevelArgs &a, int Mpad, int W, int sm_count, cudaStream_t s);
+// narrow networks: settle the children the generate pass listed (exact gcd,
+// int32 range, superset rule), then write their rows; a no-op otherwise
+cudaError_t launch_settle(const NetView &nv, const LevelArgs &a, int sm_count, cudaStream_t s);
 int generate_grid(const NetView &nv, int sm_count);
 cudaError_t launch_accept(const NetView &nv, const AcceptArgs &a, cudaStream_t s);
 // minimality test of the candidates appended since the last such launch (range read on the

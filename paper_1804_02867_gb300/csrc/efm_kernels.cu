@@ -351,7 +351,7 @@ __device__ __forceinline__ void normalise(int64_t (&t64)[EPL], int32_t (&t32)[EP
 // ---------------------------------------------------------------------------
 
 struct NarrowSum {
-    uint64_t rh, pm, nm, um;
+    uint64_t rh, pm, nm, um, om;
     uint32_t pmax;
 };
 
@@ -364,7 +364,7 @@ __device__ __forceinline__ uint64_t blob_u64(const uint32_t *bl, int o)
 template <int EPL>
 __device__ NarrowSum warp_summary(const uint32_t *bl, const NetView &nv, const int32_t (&t)[EPL], int lane)
 {
-    NarrowSum r{0, 0, 0, 0, 0};
+    NarrowSum r{0, 0, 0, 0, 0, 0};
 #pragma unroll
     for (int e = 0; e < EPL; ++e) {
         const int m = lane + 32 * e;
@@ -374,6 +374,7 @@ __device__ NarrowSum warp_summary(const uint32_t *bl, const NetView &nv, const i
             if (v > 0) r.pm |= 1ull << (rk & 0xFFu);
             else r.nm |= 1ull << ((rk >> 8) & 0xFFu);
             if (v == 1 || v == -1) r.um |= 1ull << m;
+            if (v & 1) r.om |= 1ull << m;
             const uint32_t a = (uint32_t)(v < 0 ? -v : v);
             r.pmax = a > r.pmax ? a : r.pmax;
             r.rh += (uint64_t)(int64_t)v * blob_u64(bl, nv.o_hrow + 2 * m);
@@ -384,6 +385,7 @@ __device__ NarrowSum warp_summary(const uint32_t *bl, const NetView &nv, const i
         r.pm |= __shfl_xor_sync(FULL, r.pm, off);
         r.nm |= __shfl_xor_sync(FULL, r.nm, off);
         r.um |= __shfl_xor_sync(FULL, r.um, off);
+        r.om |= __shfl_xor_sync(FULL, r.om, off);
         r.rh += __shfl_xor_sync(FULL, r.rh, off);
         const uint32_t o = __shfl_xor_sync(FULL, r.pmax, off);
         r.pmax = o > r.pmax ? o : r.pmax;
@@ -391,13 +393,25 @@ __device__ NarrowSum warp_summary(const uint32_t *bl, const NetView &nv, const i
     return r;
 }
 
+// the summary record of a state: 6 words, written as three 16-byte stores
+__device__ __forceinline__ void put_summary(uint64_t *d, const NarrowSum &s)
+{
+    *reinterpret_cast<ulonglong2 *>(d) = make_ulonglong2(s.rh, s.pm);
+    *reinterpret_cast<ulonglong2 *>(d + 2) = make_ulonglong2(s.nm, s.um);
+    *reinterpret_cast<ulonglong2 *>(d + 4) = make_ulonglong2(s.om, (uint64_t)s.pmax);
+}
+
+__device__ __forceinline__ NarrowSum get_summary(const uint64_t *d)
+{
+    const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(d);
+    const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(d + 2);
+    const ulonglong2 c = *reinterpret_cast<const ulonglong2 *>(d + 4);
+    return NarrowSum{a.x, a.y, b.x, b.y, c.x, (uint32_t)c.y};
+}
+
 __device__ __forceinline__ void store_summary(const Arena &ar, uint64_t idx, const NarrowSum &s, int lane)
 {
-    // one 16-byte store per lane pair: lanes 0 and 1 write the record
-    uint64_t *d = ar.sum + (size_t)idx * 4;
-    if (lane == 0) *reinterpret_cast<ulonglong2 *>(d) = make_ulonglong2(s.rh, s.pm);
-    if (lane == 1) *reinterpret_cast<ulonglong2 *>(d + 2) = make_ulonglong2(s.nm, s.um);
-    if (lane == 2) ar.pmax[idx] = s.pmax;
+    if (lane == 0) put_summary(ar.sum + (size_t)idx * kSumWords, s);
 }
 
 // pivot key from the two masks (0xFFFFFFFF when balanced)
@@ -1742,11 +1756,9 @@ __device__ void generate_narrow(const NetView &nv, const LevelArgs &a, const uin
 {
     constexpr int CPL = 2;
     constexpr int NG = 32 / G;
-    constexpr int EPL = 4 * CPL;
     const int lane = threadIdx.x & 31;
     const int gi = lane / G;
     const int gl = lane % G;
-    const int lead = gi * G;
     const int W = nv.W;
     const int Mpad = nv.Mpad;
     const int4 *dcol = reinterpret_cast<const int4 *>(bl + nv.o_dcols);
@@ -1788,7 +1800,7 @@ __device__ void generate_narrow(const NetView &nv, const LevelArgs &a, const uin
             for (int off = 0; off < Mpad * 4; off += 128) prefetch_l2(rp + off);
             prefetch_l2(a.par.U + (size_t)nid * W);
             prefetch_l2(a.par.meta + nid);
-            prefetch_l2(a.par.sum + (size_t)nid * 4);
+            prefetch_l2(a.par.sum + (size_t)nid * kSumWords);
         }
         const uint32_t mj = pin ? a.par.meta[pid] : 0u;
         int dj = pin ? (int)((mj >> 10) & 0x1FFFu) : 0;
@@ -1858,18 +1870,17 @@ __device__ void generate_narrow(const NetView &nv, const LevelArgs &a, const uin
             }
             if (okl) ++n_exp;
             // summaries of the child (exact signs from 64-bit entries)
-            NarrowSum sm{0, 0, 0, 0, 0};
+            NarrowSum sm{0, 0, 0, 0, 0, 0};
             bool fast = false, cert = false;
             if (okl) {
-                const uint64_t *ps = a.par.sum + (size_t)pl_ * 4;
-                const ulonglong2 s01 = *reinterpret_cast<const ulonglong2 *>(ps);
-                const ulonglong2 s23 = *reinterpret_cast<const ulonglong2 *>(ps + 2);
-                const uint32_t pmaxp = a.par.pmax[pl_];
+                const NarrowSum ps = get_summary(a.par.sum + (size_t)pl_ * kSumWords);
+                const uint32_t pmaxp = ps.pmax;
                 const int ox = nv.o_colx + kColxWordsDev * kl;
                 const uint64_t suppP = blob_u64(bl, ox), suppN = blob_u64(bl, ox + 2), suppR = blob_u64(bl, ox + 4);
                 const uint32_t smax = bl[ox + 8], gcd1 = bl[ox + 9];
                 fast = (uint64_t)Al * pmaxp + (uint64_t)Cl * smax <= 2147483647ull;
-                uint64_t newp = 0, newn = 0, newu = 0, tmax = 0;
+                uint64_t newp = 0, newn = 0, newu = 0, newo = 0, tmax = 0;
+                uint32_t gt = 0;  // gcd of the changed entries (exact when fast: they fit 32 bits)
                 for (int qq = (int)bl[nv.o_colptr + kl]; qq < (int)bl[nv.o_colptr + kl + 1]; ++qq) {
                     const uint32_t e = bl[nv.o_colent + qq];
                     const int m = ent_index(e);
@@ -1878,19 +1889,24 @@ __device__ void generate_narrow(const NetView &nv, const LevelArgs &a, const uin
                     newp |= (tm > 0 ? 1ull : 0ull) << (rk & 0xFFu);
                     newn |= (tm < 0 ? 1ull : 0ull) << ((rk >> 8) & 0xFFu);
                     newu |= ((tm == 1 || tm == -1) ? 1ull : 0ull) << m;
+                    newo |= (uint64_t)(tm & 1) << m;
                     const uint64_t am = (uint64_t)(tm < 0 ? -tm : tm);
                     tmax = am > tmax ? am : tmax;
+                    if (am != 0 && gt != 1) gt = gt == 0 ? (uint32_t)am : gcd32(gt, (uint32_t)am);
                 }
-                sm.pm = (s01.y & ~suppP) | newp;
-                sm.nm = (s23.x & ~suppN) | newn;
-                const uint64_t uout = s23.y & ~suppR;  // parent's +-1 rows outside column k
+                sm.pm = (ps.pm & ~suppP) | newp;
+                sm.nm = (ps.nm & ~suppN) | newn;
+                const uint64_t uout = ps.um & ~suppR;  // parent's +-1 rows outside column k
                 sm.um = (Al == 1 ? uout : 0ull) | newu;
-                sm.rh = (uint64_t)(int64_t)Al * s01.x + (uint64_t)(int64_t)Cl * blob_u64(bl, ox + 6);
+                sm.om = ((Al & 1) ? (ps.om & ~suppR) : 0ull) | newo;  // odd rows (A p is odd iff both are)
+                sm.rh = (uint64_t)(int64_t)Al * ps.rh + (uint64_t)(int64_t)Cl * blob_u64(bl, ox + 6);
                 const uint64_t bound = (uint64_t)Al * pmaxp > tmax ? (uint64_t)Al * pmaxp : tmax;
                 sm.pmax = bound > 2147483647ull ? 2147483647u : (uint32_t)bound;
-                // gcd(t) = 1 without computing it: a +-1 entry in the child, or
-                // a parent +-1 outside column k with A = 1 or a coprime column
-                cert = sm.um != 0 || (uout != 0 && (Al == 1 || gcd1 != 0));
+                // gcd(t) = 1 without computing it: a +-1 entry in the child, a
+                // parent +-1 outside column k with A = 1 or a coprime column, or
+                // coprime changed entries (every common divisor divides them)
+                cert = sm.um != 0 || (uout != 0 && (Al == 1 || gcd1 != 0)) || (fast && gt == 1) ||
+                       (fast && gt != 0 && (gt & (gt - 1)) == 0 && sm.om != 0);  // gcd | 2^a, and an odd entry
             }
             const bool nzl = (sm.pm | sm.nm) != 0;
             const bool ball = okl && !nzl;
@@ -1939,10 +1955,7 @@ __device__ void generate_narrow(const NetView &nv, const LevelArgs &a, const uin
                         uint64_t *du = a.child.U + (size_t)myidx * W;
                         for (int w = 0; w < W; ++w) du[w] = child_word(pu_l, w, kl);
                         a.child.meta[myidx] = pack_meta(mask_key(bl, nv, sm.pm, sm.nm), pcl + (inl ? 0 : 1));
-                        uint64_t *d = a.child.sum + (size_t)myidx * 4;
-                        *reinterpret_cast<ulonglong2 *>(d) = make_ulonglong2(sm.rh, sm.pm);
-                        *reinterpret_cast<ulonglong2 *>(d + 2) = make_ulonglong2(sm.nm, sm.um);
-                        a.child.pmax[myidx] = sm.pmax;
+                        put_summary(a.child.sum + (size_t)myidx * kSumWords, sm);
                     } else {
                         ++n_unwritten;
                     }
@@ -1956,195 +1969,56 @@ __device__ void generate_narrow(const NetView &nv, const LevelArgs &a, const uin
                     }
                 }
             }
-            // === phase B: lane groups take the ready and slow children NG at
-            // a time: the extra-flux row t = A p + C s, coalesced ===
-            const uint32_t infol = (uint32_t)kl | ((uint32_t)pcl << 12) | (inl ? 1u << 19 : 0u) |
-                                   (slowl ? 1u << 20 : 0u) | (fast ? 1u << 21 : 0u);
+            // === phase B: lane groups write the extra-flux rows of the ready
+            // children NG at a time (t = A p + C s in 32 bits, coalesced) ===
+            const uint32_t infol = (uint32_t)kl | ((uint32_t)pcl << 12) | (inl ? 1u << 19 : 0u) | (fast ? 1u << 20 : 0u);
             const uint32_t pl32 = (uint32_t)pl_;
-            unsigned vmask = __ballot_sync(FULL, ready || slowl);
+            unsigned vmask = __ballot_sync(FULL, ready);
             while (vmask) {
-                if (__any_sync(FULL, fatal)) break;
                 const int src = gi < __popc(vmask) ? (int)__fns(vmask, 0, gi + 1) : -1;
 #pragma unroll
                 for (int t = 0; t < NG; ++t) vmask &= vmask - 1;
                 const int sl = src < 0 ? 0 : src;
-                const bool ok = src >= 0;
                 const uint32_t info_i = __shfl_sync(FULL, infol, sl);
                 const int k = (int)(info_i & 0xFFFu);
-                const int pc = (int)((info_i >> 12) & 0x7Fu);
-                const bool in_u = (info_i >> 19) & 1u;
-                const bool slow = ok && ((info_i >> 20) & 1u);
-                const bool fst = (info_i >> 21) & 1u;
                 const int32_t A = __shfl_sync(FULL, Al, sl);
                 const int32_t C = __shfl_sync(FULL, Cl, sl);
                 const int64_t p = (int64_t)__shfl_sync(FULL, pl32, sl);
                 const uint64_t ridx = __shfl_sync(FULL, myidx, sl);
-                const int4 *prow4 = reinterpret_cast<const int4 *>(a.par.B + (size_t)p * Mpad);
-                const int4 *col4 = dcol + (size_t)k * (Mpad >> 2);
-                int32_t t32[EPL];
-                bool big = false;
-                if (ok && fst) {
-#pragma unroll
-                    for (int i = 0; i < CPL; ++i) {
-                        const int4 v = prow4[gl + G * i];
-                        const int4 w = col4[gl + G * i];
-                        t32[4 * i + 0] = A * v.x + C * w.x;
-                        t32[4 * i + 1] = A * v.y + C * w.y;
-                        t32[4 * i + 2] = A * v.z + C * w.z;
-                        t32[4 * i + 3] = A * v.w + C * w.w;
-                    }
-                } else if (ok) {
-#pragma unroll
-                    for (int i = 0; i < CPL; ++i) {
-                        const int4 v = prow4[gl + G * i];
-                        const int4 w = col4[gl + G * i];
-                        const int32_t pv[4] = {v.x, v.y, v.z, v.w}, cv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                        for (int jj = 0; jj < 4; ++jj) {
-                            const int64_t tt = (int64_t)A * pv[jj] + (int64_t)C * cv[jj];
-                            const int32_t lo = (int32_t)tt;
-                            big = big || tt != (int64_t)lo || lo == INT32_MIN;
-                            t32[4 * i + jj] = lo;
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < EPL; ++e) t32[e] = 0;
-                }
-                if (__any_sync(FULL, slow)) {
-                    // a slow child: exact gcd and int32 range over the whole row,
-                    // then the superset rule, and its row's summaries
-                    uint64_t gg = 0, amax = 0;
-                    if (slow && !big) {
-#pragma unroll
-                        for (int e = 0; e < EPL; ++e) {
-                            const uint32_t at = (uint32_t)(t32[e] < 0 ? -t32[e] : t32[e]);
-                            if (at != 0) gg = gg == 0 ? at : gcd32((uint32_t)gg, at);
-                            amax = at > amax ? at : amax;
-                        }
-                    } else if (slow) {
-                        const GcdMax gmx = raw_gcd_max(prow4, col4, gl, G, CPL, A, C);
-                        gg = gmx.g;
-                        amax = gmx.m;
-                    }
-#pragma unroll
-                    for (int off = G / 2; off > 0; off >>= 1) {
-                        const uint64_t og = __shfl_xor_sync(FULL, gg, off);
-                        gg = og == 0 ? gg : (gg == 0 ? og : gcd64(gg, og));
-                        const uint64_t y = __shfl_xor_sync(FULL, amax, off);
-                        amax = y > amax ? y : amax;
-                    }
-                    if (gg == 0) gg = 1;
-                    const bool ovf = slow && amax / gg > 2147483647ull;
-                    if (slow && !ovf && gg > 1) {
-                        if (!big) {
-#pragma unroll
-                            for (int e = 0; e < EPL; ++e) t32[e] = t32[e] / (int32_t)gg;
-                        } else {
-#pragma unroll
-                            for (int i = 0; i < CPL; ++i) {
-                                const int4 v = prow4[gl + G * i];
-                                const int4 w = col4[gl + G * i];
-                                const int32_t pv[4] = {v.x, v.y, v.z, v.w}, cv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                                for (int jj = 0; jj < 4; ++jj) {
-                                    const int64_t tt = (int64_t)A * pv[jj] + (int64_t)C * cv[jj];
-                                    t32[4 * i + jj] = (int32_t)(tt / (int64_t)gg);
-                                }
-                            }
-                        }
-                    }
-                    if (ovf && gl == 0) ++n_ovf;
-                    const uint64_t *pu = a.par.U + (size_t)p * W;
-                    bool pr = false;
-                    const bool cand = slow && !ovf;
-                    if (cand && !in_u) {
-                        const int64_t b1 = a.bptr[k];
-                        const int64_t n = a.bptr[k + 1] - b1;
-                        if (W <= 2) {
-                            const uint64_t u0 = child_word(pu, 0, k), u1 = W == 2 ? child_word(pu, 1, k) : 0ull;
-                            bool maybe = n > 0;
-                            if (maybe && a.band) {
-                                const uint64_t i0 = __ldg(a.band + (size_t)k * W), i1 = W == 2 ? __ldg(a.band + (size_t)k * W + 1) : 0ull;
-                                maybe = ((i0 & ~u0) | (i1 & ~u1)) == 0;
-                            }
-                            for (int64_t i = gl; i < n && !pr && maybe; i += G) {
-                                const uint64_t *E = a.bres + (size_t)(b1 + i) * W;
-                                const uint64_t e0 = __ldg(E), e1 = W == 2 ? __ldg(E + 1) : 0ull;
-                                pr = ((e0 & ~u0) | (e1 & ~u1)) == 0;
-                            }
-                        } else {
-                            for (int64_t i = gl; i < n && !pr; i += G) pr = result_inside_wide(a, pu, k, b1 + i);
-                        }
-                    }
-                    pr = group_or<G>(pr ? 1u : 0u) != 0;
-                    if (pr && gl == 0) ++n_pruned;
-                    const bool keep = cand && !pr;
-                    // summaries of the settled row: signs from phase A (a
-                    // positive scale keeps them), the rest over the row
-                    uint64_t um = 0, rh = 0;
-                    if (keep) {
-#pragma unroll
-                        for (int i = 0; i < CPL; ++i)
-#pragma unroll
-                            for (int jj = 0; jj < 4; ++jj) {
-                                const int m = 4 * (gl + G * i) + jj;
-                                const int32_t v = t32[4 * i + jj];
-                                if (m < nv.M && v != 0) {
-                                    if (v == 1 || v == -1) um |= 1ull << m;
-                                    rh += (uint64_t)(int64_t)v * blob_u64(bl, nv.o_hrow + 2 * m);
-                                }
-                            }
-                    }
-#pragma unroll
-                    for (int off = G / 2; off > 0; off >>= 1) {
-                        um |= __shfl_xor_sync(FULL, um, off);
-                        rh += __shfl_xor_sync(FULL, rh, off);
-                    }
-                    // the slow child's lane (sl) holds its phase-A sign masks
-                    const uint64_t spm = __shfl_sync(FULL, sm.pm, sl);
-                    const uint64_t snm = __shfl_sync(FULL, sm.nm, sl);
-                    const unsigned km = __ballot_sync(FULL, keep && gl == 0);
-                    if (km) {
-                        const uint64_t idx = reserve(__popc(km), __popc(km & ((1u << lead) - 1u)));
-                        if (keep) {
-                            if ((int64_t)idx < row_cap) {
-                                int4 *db = reinterpret_cast<int4 *>(a.child.B + (size_t)idx * Mpad);
-#pragma unroll
-                                for (int i = 0; i < CPL; ++i)
-                                    db[gl + G * i] = make_int4(t32[4 * i + 0], t32[4 * i + 1], t32[4 * i + 2], t32[4 * i + 3]);
-                                uint64_t *du = a.child.U + (size_t)idx * W;
-                                for (int w = gl; w < W; w += G) du[w] = child_word(pu, w, k);
-                                if (gl == 0) {
-                                    a.child.meta[idx] = pack_meta(mask_key(bl, nv, spm, snm), pc + (in_u ? 0 : 1));
-                                    uint64_t *d = a.child.sum + (size_t)idx * 4;
-                                    *reinterpret_cast<ulonglong2 *>(d) = make_ulonglong2(rh, spm);
-                                    *reinterpret_cast<ulonglong2 *>(d + 2) = make_ulonglong2(snm, um);
-                                    a.child.pmax[idx] = (uint32_t)(amax / gg);
-                                }
-                            } else if (gl == 0) {
-                                ++n_unwritten;
-                            }
-                            if (gl == 0) {
-                                if ((int64_t)idx < a.fp_cap) {
-                                    uint64_t f = rh ^ mix64(support_hash(pu, W, k) + 0x632BE59BD9B4E019ull);
-                                    if (f == kDeadFp) f = kDeadFp - 1;
-                                    a.fp[idx] = f;
-                                } else {
-                                    record_diag(a.ctr, ERR_BOUNDS, 7, (long long)idx, a.fp_cap, a.level);
-                                    fatal = true;
-                                }
-                            }
-                        }
-                    }
-                    fatal = group_or<G>(fatal ? 1u : 0u) != 0;
-                }
-                // a ready child: its row (phase A wrote the rest)
-                if (ok && !slow && (int64_t)ridx < row_cap) {
+                if (src >= 0 && (int64_t)ridx < row_cap) {
+                    const int4 *prow4 = reinterpret_cast<const int4 *>(a.par.B + (size_t)p * Mpad);
+                    const int4 *col4 = dcol + (size_t)k * (Mpad >> 2);
                     int4 *db = reinterpret_cast<int4 *>(a.child.B + (size_t)ridx * Mpad);
 #pragma unroll
-                    for (int i = 0; i < CPL; ++i)
-                        db[gl + G * i] = make_int4(t32[4 * i + 0], t32[4 * i + 1], t32[4 * i + 2], t32[4 * i + 3]);
+                    for (int i = 0; i < CPL; ++i) {
+                        const int4 v = prow4[gl + G * i];
+                        const int4 w = col4[gl + G * i];
+                        db[gl + G * i] = make_int4(A * v.x + C * w.x, A * v.y + C * w.y, A * v.z + C * w.z, A * v.w + C * w.w);
+                    }
+                }
+            }
+            // === the slow children (no gcd certificate or a possible overflow)
+            // go to the settle pass as records ===
+            const unsigned smask = __ballot_sync(FULL, slowl);
+            if (smask) {
+                unsigned long long sbase = 0;
+                if (lane == 0) sbase = atomicAdd(&a.ctr[C_SLOW], (unsigned long long)__popc(smask));
+                sbase = __shfl_sync(FULL, sbase, 0);
+                if (slowl) {
+                    const uint64_t si = sbase + (uint64_t)__popc(smask & ((1u << lane) - 1u));
+                    if ((int64_t)si < a.slow_cap) {
+                        uint64_t *r = a.slow + (size_t)si * kSlowWords;
+                        const uint64_t w0 = (uint64_t)pl32 | ((uint64_t)kl << 32) | ((uint64_t)pcl << 44) |
+                                            (inl ? 1ull << 51 : 0ull) | (fast ? 1ull << 52 : 0ull);
+                        const uint64_t w1 = (uint64_t)(uint32_t)Al | ((uint64_t)(uint32_t)Cl << 32);
+                        *reinterpret_cast<ulonglong2 *>(r) = make_ulonglong2(w0, w1);
+                        *reinterpret_cast<ulonglong2 *>(r + 2) = make_ulonglong2(sm.rh, sm.pm);
+                        *reinterpret_cast<ulonglong2 *>(r + 4) = make_ulonglong2(sm.nm, sm.um);
+                        *reinterpret_cast<ulonglong2 *>(r + 6) = make_ulonglong2(sm.om, 0ull);
+                    } else {
+                        record_diag(a.ctr, ERR_BOUNDS, 9, (long long)si, a.slow_cap, a.level);
+                        fatal = true;
+                    }
                 }
             }
         }
@@ -2168,6 +2042,275 @@ __global__ void __launch_bounds__(kExpandWarps * 32, 3) generate_narrow_kernel(N
     const uint32_t *bl = stage_blob(nv, smem, mbar, staged != 0, a.ctr);
     if (bl == nullptr) return;
     generate_narrow<G>(nv, a, bl, (int64_t)blockIdx.x * kExpandWarps + wid, (int64_t)gridDim.x * kExpandWarps);
+}
+
+// ---------------------------------------------------------------------------
+// Settle pass (narrow networks): the children whose gcd the summaries do not
+// certify, or whose update may leave int32, listed by the generate pass as
+// records (parent, column, |U|, flags, A, C and their phase-A summaries).
+// A group of G lanes per record: the row in 32 or 64 bits, the exact gcd and
+// int32 range over the whole row (the overflow rule comes before the
+// superset rule, as in the definition), the superset rule, then a reserved
+// row.  Keeping this rare, long path out of the generate kernel keeps that
+// kernel's instruction footprint small.
+// ---------------------------------------------------------------------------
+template <int G>
+__global__ void __launch_bounds__(kExpandWarps * 32) settle_kernel(NetView nv, LevelArgs a)
+{
+    constexpr int CPL = 2;
+    constexpr int NG = 32 / G;
+    constexpr int EPL = 4 * CPL;
+    const int lane = threadIdx.x & 31;
+    const int gi = lane / G;
+    const int gl = lane % G;
+    const int lead = gi * G;
+    const int W = nv.W;
+    const int Mpad = nv.Mpad;
+    const uint32_t *bl = nv.blob;
+    const int4 *dcol = reinterpret_cast<const int4 *>(bl + nv.o_dcols);
+    const int64_t row_cap = a.child.cap;
+    int64_t n_slow = (int64_t)a.ctr[C_SLOW];
+    n_slow = n_slow < a.slow_cap ? n_slow : a.slow_cap;
+    unsigned long long n_ovf = 0, n_pruned = 0, n_unwritten = 0;
+    bool fatal = false;
+    uint64_t pool_next = 0;
+    int pool_left = 0;
+    auto reserve = [&](int cnt, int rank) -> uint64_t {
+        uint64_t fresh = 0;
+        if (pool_left < cnt) {
+            const int want = cnt;  // exactly what the round needs: no unused rows
+            if (lane == 0) fresh = atomicAdd(&a.ctr[C_WRITTEN], (unsigned long long)want);
+            fresh = __shfl_sync(FULL, fresh, 0);
+            const uint64_t idx = rank < pool_left ? pool_next + (uint64_t)rank : fresh + (uint64_t)(rank - pool_left);
+            pool_next = fresh + (uint64_t)(cnt - pool_left);
+            pool_left = want - (cnt - pool_left);
+            return idx;
+        }
+        const uint64_t idx = pool_next + (uint64_t)rank;
+        pool_next += (uint64_t)cnt;
+        pool_left -= cnt;
+        return idx;
+    };
+    const int64_t wid = (int64_t)blockIdx.x * kExpandWarps + (threadIdx.x >> 5);
+    const int64_t wstride = (int64_t)gridDim.x * kExpandWarps * NG;
+    for (int64_t base = wid * NG; base < n_slow; base += wstride) {
+        if (__any_sync(FULL, fatal)) break;
+            const int64_t r = base + gi;
+            const bool slow = r < n_slow;
+            // the record (every lane of the group reads it)
+            uint64_t w0 = 0, w1 = 0, srh = 0, spm = 0, snm = 0, sum_ = 0, som = 0;
+            if (slow) {
+                const uint64_t *rec = a.slow + (size_t)r * kSlowWords;
+                const ulonglong2 q0 = *reinterpret_cast<const ulonglong2 *>(rec);
+                const ulonglong2 q1 = *reinterpret_cast<const ulonglong2 *>(rec + 2);
+                const ulonglong2 q2 = *reinterpret_cast<const ulonglong2 *>(rec + 4);
+                const ulonglong2 q3 = *reinterpret_cast<const ulonglong2 *>(rec + 6);
+                w0 = q0.x;
+                w1 = q0.y;
+                srh = q1.x;
+                spm = q1.y;
+                snm = q2.x;
+                sum_ = q2.y;
+                som = q3.x;
+            }
+            const int64_t p = (int64_t)(uint32_t)w0;
+            const int k = (int)((w0 >> 32) & 0xFFFu);
+            const int pc = (int)((w0 >> 44) & 0x7Fu);
+            const bool in_u = (w0 >> 51) & 1ull;
+            const bool fst = (w0 >> 52) & 1ull;  // the update fits 32 bits
+            const int32_t A = (int32_t)(uint32_t)w1;
+            const int32_t C = (int32_t)(uint32_t)(w1 >> 32);
+                const int4 *prow4 = reinterpret_cast<const int4 *>(a.par.B + (size_t)p * Mpad);
+                const int4 *col4 = dcol + (size_t)k * (Mpad >> 2);
+                int32_t t32[EPL];
+                bool big = false;
+                uint64_t gg = 0, amax = 0;
+                if (slow && fst) {
+                    uint32_t g32 = 0, m32 = 0;
+#pragma unroll
+                    for (int i = 0; i < CPL; ++i) {
+                        const int4 v = prow4[gl + G * i];
+                        const int4 w = col4[gl + G * i];
+                        t32[4 * i + 0] = A * v.x + C * w.x;
+                        t32[4 * i + 1] = A * v.y + C * w.y;
+                        t32[4 * i + 2] = A * v.z + C * w.z;
+                        t32[4 * i + 3] = A * v.w + C * w.w;
+                    }
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) {
+                        const uint32_t at = (uint32_t)(t32[e] < 0 ? -t32[e] : t32[e]);
+                        if (at != 0 && g32 != 1) g32 = g32 == 0 ? at : gcd32(g32, at);
+                        m32 = at > m32 ? at : m32;
+                    }
+                    gg = g32;
+                    amax = m32;
+                } else if (slow) {
+#pragma unroll
+                    for (int i = 0; i < CPL; ++i) {
+                        const int4 v = prow4[gl + G * i];
+                        const int4 w = col4[gl + G * i];
+                        const int32_t pv[4] = {v.x, v.y, v.z, v.w}, cv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) {
+                            const int64_t tt = (int64_t)A * pv[jj] + (int64_t)C * cv[jj];
+                            const int32_t lo = (int32_t)tt;
+                            big = big || tt != (int64_t)lo || lo == INT32_MIN;
+                            t32[4 * i + jj] = lo;
+                        }
+                    }
+                    if (!big) {
+#pragma unroll
+                        for (int e = 0; e < EPL; ++e) {
+                            const uint32_t at = (uint32_t)(t32[e] < 0 ? -t32[e] : t32[e]);
+                            if (at != 0 && gg != 1) gg = gg == 0 ? at : gcd32((uint32_t)gg, at);
+                            amax = at > amax ? at : amax;
+                        }
+                    } else {
+                        const GcdMax gmx = raw_gcd_max(prow4, col4, gl, G, CPL, A, C);
+                        gg = gmx.g;
+                        amax = gmx.m;
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) t32[e] = 0;
+                }
+                big = group_or<G>(big ? 1u : 0u) != 0;
+                if (!__any_sync(FULL, big)) {
+                    // every entry of every slow row of the round fits 32 bits
+                    uint32_t g32 = (uint32_t)gg, m32 = (uint32_t)amax;
+#pragma unroll
+                    for (int off = G / 2; off > 0; off >>= 1) {
+                        const uint32_t og = __shfl_xor_sync(FULL, g32, off);
+                        g32 = (og == 0 || g32 == 1) ? g32 : (g32 == 0 ? og : gcd32(g32, og));
+                        const uint32_t y = __shfl_xor_sync(FULL, m32, off);
+                        m32 = y > m32 ? y : m32;
+                    }
+                    gg = g32;
+                    amax = m32;
+                } else {
+#pragma unroll
+                    for (int off = G / 2; off > 0; off >>= 1) {
+                        const uint64_t og = __shfl_xor_sync(FULL, gg, off);
+                        gg = og == 0 ? gg : (gg == 0 ? og : gcd64(gg, og));
+                        const uint64_t y = __shfl_xor_sync(FULL, amax, off);
+                        amax = y > amax ? y : amax;
+                    }
+                }
+                if (gg == 0) gg = 1;
+                const bool ovf = slow && amax / gg > 2147483647ull;
+                if (slow && !ovf && gg > 1) {
+                    if (!big) {
+#pragma unroll
+                        for (int e = 0; e < EPL; ++e) t32[e] = t32[e] / (int32_t)gg;
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < CPL; ++i) {
+                            const int4 v = prow4[gl + G * i];
+                            const int4 w = col4[gl + G * i];
+                            const int32_t pv[4] = {v.x, v.y, v.z, v.w}, cv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                            for (int jj = 0; jj < 4; ++jj) {
+                                const int64_t tt = (int64_t)A * pv[jj] + (int64_t)C * cv[jj];
+                                t32[4 * i + jj] = (int32_t)(tt / (int64_t)gg);
+                            }
+                        }
+                    }
+                }
+                if (ovf && gl == 0) ++n_ovf;
+                const uint64_t *pu = a.par.U + (size_t)p * W;
+                bool pr = false;
+                const bool cand = slow && !ovf;
+                if (cand && !in_u) {
+                    const int64_t b1 = a.bptr[k];
+                    const int64_t n = a.bptr[k + 1] - b1;
+                    if (W <= 2) {
+                        const uint64_t u0 = child_word(pu, 0, k), u1 = W == 2 ? child_word(pu, 1, k) : 0ull;
+                        bool maybe = n > 0;
+                        if (maybe && a.band) {
+                            const uint64_t i0 = __ldg(a.band + (size_t)k * W), i1 = W == 2 ? __ldg(a.band + (size_t)k * W + 1) : 0ull;
+                            maybe = ((i0 & ~u0) | (i1 & ~u1)) == 0;
+                        }
+                        for (int64_t i = gl; i < n && !pr && maybe; i += G) {
+                            const uint64_t *E = a.bres + (size_t)(b1 + i) * W;
+                            const uint64_t e0 = __ldg(E), e1 = W == 2 ? __ldg(E + 1) : 0ull;
+                            pr = ((e0 & ~u0) | (e1 & ~u1)) == 0;
+                        }
+                    } else {
+                        for (int64_t i = gl; i < n && !pr; i += G) pr = result_inside_wide(a, pu, k, b1 + i);
+                    }
+                }
+                pr = group_or<G>(pr ? 1u : 0u) != 0;
+                if (pr && gl == 0) ++n_pruned;
+                const bool keep = cand && !pr;
+                // a row divided by its gcd: +-1 rows and hash over the row (the
+                // signs do not change); otherwise phase A's values stand
+                uint64_t um = sum_, om = som, rh = srh;
+                if (__any_sync(FULL, keep && gg > 1)) {
+                    uint64_t u2 = 0, o2 = 0, h2 = 0;
+                    if (keep && gg > 1) {
+#pragma unroll
+                        for (int i = 0; i < CPL; ++i)
+#pragma unroll
+                            for (int jj = 0; jj < 4; ++jj) {
+                                const int m = 4 * (gl + G * i) + jj;
+                                const int32_t v = t32[4 * i + jj];
+                                if (m < nv.M && v != 0) {
+                                    if (v == 1 || v == -1) u2 |= 1ull << m;
+                                    if (v & 1) o2 |= 1ull << m;
+                                    h2 += (uint64_t)(int64_t)v * blob_u64(bl, nv.o_hrow + 2 * m);
+                                }
+                            }
+                    }
+#pragma unroll
+                    for (int off = G / 2; off > 0; off >>= 1) {
+                        u2 |= __shfl_xor_sync(FULL, u2, off);
+                        o2 |= __shfl_xor_sync(FULL, o2, off);
+                        h2 += __shfl_xor_sync(FULL, h2, off);
+                    }
+                    if (keep && gg > 1) {
+                        um = u2;
+                        om = o2;
+                        rh = h2;
+                    }
+                }
+                const unsigned km = __ballot_sync(FULL, keep && gl == 0);
+                if (km) {
+                    const uint64_t idx = reserve(__popc(km), __popc(km & ((1u << lead) - 1u)));
+                    if (keep) {
+                        if ((int64_t)idx < row_cap) {
+                            int4 *db = reinterpret_cast<int4 *>(a.child.B + (size_t)idx * Mpad);
+#pragma unroll
+                            for (int i = 0; i < CPL; ++i)
+                                db[gl + G * i] = make_int4(t32[4 * i + 0], t32[4 * i + 1], t32[4 * i + 2], t32[4 * i + 3]);
+                            uint64_t *du = a.child.U + (size_t)idx * W;
+                            for (int w = gl; w < W; w += G) du[w] = child_word(pu, w, k);
+                            if (gl == 0) {
+                                a.child.meta[idx] = pack_meta(mask_key(bl, nv, spm, snm), pc + (in_u ? 0 : 1));
+                                put_summary(a.child.sum + (size_t)idx * kSumWords,
+                                            NarrowSum{rh, spm, snm, um, om, (uint32_t)(amax / gg)});
+                            }
+                        } else if (gl == 0) {
+                            ++n_unwritten;
+                        }
+                        if (gl == 0) {
+                            if ((int64_t)idx < a.fp_cap) {
+                                uint64_t f = rh ^ mix64(support_hash(pu, W, k) + 0x632BE59BD9B4E019ull);
+                                if (f == kDeadFp) f = kDeadFp - 1;
+                                a.fp[idx] = f;
+                            } else {
+                                record_diag(a.ctr, ERR_BOUNDS, 7, (long long)idx, a.fp_cap, a.level);
+                                fatal = true;
+                            }
+                        }
+                    }
+                }
+                fatal = group_or<G>(fatal ? 1u : 0u) != 0;
+    }
+    for (int x = lane; x < pool_left; x += 32)
+        if ((int64_t)(pool_next + x) < a.fp_cap) a.fp[pool_next + x] = kDeadFp;
+    if (n_ovf) atomicAdd(&a.ctr[C_OVF], n_ovf);
+    if (n_pruned) atomicAdd(&a.ctr[C_PRUNED], n_pruned);
+    if (n_unwritten) atomicAdd(&a.ctr[C_UNWRITTEN], n_unwritten);
 }
 
 // Are reserved rows i and j the same state (support and extra-flux row)?
@@ -2985,6 +3128,16 @@ int generate_grid(const NetView &nv, int sm_count)
     EFM_GROUP_DISPATCH(nv.EPL, CALL_GGRID)
 #undef CALL_GGRID
     return sm_count;
+}
+
+cudaError_t launch_settle(const NetView &nv, const LevelArgs &a, int sm_count, cudaStream_t s)
+{
+    if (!(nv.narrow && a.par.sum && a.child.sum && a.slow)) return cudaSuccess;
+    if (nv.EPL == 1)
+        settle_kernel<4><<<sm_count * 4, kExpandWarps * 32, 0, s>>>(nv, a);
+    else if (nv.EPL == 2)
+        settle_kernel<8><<<sm_count * 4, kExpandWarps * 32, 0, s>>>(nv, a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_dedup(const LevelArgs &a, int Mpad, int W, int sm_count, cudaStream_t s)

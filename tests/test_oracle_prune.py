@@ -111,3 +111,21 @@ def test_extreme_coefficients_agree_with_unbounded_integers(oracle_lib):
             assert ctr == rctr, (trial, t)
             checked += ctr["overflow"]
     assert checked > 0  # the int32 rule is exercised
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_budgeted_levels_match_the_python_reference(oracle_lib, seed):
+    """Small frontier budgets make the C oracle compact (deduplicate) a
+    level's children before the level ends and stop storing them once the
+    budget is exceeded; results and every counter still equal the pure-Python
+    restatement, which never does either."""
+    from oracle import reference
+
+    net = synth.tiny(seed)
+    for t in list(net.targets) + [-1]:
+        for budget in (3, 7, 20, 60):
+            sup, ctr = oracle_lib.enumerate_pathways(net, t, oracle_lib.Limits(10, 2, 0, budget))
+            res, rctr = reference.enumerate_reference(net, t, 10, 2, max_frontier=budget)
+            got = [tuple(k for k in range(64) if (U >> k) & 1) for U in res]
+            assert got == oracle_lib.supports_to_lists(sup), (seed, t, budget)
+            assert ctr == rctr, (seed, t, budget)
