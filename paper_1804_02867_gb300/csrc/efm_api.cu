@@ -536,7 +536,6 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
     else
         CK(launch_seed(nv, a, target, s));
     out.kernel_launches += 1;
-    const uint32_t *par_map = nullptr;  // frontier position -> arena row (null: identity)
     AcceptArgs acc{};
     acc.cand = (const uint64_t *)w.cand.p;
     acc.res = (uint64_t *)w.res.p;
@@ -574,7 +573,8 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
         top.add(fresh.data(), res_n);
         if (top.pc > 0) CK(cudaMemcpyAsync(w.fkb.p, top.kth.data(), (size_t)nv.W * 8, cudaMemcpyHostToDevice, s));
     }
-    int64_t n_front = (int64_t)h[C_NEXT];
+    int64_t n_front = (int64_t)h[C_NEXT];  // distinct states of the level
+    int64_t n_rows = n_front;              // arena rows the next level reads (seeds are dense)
     uint64_t deg_sum = h[C_DEGSUM];
     int status = 0;
     c.levels = 1;
@@ -615,28 +615,38 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
             buckets_built_for = res_n;
         }
         if (trace && n_front > 0) {
-            // training rows: a strided sample of this frontier (level - 1)
-            const int64_t stride = std::max<int64_t>(1, (n_front + trace->rows_per_level - 1) / trace->rows_per_level);
-            const int64_t cnt = (n_front + stride - 1) / stride;
+            // training rows: a strided sample of this frontier (level - 1),
+            // through the list of its surviving rows
+            unsigned long long n_live = 0;
+            CK(cudaMemsetAsync(ctr + C_LIVE, 0, 8, s));
+            CK(launch_live_list((const uint32_t *)w.meta[cur].p, n_rows, (uint32_t *)w.live[cur].p, ctr + C_LIVE,
+                                net->sm_count, s));
+            CK(cudaMemcpyAsync(&n_live, ctr + C_LIVE, 8, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            const int64_t nl = (int64_t)n_live;
+            const int64_t stride = std::max<int64_t>(1, (nl + trace->rows_per_level - 1) / trace->rows_per_level);
+            const int64_t cnt = (nl + stride - 1) / stride;
             efm_model *m = trace->m;
             if (!model_reserve_rows(m, m->n_rows + cnt)) return EFM_ENOMEM;
             if ((rc = ensure_dep_tags(net))) return rc;
-            CK(launch_features(nv, arena(cur), par_map, 0, stride, cnt, level - 1, lim.max_len, lim.max_secondary,
+            const uint32_t *live = (const uint32_t *)w.live[cur].p;
+            CK(launch_features(nv, arena(cur), live, 0, stride, cnt, level - 1, lim.max_len, lim.max_secondary,
                                (const uint64_t *)net->dep.p, m->X.p, m->n_rows, s));
-            CK(launch_labels((const uint64_t *)w.U[cur].p, nv.W, par_map, 0, stride, cnt, trace->ans, trace->n_ans,
+            CK(launch_labels((const uint64_t *)w.U[cur].p, nv.W, live, 0, stride, cnt, trace->ans, trace->n_ans,
                              (float *)m->y.p, m->n_rows, s));
             m->n_rows += cnt;
         }
         // first-K: the level's parents in proposal order (positions -> arena
         // rows), expanded in chunks with the bound refreshed between them
-        int64_t chunk = n_front;
-        const uint32_t *order = par_map;
+        // (rows of later copies have no branches: they cost a meta read)
+        int64_t chunk = n_rows;
+        const uint32_t *order = nullptr;
         if (fk) {
-            chunk = std::max<int64_t>(kFirstKChunkMin, (n_front + kFirstKChunks - 1) / kFirstKChunks);
-            if (model && lim.proposal == EFM_LEARNED && n_front > chunk) {
+            chunk = std::max<int64_t>(kFirstKChunkMin, (n_rows + kFirstKChunks - 1) / kFirstKChunks);
+            if (model && lim.proposal == EFM_LEARNED && n_rows > chunk) {
                 // the model's order: features of every parent, scores, and a
                 // counting sort by score (highest first)
-                const int64_t rows = (n_front + kMlpTileRows - 1) / kMlpTileRows * kMlpTileRows;
+                const int64_t rows = (n_rows + kMlpTileRows - 1) / kMlpTileRows * kMlpTileRows;
                 if (rows > w.lx_rows) {
                     dev_free(w.lx, s);
                     dev_free(w.lscore, s);
@@ -645,9 +655,9 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
                         return EFM_ENOMEM;
                     w.lx_rows = cap;
                 }
-                if (n_front > w.perm_cap) {
+                if (n_rows > w.perm_cap) {
                     dev_free(w.perm, s);
-                    const int64_t cap = std::max<int64_t>(n_front, 2 * w.perm_cap);
+                    const int64_t cap = std::max<int64_t>(n_rows, 2 * w.perm_cap);
                     if (!dev_alloc(w.perm, (size_t)cap * 4, s)) return EFM_ENOMEM;
                     w.perm_cap = cap;
                 }
@@ -656,45 +666,37 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
                     CK(cudaMemsetAsync(w.lerr.p, 0, 4, s));
                 }
                 if ((rc = ensure_dep_tags(net))) return rc;
-                CK(launch_features(nv, arena(cur), par_map, 0, 1, n_front, level - 1, lim.max_len, lim.max_secondary,
+                CK(launch_features(nv, arena(cur), nullptr, 0, 1, n_rows, level - 1, lim.max_len, lim.max_secondary,
                                    (const uint64_t *)net->dep.p, w.lx.p, 0, s));
-                CK(launch_mlp_score(w.lx.p, n_front, model->wb.p, (const float *)model->params.p,
+                CK(launch_mlp_score(w.lx.p, n_rows, model->wb.p, (const float *)model->params.p,
                                     (float *)w.lscore.p, (unsigned *)w.lerr.p, s));
-                CK(launch_score_order((const float *)w.lscore.p, n_front, par_map, (unsigned *)w.lhist.p,
+                CK(launch_score_order((const float *)w.lscore.p, n_rows, nullptr, (unsigned *)w.lhist.p,
                                       (uint32_t *)w.perm.p, s));
                 order = (const uint32_t *)w.perm.p;
                 out.kernel_launches += 6;
-            } else if (!order && chunk < n_front) {
-                if (n_front > w.perm_cap) {
-                    dev_free(w.perm, s);
-                    const int64_t cap = std::max<int64_t>(n_front, 2 * w.perm_cap);
-                    if (!dev_alloc(w.perm, (size_t)cap * 4, s)) return EFM_ENOMEM;
-                    w.perm_cap = cap;
-                }
-                CK(launch_iota((uint32_t *)w.perm.p, n_front, s));
-                order = (const uint32_t *)w.perm.p;
-                out.kernel_launches += 1;
             }
         }
         // rows one warp reserves at a time: few for small or chunked levels
         // (a warp's unused reserved rows at the end of every launch are dead
         // weight in the arena), 32 for large ones
-        const int64_t launches = (n_front + chunk - 1) / chunk;
+        const int64_t launches = (n_rows + chunk - 1) / chunk;
         const int blk = launches > 1 ? NG
                                      : (int)std::min<uint64_t>(32, std::max<uint64_t>((uint64_t)NG,
                                                                                      deg_sum / (64ull * total_warps)));
         const uint64_t reserved = deg_sum + (uint64_t)launches * blk * total_warps + 64;
         if (!ensure_level_tables(w, reserved, s)) return EFM_ENOMEM;
         // narrow networks: room for every child of a launch in the settle list
-        if (nv.narrow && (int64_t)deg_sum + 64 > w.slow_cap) {
+        const int64_t slow_need = (int64_t)deg_sum + 32 * (int64_t)total_warps + 64;  // + unused pool slots
+        if (nv.narrow && slow_need > w.slow_cap) {
             dev_free(w.slow, s);
-            const int64_t cap = std::max<int64_t>((int64_t)deg_sum + 64, w.slow_cap + w.slow_cap / 2);
+            const int64_t cap = std::max<int64_t>(slow_need, w.slow_cap + w.slow_cap / 2);
             if (!dev_alloc(w.slow, (size_t)cap * kSlowWords * 8, s)) return EFM_ENOMEM;
             w.slow_cap = cap;
         }
         const uint64_t nslots = next_pow2(2 * reserved + 64);
         unsigned long long snap[C_COUNT];
         memcpy(snap, h, sizeof(h));
+        const int64_t n_front_level = n_front;  // distinct parents of this level
         // the level, run again with a larger child arena if some children
         // found no row and the fingerprints alone cannot show a truncation
         for (int attempt = 0;; ++attempt) {
@@ -716,10 +718,11 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
             a.level = level;
             unsigned long long exp_before = h[C_EXP];
             uint64_t next_before = 0;
-            for (int64_t c0 = 0; c0 < n_front; c0 += chunk) {
-                const int64_t cn = std::min<int64_t>(chunk, n_front - c0);
+            for (int64_t c0 = 0; c0 < n_rows; c0 += chunk) {
+                const int64_t cn = std::min<int64_t>(chunk, n_rows - c0);
                 a.n_par = cn;
                 a.perm = order ? order + c0 : nullptr;
+                a.par_base = order ? 0 : c0;
                 a.cpw = (int)std::min<int64_t>(32, std::max<int64_t>(1, (cn + total_warps - 1) / total_warps));
                 a.fk_pc = fk ? top.pc : 0;
                 a.fk_sup = (const uint64_t *)w.fkb.p;
@@ -748,12 +751,15 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
                     const uint64_t next_now = h[C_NEXT];
                     const double n_new = (double)(next_now - next_before);
                     const double n_child = (double)(h[C_EXP] - exp_before);
-                    out.expand_bytes += state_bytes * ((double)cn + n_new) + 16.0 * n_child;
+                    // distinct parents of the chunk (its rows include later copies
+                    // and unused rows, which carry no state)
+                    const double n_par = (double)cn * (double)n_front_level / (double)std::max<int64_t>(n_rows, 1);
+                    out.expand_bytes += state_bytes * (n_par + n_new) + 16.0 * n_child;
                     if (getenv("EFM_DEBUG"))
                         fprintf(stderr,
                                 "efm: level %d parents %lld items %llu children %.0f new %.0f rows %llu bytes %.0f ms %.3f\n",
-                                level, (long long)cn, (unsigned long long)(c0 == 0 && chunk >= n_front ? deg_sum : 0),
-                                n_child, n_new, h[C_WRITTEN], state_bytes * ((double)cn + n_new) + 16.0 * n_child, ms);
+                                level, (long long)cn, (unsigned long long)(c0 == 0 && chunk >= n_rows ? deg_sum : 0),
+                                n_child, n_new, h[C_WRITTEN], state_bytes * (n_par + n_new) + 16.0 * n_child, ms);
                     exp_before = h[C_EXP];
                     next_before = next_now;
                 }
@@ -795,10 +801,10 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
         }
         const bool unwritten = h[C_UNWRITTEN] != 0;
         n_front = unwritten ? (int64_t)(h[C_NEXT] + h[C_UNV]) : (int64_t)h[C_NEXT];
+        n_rows = (int64_t)std::min<unsigned long long>(h[C_WRITTEN], (unsigned long long)w.rows[cur ^ 1]);
         deg_sum = h[C_DEGSUM];
         c.levels = level - level0 + 1;
         cur ^= 1;
-        par_map = (const uint32_t *)w.live[cur].p;
         if (lim.max_frontier > 0 && n_front > lim.max_frontier) {
             status |= EFM_TRUNCATED;
             break;

@@ -44,6 +44,7 @@ enum {
     C_DIAG = 24,  // first bounds/watchdog record: code, value, limit, level
     C_ZERO = 28,  // subtractive steps discarded: no positive flux left on the reaction (Prop. 3)
     C_SLOW,       // narrow networks: children handed to the settle pass in this launch
+    C_LIVE,       // surviving rows counted by the live-list pass
     C_COUNT = 32
 };
 
@@ -113,14 +114,15 @@ struct LevelArgs {
     int cpw;                    // parents per warp chunk (1..32)
     unsigned long long *ctr;
     // first-K search (zero / null otherwise)
-    const uint32_t *perm;       // parent order: position -> arena index (null = arena order)
+    const uint32_t *perm;       // parent order: position -> arena index (null: arena rows par_base + position)
+    int64_t par_base;
     int fk_pc;                  // bound: |U| of the K-th smallest result found so far (0 = no bound)
     const uint64_t *fk_sup;     // bound: its support (W words)
     // generate/dedup split (single-job traversal): every surviving child gets
     // a reserved row and a fingerprint; the dedup pass keeps one per state
     uint64_t *fp;               // [fp_cap] fingerprint per reserved row (kDeadFp: unused)
     int64_t fp_cap;
-    uint32_t *live;             // dedup output: arena rows of the distinct children
+    uint32_t *live;             // unused by the kernels (kept for the host's bookkeeping)
     int blk;                    // rows a warp reserves at a time (NG..32)
     // subtractive variant (Eq. 5): rows hold the extra flux (M entries), then
     // the flux of every column; a state's branches also take flux away from
@@ -229,6 +231,9 @@ cudaError_t launch_dedup(const LevelArgs &a, int Mpad, int W, int sm_count, cuda
 // narrow networks: settle the children the generate pass listed (exact gcd,
 // int32 range, superset rule), then write their rows; a no-op otherwise
 cudaError_t launch_settle(const NetView &nv, const LevelArgs &a, int sm_count, cudaStream_t s);
+// the surviving rows (meta != 0) of [0, n) appended to live; *count must be 0
+cudaError_t launch_live_list(const uint32_t *meta, int64_t n, uint32_t *live, unsigned long long *count,
+                             int sm_count, cudaStream_t s);
 int generate_grid(const NetView &nv, int sm_count);
 cudaError_t launch_accept(const NetView &nv, const AcceptArgs &a, cudaStream_t s);
 // minimality test of the candidates appended since the last such launch (range read on the

@@ -1392,10 +1392,10 @@ __device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint
     for (int64_t p0 = worker * cpw; p0 < a.n_par; p0 += wstride) {
         const int64_t pl = p0 + lane;
         const bool pin = lane < cpw && pl < a.n_par;
-        const int64_t pid = pin ? (a.perm ? (int64_t)a.perm[pl] : pl) : 0;  // this lane's parent
+        const int64_t pid = pin ? (a.perm ? (int64_t)a.perm[pl] : a.par_base + pl) : 0;  // this lane's parent
         const int64_t pn = pl + wstride;
         if (lane < cpw && pn < a.n_par) {
-            const int64_t nid = a.perm ? (int64_t)a.perm[pn] : pn;
+            const int64_t nid = a.perm ? (int64_t)a.perm[pn] : a.par_base + pn;
             const char *rp = reinterpret_cast<const char *>(a.par.B + (size_t)nid * Mpad);
             for (int off = 0; off < Mpad * 4; off += 128) prefetch_l2(rp + off);
             prefetch_l2(a.par.U + (size_t)nid * W);
@@ -1695,8 +1695,12 @@ __device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint
         }
         if (__any_sync(FULL, fatal)) break;
     }
-    // rows reserved but not used: marked so that the dedup pass skips them
-    if (lane < pool_left && (int64_t)(pool_next + lane) < a.fp_cap) a.fp[pool_next + lane] = kDeadFp;
+    // rows reserved but not used: no fingerprint (the dedup pass skips them) and
+    // no branches (the next level reads every row of the arena)
+    for (int x = lane; x < pool_left; x += 32) {
+        if ((int64_t)(pool_next + x) < a.fp_cap) a.fp[pool_next + x] = kDeadFp;
+        if ((int64_t)(pool_next + x) < row_cap) a.child.meta[pool_next + x] = 0u;
+    }
     if (n_exp) atomicAdd(&a.ctr[C_EXP], n_exp);
     if (n_ovf) atomicAdd(&a.ctr[C_OVF], n_ovf);
     if (n_bal) atomicAdd(&a.ctr[C_BAL], n_bal);
@@ -1768,6 +1772,8 @@ __device__ void generate_narrow(const NetView &nv, const LevelArgs &a, const uin
     bool fatal = false;
     uint64_t pool_next = 0;
     int pool_left = 0;
+    uint64_t spool_next = 0;  // this warp's settle-record slots
+    int spool_left = 0;
     // rows for cnt children of the warp (warp-uniform call); returns the
     // first row of the calling lane's share given its rank among them
     auto reserve = [&](int cnt, int rank) -> uint64_t {
@@ -1792,10 +1798,10 @@ __device__ void generate_narrow(const NetView &nv, const LevelArgs &a, const uin
     for (int64_t p0 = worker * cpw; p0 < a.n_par; p0 += wstride) {
         const int64_t pl = p0 + lane;
         const bool pin = lane < cpw && pl < a.n_par;
-        const int64_t pid = pin ? (a.perm ? (int64_t)a.perm[pl] : pl) : 0;
+        const int64_t pid = pin ? (a.perm ? (int64_t)a.perm[pl] : a.par_base + pl) : 0;
         const int64_t pn = pl + wstride;
         if (lane < cpw && pn < a.n_par) {
-            const int64_t nid = a.perm ? (int64_t)a.perm[pn] : pn;
+            const int64_t nid = a.perm ? (int64_t)a.perm[pn] : a.par_base + pn;
             const char *rp = reinterpret_cast<const char *>(a.par.B + (size_t)nid * Mpad);
             for (int off = 0; off < Mpad * 4; off += 128) prefetch_l2(rp + off);
             prefetch_l2(a.par.U + (size_t)nid * W);
@@ -2001,11 +2007,23 @@ __device__ void generate_narrow(const NetView &nv, const LevelArgs &a, const uin
             // go to the settle pass as records ===
             const unsigned smask = __ballot_sync(FULL, slowl);
             if (smask) {
-                unsigned long long sbase = 0;
-                if (lane == 0) sbase = atomicAdd(&a.ctr[C_SLOW], (unsigned long long)__popc(smask));
-                sbase = __shfl_sync(FULL, sbase, 0);
+                // record slots from this warp's pool (32 at a time, one atomic)
+                const int scnt = __popc(smask), srank = __popc(smask & ((1u << lane) - 1u));
+                uint64_t sfresh = 0;
+                if (spool_left < scnt) {
+                    if (lane == 0) sfresh = atomicAdd(&a.ctr[C_SLOW], 32ull);
+                    sfresh = __shfl_sync(FULL, sfresh, 0);
+                }
+                const uint64_t si = srank < spool_left ? spool_next + (uint64_t)srank
+                                                       : sfresh + (uint64_t)(srank - spool_left);
+                if (spool_left < scnt) {
+                    spool_next = sfresh + (uint64_t)(scnt - spool_left);
+                    spool_left = 32 - (scnt - spool_left);
+                } else {
+                    spool_next += (uint64_t)scnt;
+                    spool_left -= scnt;
+                }
                 if (slowl) {
-                    const uint64_t si = sbase + (uint64_t)__popc(smask & ((1u << lane) - 1u));
                     if ((int64_t)si < a.slow_cap) {
                         uint64_t *r = a.slow + (size_t)si * kSlowWords;
                         const uint64_t w0 = (uint64_t)pl32 | ((uint64_t)kl << 32) | ((uint64_t)pcl << 44) |
@@ -2024,7 +2042,12 @@ __device__ void generate_narrow(const NetView &nv, const LevelArgs &a, const uin
         }
         if (__any_sync(FULL, fatal)) break;
     }
-    if (lane < pool_left && (int64_t)(pool_next + lane) < a.fp_cap) a.fp[pool_next + lane] = kDeadFp;
+    for (int x = lane; x < pool_left; x += 32) {
+        if ((int64_t)(pool_next + x) < a.fp_cap) a.fp[pool_next + x] = kDeadFp;
+        if ((int64_t)(pool_next + x) < row_cap) a.child.meta[pool_next + x] = 0u;
+    }
+    // settle-record slots left unused: marked so that the settle pass skips them
+    if (lane < spool_left && (int64_t)(spool_next + lane) < a.slow_cap) a.slow[(spool_next + lane) * kSlowWords] = ~0ull;
     if (n_exp) atomicAdd(&a.ctr[C_EXP], n_exp);
     if (n_ovf) atomicAdd(&a.ctr[C_OVF], n_ovf);
     if (n_bal) atomicAdd(&a.ctr[C_BAL], n_bal);
@@ -2096,7 +2119,7 @@ __global__ void __launch_bounds__(kExpandWarps * 32) settle_kernel(NetView nv, L
     for (int64_t base = wid * NG; base < n_slow; base += wstride) {
         if (__any_sync(FULL, fatal)) break;
             const int64_t r = base + gi;
-            const bool slow = r < n_slow;
+            bool slow = r < n_slow;
             // the record (every lane of the group reads it)
             uint64_t w0 = 0, w1 = 0, srh = 0, spm = 0, snm = 0, sum_ = 0, som = 0;
             if (slow) {
@@ -2112,6 +2135,7 @@ __global__ void __launch_bounds__(kExpandWarps * 32) settle_kernel(NetView nv, L
                 snm = q2.x;
                 sum_ = q2.y;
                 som = q3.x;
+                slow = w0 != ~0ull;  // an unused slot
             }
             const int64_t p = (int64_t)(uint32_t)w0;
             const int k = (int)((w0 >> 32) & 0xFFFu);
@@ -2328,30 +2352,37 @@ __device__ __forceinline__ bool same_state(const Arena &ar, int Mpad, int W, uin
     return eq;
 }
 
-// One thread per reserved row in [ctr[C_DEDUP_BEGIN], ctr[C_WRITTEN]).
+// One thread per reserved row in [ctr[C_DEDUP_BEGIN], ctr[C_WRITTEN]).  The
+// first row of every distinct state survives in place; a later copy gets a
+// zero meta word (no branches), so the next level reads the arena's rows in
+// order and no survivor list is built.  Survivors and their branch counts
+// are summed per block, with one atomic per block.
 __global__ void __launch_bounds__(256) dedup_kernel(LevelArgs a, int Mpad, int W)
 {
-    const int lane = threadIdx.x & 31;
+    __shared__ unsigned long long s_keep[8], s_deg[8], s_unv[8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint64_t begin = a.ctr[C_DEDUP_BEGIN];
     uint64_t end = a.ctr[C_WRITTEN];
     end = end < (uint64_t)a.fp_cap ? end : (uint64_t)a.fp_cap;
     const uint64_t row_cap = (uint64_t)a.child.cap;
-    unsigned long long deg = 0, n_unv = 0;
+    unsigned long long deg = 0, n_unv = 0, n_keep = 0;
     bool fatal = false;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    // warp-uniform trip count so that the ballots below see the whole warp
     for (uint64_t i0 = begin + (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < end; i0 += stride) {
         const uint64_t i = i0 + lane;
         bool mine = i < end;
         const uint64_t f = mine ? a.fp[i] : kDeadFp;
         mine = mine && f != kDeadFp;
-        bool keep = false;  // distinct state with a row: survives into the next frontier
         if (mine) {
             uint64_t pos;
             uint32_t tag;
             slot_tag_pos(f, a.slot_mask, pos, tag);
             const bool written = i < row_cap;
-            for (uint64_t probe = 0;; ++probe) {
+            if (i >= 0xFFFFFFFEull) {
+                record_diag(a.ctr, ERR_BOUNDS, 10, (long long)i, 0xFFFFFFFEll, a.level);
+                fatal = true;
+            }
+            for (uint64_t probe = 0; !fatal; ++probe) {
                 if (probe > a.slot_mask) {
                     record_diag(a.ctr, ERR_TABLE_FULL, 8, (long long)i, (long long)a.slot_mask, a.level);
                     fatal = true;
@@ -2359,33 +2390,28 @@ __global__ void __launch_bounds__(256) dedup_kernel(LevelArgs a, int Mpad, int W
                 }
                 const unsigned long long v = atomicCAS(&a.slots[pos], kEmpty, ((unsigned long long)tag << 32) | i);
                 if (v == kEmpty) {  // first of its state
-                    if (written)
-                        keep = true;
-                    else
+                    if (written) {
+                        ++n_keep;
+                        deg += (a.child.meta[i] >> 10) & 0x1FFFu;
+                    } else {
                         ++n_unv;
+                    }
                     break;
                 }
                 if ((uint32_t)(v >> 32) == tag) {
                     const uint64_t jrow = (uint32_t)v;
                     // a row without its state written cannot be compared: the
                     // level is then decided from the lower bound, or run again
-                    if (!written || jrow >= row_cap) break;
-                    if (same_state(a.child, Mpad, W, i, jrow)) break;  // duplicate
+                    if (!written || jrow >= row_cap) {
+                        if (written) a.child.meta[i] = 0u;
+                        break;
+                    }
+                    if (same_state(a.child, Mpad, W, i, jrow)) {  // a later copy
+                        a.child.meta[i] = 0u;
+                        break;
+                    }
                 }
                 pos = (pos + 1) & a.slot_mask;
-            }
-        }
-        const unsigned km = __ballot_sync(FULL, keep);
-        if (km) {
-            unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(&a.ctr[C_NEXT], (unsigned long long)__popc(km));
-            base = __shfl_sync(FULL, base, 0);
-            if (keep) {
-                const uint64_t slot = base + (uint64_t)__popc(km & ((1u << lane) - 1u));
-                if (slot < row_cap) {
-                    a.live[slot] = (uint32_t)i;
-                    deg += (a.child.meta[i] >> 10) & 0x1FFFu;
-                }
             }
         }
         if (__any_sync(FULL, fatal)) break;
@@ -2394,10 +2420,41 @@ __global__ void __launch_bounds__(256) dedup_kernel(LevelArgs a, int Mpad, int W
     for (int off = 16; off > 0; off >>= 1) {
         deg += __shfl_xor_sync(FULL, deg, off);
         n_unv += __shfl_xor_sync(FULL, n_unv, off);
+        n_keep += __shfl_xor_sync(FULL, n_keep, off);
     }
     if (lane == 0) {
-        if (deg) atomicAdd(&a.ctr[C_DEGSUM], deg);
-        if (n_unv) atomicAdd(&a.ctr[C_UNV], n_unv);
+        s_keep[wid] = n_keep;
+        s_deg[wid] = deg;
+        s_unv[wid] = n_unv;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long k = 0, d = 0, u = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            k += s_keep[w];
+            d += s_deg[w];
+            u += s_unv[w];
+        }
+        if (k) atomicAdd(&a.ctr[C_NEXT], k);
+        if (d) atomicAdd(&a.ctr[C_DEGSUM], d);
+        if (u) atomicAdd(&a.ctr[C_UNV], u);
+    }
+}
+
+// Surviving rows [0, n) of an arena (meta != 0: every state has |U| >= 1)
+// appended to a list, for the passes that sample or order a frontier.
+__global__ void live_list_kernel(const uint32_t *meta, int64_t n, uint32_t *live, unsigned long long *count)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; i0 < n;
+         i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + lane;
+        const bool keep = i < n && meta[i] != 0u;
+        const unsigned m = __ballot_sync(FULL, keep);
+        unsigned long long base = 0;
+        if (lane == 0 && m) base = atomicAdd(count, (unsigned long long)__popc(m));
+        base = __shfl_sync(FULL, base, 0);
+        if (keep) live[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
     }
 }
 
@@ -3128,6 +3185,15 @@ int generate_grid(const NetView &nv, int sm_count)
     EFM_GROUP_DISPATCH(nv.EPL, CALL_GGRID)
 #undef CALL_GGRID
     return sm_count;
+}
+
+cudaError_t launch_live_list(const uint32_t *meta, int64_t n, uint32_t *live, unsigned long long *count,
+                             int sm_count, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)sm_count * 8);
+    live_list_kernel<<<(unsigned)blocks, 256, 0, s>>>(meta, n, live, count);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_settle(const NetView &nv, const LevelArgs &a, int sm_count, cudaStream_t s)
