@@ -300,6 +300,7 @@ struct Work {
     int64_t slow_cap = 0;
     DevBuf perm, fkb;  // first-K search: parent order of a level, bound support
     DevBuf band;       // per column: intersection of the results containing it (W <= 2)
+    DevBuf ccnt, cfill, cptr, cne, csingle, cent;  // W <= 2: the superset rule's sentinel index
     DevBuf lx, lscore, lhist, lerr;  // learned order: features, scores, buckets, error flag
     int64_t lx_rows = 0;
     int64_t rows[2] = {0, 0};  // capacity of each arena (rows)
@@ -324,7 +325,8 @@ void free_work(Work &w, cudaStream_t s)
     for (int i = 0; i < 2; ++i) free_arena(w, i, s);
     DevBuf *bufs[] = {&w.slots, &w.cslots, &w.cand, &w.res, &w.bcnt,    &w.bfill, &w.bptr,
                       &w.bres,  &w.ctr,    &w.sortidx, &w.rcols, &w.perm, &w.fkb,
-                      &w.lx,    &w.lscore, &w.lhist,   &w.lerr, &w.band, &w.fp, &w.slow};
+                      &w.lx,    &w.lscore, &w.lhist,   &w.lerr, &w.band, &w.fp, &w.slow,
+                      &w.ccnt,  &w.cfill,  &w.cptr,    &w.cne,  &w.csingle, &w.cent};
     for (DevBuf *b : bufs) dev_free(*b, s);
     for (auto &e : w.ev)
         if (e) cudaEventDestroy(e);
@@ -391,7 +393,12 @@ int alloc_work(Work &w, const efm_net *net, const efm_limits &lim, int total_war
     ok = ok && dev_alloc(w.bptr, (size_t)(nv.N + 1) * 4, s);
     ok = ok && dev_alloc(w.ctr, C_COUNT * 8, s);
     if (nv.W > 2) ok = ok && dev_alloc(w.rcols, (size_t)w.res_cap * kRcolStride * 2, s);
-    if (nv.W <= 2) ok = ok && dev_alloc(w.band, (size_t)nv.N * nv.W * 8, s);
+    if (nv.W <= 2) {
+        const size_t cells = (size_t)nv.N * nv.N;
+        ok = ok && dev_alloc(w.band, (size_t)nv.N * nv.W * 8, s) && dev_alloc(w.ccnt, cells * 4, s) &&
+             dev_alloc(w.cfill, cells * 4, s) && dev_alloc(w.cptr, (cells + 1) * 4, s) &&
+             dev_alloc(w.cne, (size_t)nv.N * nv.W * 8, s) && dev_alloc(w.csingle, (size_t)nv.N * 4, s);
+    }
     if (lim.first_k > 0) ok = ok && dev_alloc(w.fkb, W * 8, s);
     for (auto &e : w.ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
     if (!ok) {
@@ -603,14 +610,26 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
             const int64_t need = std::max<int64_t>(res_n * (int64_t)lim.max_len, 1);
             if (need > w.bres_cap) {
                 dev_free(w.bres, s);
+                dev_free(w.cent, s);
                 const int64_t cap = std::max<int64_t>(need, 2 * w.bres_cap);
                 if (!dev_alloc(w.bres, (size_t)cap * nv.W * 8, s)) return EFM_ENOMEM;
+                if (nv.W <= 2 && !dev_alloc(w.cent, (size_t)cap * nv.W * 8, s)) return EFM_ENOMEM;
                 w.bres_cap = cap;
             }
             a.bres = (const uint64_t *)w.bres.p;
             a.bids = (const int32_t *)w.bres.p;
             CK(launch_buckets(nv, (const uint64_t *)w.res.p, res_n, (int32_t *)w.bcnt.p, (int32_t *)w.bptr.p,
                               (int32_t *)w.bfill.p, (uint64_t *)w.bres.p, (uint64_t *)w.band.p, s));
+            if (nv.W <= 2) {
+                CK(launch_sentinel_index(nv, (const uint64_t *)w.res.p, res_n, (const int32_t *)w.bcnt.p,
+                                         (int32_t *)w.ccnt.p, (int32_t *)w.cfill.p, (int32_t *)w.cptr.p,
+                                         (uint64_t *)w.cent.p, (uint64_t *)w.cne.p, (uint32_t *)w.csingle.p, s));
+                a.cptr = (const int32_t *)w.cptr.p;
+                a.cent = (const uint64_t *)w.cent.p;
+                a.cne = (const uint64_t *)w.cne.p;
+                a.csingle = (const uint32_t *)w.csingle.p;
+                out.kernel_launches += res_n > 0 ? 4 : 2;
+            }
             out.kernel_launches += res_n > 0 ? 3 : 1;
             buckets_built_for = res_n;
         }

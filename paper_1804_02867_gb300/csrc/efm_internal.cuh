@@ -110,6 +110,14 @@ struct LevelArgs {
     const int32_t *bids;        // bucket entries: result ids (W > 2), same buffer as bres
     const uint16_t *rcols;      // per result: column count, then its columns (stride kRcolStride)
     const uint64_t *band;       // W <= 2: per column, the intersection of the results containing it (or null)
+    // W <= 2: the superset rule's index.  A result E is filed, for each of its
+    // columns k, in cell (k, s) where s is E's other column with the fewest
+    // results (its sentinel); a child adding k scans only the cells whose
+    // sentinel lies in its support.  Null: the buckets above.
+    const int32_t *cptr;        // [N * N + 1] cell offsets into cent
+    const uint64_t *cent;       // cell entries: the result's W support words
+    const uint64_t *cne;        // [N][W]: sentinels with a non-empty cell (k, s)
+    const uint32_t *csingle;    // [N]: 1 if {k} itself is a result
     int level, max_len, max_sec;
     int cpw;                    // parents per warp chunk (1..32)
     unsigned long long *ctr;
@@ -242,6 +250,11 @@ cudaError_t launch_accept_new(const NetView &nv, const AcceptArgs &a, int sm_cou
 cudaError_t launch_buckets(const NetView &nv, const uint64_t *res, int64_t n_res, int32_t *bcnt, int32_t *bptr,
                            int32_t *bfill, uint64_t *bres, uint64_t *band,
                            cudaStream_t s);  // W > 2: bres holds int32 ids; band (W <= 2, may be null)
+// W <= 2: the sentinel index of the superset rule over results [0, n_res)
+// (bcnt: results per column, from launch_buckets); ccnt/cfill: N*N scratch
+cudaError_t launch_sentinel_index(const NetView &nv, const uint64_t *res, int64_t n_res, const int32_t *bcnt,
+                                  int32_t *ccnt, int32_t *cfill, int32_t *cptr, uint64_t *cent, uint64_t *cne,
+                                  uint32_t *csingle, cudaStream_t s);
 cudaError_t launch_sort_results(const uint64_t *res, int64_t n, int W, uint32_t *idx, int64_t n_pow2,
                                 uint64_t *out, int64_t n_keep, cudaStream_t s);
 int expand_grid(const NetView &nv, int sm_count);

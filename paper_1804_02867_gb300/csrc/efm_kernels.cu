@@ -826,6 +826,30 @@ __device__ __forceinline__ bool child_after(const uint64_t *pu, int k, const uin
     return false;
 }
 
+// Superset rule through the sentinel index (W <= 2): does a result E with
+// k in E lie inside U + {k}?  Only the cells (k, s) with s in U are scanned:
+// E's sentinel is one of its columns other than k, so E inside U + {k}
+// requires the sentinel in U.
+__device__ __forceinline__ bool pruned_indexed(const LevelArgs &a, const uint64_t *pu, int k, int W, int N)
+{
+    if (a.csingle[k]) return true;
+    const uint64_t u0 = child_word(pu, 0, k), u1 = W == 2 ? child_word(pu, 1, k) : 0ull;
+    for (int w = 0; w < W; ++w) {
+        uint64_t m = __ldg(a.cne + (size_t)k * W + w) & (w == 0 ? u0 : u1);
+        while (m) {
+            const int sent = w * 64 + __ffsll((long long)m) - 1;
+            m &= m - 1;
+            const int32_t lo = __ldg(a.cptr + (size_t)k * N + sent), hi = __ldg(a.cptr + (size_t)k * N + sent + 1);
+            for (int32_t e = lo; e < hi; ++e) {
+                const uint64_t *E = a.cent + (size_t)e * W;
+                const uint64_t e0 = __ldg(E), e1 = W == 2 ? __ldg(E + 1) : 0ull;
+                if (((e0 & ~u0) | (e1 & ~u1)) == 0) return true;
+            }
+        }
+    }
+    return false;
+}
+
 template <int G, int CPL>
 struct BatchShape {
     static constexpr int NCH = G * CPL;          // 16-byte chunks per row
@@ -1603,7 +1627,9 @@ __device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint
                 if (grown && !in_u) {
                     const int64_t b1 = a.bptr[k];
                     const int64_t n = a.bptr[k + 1] - b1;
-                    if (W <= 2) {
+                    if (W <= 2 && a.cptr) {
+                        if (gl == 0) pr = pruned_indexed(a, pu, k, W, nv.N);
+                    } else if (W <= 2) {
                         const uint64_t u0 = child_word(pu, 0, k), u1 = W == 2 ? child_word(pu, 1, k) : 0ull;
                         bool maybe = n > 0;
                         if (maybe && a.band) {
@@ -1928,7 +1954,9 @@ __device__ void generate_narrow(const NetView &nv, const LevelArgs &a, const uin
                 const int64_t b1 = a.bptr[kl];
                 const int64_t n = a.bptr[kl + 1] - b1;
                 bool pr = false;
-                if (n > 0) {
+                if (W <= 2 && a.cptr) {
+                    pr = pruned_indexed(a, pu_l, kl, W, nv.N);
+                } else if (n > 0) {
                     if (W <= 2) {
                         const uint64_t u0 = child_word(pu_l, 0, kl), u1 = W == 2 ? child_word(pu_l, 1, kl) : 0ull;
                         bool maybe = true;
@@ -2247,7 +2275,9 @@ __global__ void __launch_bounds__(kExpandWarps * 32) settle_kernel(NetView nv, L
                 if (cand && !in_u) {
                     const int64_t b1 = a.bptr[k];
                     const int64_t n = a.bptr[k + 1] - b1;
-                    if (W <= 2) {
+                    if (W <= 2 && a.cptr) {
+                        if (gl == 0) pr = pruned_indexed(a, pu, k, W, nv.N);
+                    } else if (W <= 2) {
                         const uint64_t u0 = child_word(pu, 0, k), u1 = W == 2 ? child_word(pu, 1, k) : 0ull;
                         bool maybe = n > 0;
                         if (maybe && a.band) {
@@ -2708,6 +2738,102 @@ __global__ void bucket_fill_kernel(const uint64_t *res, int64_t n, int W, const 
             }
         }
     }
+}
+
+// The superset rule's sentinel index (W <= 2, N <= 128): for each result E
+// its two columns with the fewest results, (m1, m2), ties by column; for each
+// k in E the sentinel is m1, or m2 when k = m1.
+__device__ __forceinline__ void result_sentinels(const uint64_t *E, int W, const int32_t *bcnt, int &m1, int &m2)
+{
+    m1 = m2 = -1;
+    long long k1 = 0x7FFFFFFFFFFFFFFFll, k2 = 0x7FFFFFFFFFFFFFFFll;
+    for (int w = 0; w < W; ++w)
+        for (uint64_t x = E[w]; x; x &= x - 1) {
+            const int c = w * 64 + __ffsll((long long)x) - 1;
+            const long long key = ((long long)bcnt[c] << 16) | c;
+            if (key < k1) {
+                k2 = k1;
+                m2 = m1;
+                k1 = key;
+                m1 = c;
+            } else if (key < k2) {
+                k2 = key;
+                m2 = c;
+            }
+        }
+}
+
+__global__ void sentinel_count_kernel(const uint64_t *res, int64_t n, int W, int N, const int32_t *bcnt, int32_t *ccnt,
+                                      uint32_t *csingle)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const uint64_t *E = res + (size_t)r * W;
+    int m1, m2;
+    result_sentinels(E, W, bcnt, m1, m2);
+    if (m2 < 0) {  // a one-column result: every child adding that column contains it
+        if (m1 >= 0) csingle[m1] = 1u;
+        return;
+    }
+    for (int w = 0; w < W; ++w)
+        for (uint64_t x = E[w]; x; x &= x - 1) {
+            const int k = w * 64 + __ffsll((long long)x) - 1;
+            atomicAdd(&ccnt[(size_t)k * N + (k == m1 ? m2 : m1)], 1);
+        }
+}
+
+__global__ void sentinel_scan_kernel(const int32_t *ccnt, int cells, int32_t *cptr)
+{
+    // one CTA of 1024 threads: exclusive scan over the cells
+    __shared__ int32_t part[1024];
+    const int per = (cells + 1023) / 1024;
+    const int beg = threadIdx.x * per;
+    int32_t s = 0;
+    for (int i = beg; i < beg + per && i < cells; ++i) s += ccnt[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int32_t run = part[threadIdx.x] - s;
+    for (int i = beg; i < beg + per && i < cells; ++i) {
+        cptr[i] = run;
+        run += ccnt[i];
+    }
+    if (threadIdx.x == 1023) cptr[cells] = part[1023];
+}
+
+__global__ void sentinel_mask_kernel(const int32_t *ccnt, int N, int W, uint64_t *cne)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    for (int w = 0; w < W; ++w) {
+        uint64_t m = 0;
+        for (int b = 0; b < 64 && w * 64 + b < N; ++b)
+            if (ccnt[(size_t)k * N + w * 64 + b] > 0) m |= 1ull << b;
+        cne[(size_t)k * W + w] = m;
+    }
+}
+
+__global__ void sentinel_fill_kernel(const uint64_t *res, int64_t n, int W, int N, const int32_t *bcnt,
+                                     const int32_t *cptr, int32_t *cfill, uint64_t *cent)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const uint64_t *E = res + (size_t)r * W;
+    int m1, m2;
+    result_sentinels(E, W, bcnt, m1, m2);
+    if (m2 < 0) return;
+    for (int w = 0; w < W; ++w)
+        for (uint64_t x = E[w]; x; x &= x - 1) {
+            const int k = w * 64 + __ffsll((long long)x) - 1;
+            const size_t cell = (size_t)k * N + (k == m1 ? m2 : m1);
+            const int32_t pos = cptr[cell] + atomicAdd(&cfill[cell], 1);
+            for (int v = 0; v < W; ++v) cent[(size_t)pos * W + v] = E[v];
+        }
 }
 
 // ---------------------------------------------------------------------------
@@ -3263,6 +3389,26 @@ cudaError_t launch_buckets(const NetView &nv, const uint64_t *res, int64_t n_res
     if (items > 0)
         bucket_fill_kernel<<<(int)((items + tb - 1) / tb), tb, 0, s>>>(res, n_res, nv.W, bptr, bfill, bres,
                                                                       reinterpret_cast<unsigned long long *>(band));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sentinel_index(const NetView &nv, const uint64_t *res, int64_t n_res, const int32_t *bcnt,
+                                  int32_t *ccnt, int32_t *cfill, int32_t *cptr, uint64_t *cent, uint64_t *cne,
+                                  uint32_t *csingle, cudaStream_t s)
+{
+    const int N = nv.N, W = nv.W;
+    const size_t cells = (size_t)N * N;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(ccnt, 0, cells * 4, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(cfill, 0, cells * 4, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(csingle, 0, (size_t)N * 4, s)) != cudaSuccess) return e;
+    const int tb = 256;
+    if (n_res > 0)
+        sentinel_count_kernel<<<(int)((n_res + tb - 1) / tb), tb, 0, s>>>(res, n_res, W, N, bcnt, ccnt, csingle);
+    sentinel_scan_kernel<<<1, 1024, 0, s>>>(ccnt, (int)cells, cptr);
+    sentinel_mask_kernel<<<(N + 127) / 128, 128, 0, s>>>(ccnt, N, W, cne);
+    if (n_res > 0)
+        sentinel_fill_kernel<<<(int)((n_res + tb - 1) / tb), tb, 0, s>>>(res, n_res, W, N, bcnt, cptr, cfill, cent);
     return cudaGetLastError();
 }
 
