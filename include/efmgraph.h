@@ -66,9 +66,13 @@ typedef struct {
     int64_t max_frontier;  /* <= 0: no budget (2^22 states per level); else stop when a level
                               exceeds it (EFM_TRUNCATED); at most 2^31 */
     int32_t first_k;       /* 0: every result; K > 0: exactly the K smallest results in the
-                              output order (|U|, then the ascending column list), found by
-                              the same traversal with an exact branch and bound; max_results
-                              must then be 0 (not with the batched call) */
+                              output order (|U|, then the ascending column list).  Found by
+                              traversals with the length cap deepened, P = 1, 2, ... up to
+                              max_len, until one holds at least K results (those of size <= P
+                              are exactly that run's results), each with an exact branch and
+                              bound; the counters are those of the last run.  The answer is
+                              certified unless EFM_TRUNCATED is set.  max_results must be 0
+                              (not with the batched call) */
     int32_t proposal;      /* order of a first-K search: EFM_PLAIN (arena order) or
                               EFM_LEARNED (scores of the model passed with the call); the
                               result set is the same either way */
@@ -371,8 +375,8 @@ int efm_model_train(efm_model *model, int32_t epochs, int32_t batch_tiles, float
                     float *last_loss);
 
 /* Training rows from traces: for each target, run the first-K search of
- * `limits` (first_k > 0, max_results = 0) in plain order, then run it
- * again and record the features of up to rows_per_level states of every
+ * `limits` (first_k > 0, max_results = 0) in plain order, then run its last
+ * deepening run again and record the features of up to rows_per_level states of every
  * level's frontier (an evenly strided sample), labelled 1 when the state's
  * support lies inside a support of the answer.  Targets whose search is
  * truncated or finds nothing add no rows. */

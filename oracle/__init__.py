@@ -256,3 +256,19 @@ def first_k(net, target: int, k: int, max_len: int, max_secondary: int):
         if len(sup) >= k or P == max_len:
             return sup[:k], P
     raise AssertionError("unreachable")
+
+
+def first_k_within(net, target: int, k: int, max_len: int, max_secondary: int, max_frontier: int):
+    """first_k evaluated under a frontier budget, for networks whose complete
+    levels do not fit in host memory.  The same deepening; a run at P whose
+    every level stayed within max_frontier holds exactly the results of
+    popcount <= P, so the answer is the definition's.  Returns (supports,
+    the P used, certified); certified is False when the run at P overflowed
+    the budget, and the supports are then not the definition's answer."""
+    for P in range(1, max_len + 1):
+        sup, ctr = enumerate_pathways(net, target, Limits(P, max_secondary, 0, max_frontier))
+        if ctr["status"] & TRUNCATED:
+            return sup[:k], P, False
+        if len(sup) >= k or P == max_len:
+            return sup[:k], P, True
+    raise AssertionError("unreachable")

@@ -181,6 +181,8 @@ extern "C" int efm_load_network(int32_t n_met, int32_t n_rxn, const int32_t *row
     nv.o_keyr = prep.o_keyr;
     nv.o_hrow = prep.o_hrow;
     nv.o_colx = prep.o_colx;
+    nv.o_fixc = prep.o_fixc;
+    nv.o_fixp = prep.o_fixp;
     nv.blob_words = (int)blob.size();
     nv.M = prep.M;
     nv.N = prep.N;
@@ -250,6 +252,7 @@ extern "C" int efm_load_network(int32_t n_met, int32_t n_rxn, const int32_t *row
         vs.EPL = sub.EPL;
         vs.Mpad = sub.Mpad;
         vs.narrow = 0;
+        vs.o_fixc = vs.o_fixp = 0;
         net->has_sub = true;
     }
     *out = net;
@@ -294,6 +297,8 @@ namespace {
 struct Work {
     DevBuf U[2], B[2], meta[2], live[2];
     DevBuf sum[2];  // narrow networks: per-state summaries of the extra-flux row
+    DevBuf fx[2];   // first-K on wide networks: per-state lane masks of the rows U consumes / produces
+    int fx_words = 0;  // lane-mask words per state (0: not kept)
     DevBuf slots, cslots, cand, res, bcnt, bfill, bptr, bres, ctr, sortidx, rcols;
     DevBuf fp;         // fingerprints of one level's reserved child rows
     DevBuf slow;       // narrow networks: records of the children the settle pass decides
@@ -317,6 +322,7 @@ void free_arena(Work &w, int i, cudaStream_t s)
     dev_free(w.meta[i], s);
     dev_free(w.live[i], s);
     dev_free(w.sum[i], s);
+    dev_free(w.fx[i], s);
     w.rows[i] = 0;
 }
 
@@ -340,6 +346,7 @@ bool alloc_arena(Work &w, const NetView &nv, int i, int64_t rows, cudaStream_t s
     bool ok = dev_alloc(w.U[i], F * nv.W * 8, s) && dev_alloc(w.B[i], F * nv.Mpad * 4, s) &&
               dev_alloc(w.meta[i], F * 4, s) && dev_alloc(w.live[i], F * 4, s);
     if (ok && nv.narrow) ok = dev_alloc(w.sum[i], F * kSumWords * 8, s);
+    if (ok && w.fx_words) ok = dev_alloc(w.fx[i], F * w.fx_words * 4, s);
     if (ok) w.rows[i] = rows;
     return ok;
 }
@@ -382,6 +389,8 @@ int alloc_work(Work &w, const efm_net *net, const efm_limits &lim, int total_war
     w.cand_cap = (int64_t)1 << 20;
     w.res_cap = w.cand_cap;
     w.cslot_cap = next_pow2(2 * (uint64_t)w.cand_cap);
+    // first-K on a wide network keeps the lane masks of the length-cap rule
+    w.fx_words = (lim.first_k > 0 && nv.o_fixc > 0 && !nv.narrow) ? 2 * std::min(32, 4 * nv.EPL) : 0;
     const size_t W = (size_t)nv.W;
     bool ok = alloc_arena(w, nv, 0, rows, s) && alloc_arena(w, nv, 1, rows, s);
     ok = ok && ensure_level_tables(w, 1024 + 32 * (uint64_t)total_warps, s);
@@ -517,13 +526,15 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
     a.max_sec = lim.max_secondary;
     a.ctr = ctr;
     a.sub = lim.variant == EFM_SUBTRACTIVE ? 1 : 0;
+    a.cap_dead = lim.first_k > 0 ? 1 : 0;
     auto arena = [&](int i) {
-        Arena r;
+        Arena r{};
         r.U = (uint64_t *)w.U[i].p;
         r.B = (int32_t *)w.B[i].p;
         r.meta = (uint32_t *)w.meta[i].p;
         r.cap = w.rows[i];
         r.sum = (uint64_t *)w.sum[i].p;
+        r.fx = (uint32_t *)w.fx[i].p;
         return r;
     };
 
@@ -879,6 +890,48 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
     return EFM_OK;
 }
 
+// First-K by deepening the length cap.  The results of size <= P are exactly
+// the results of the traversal run with max_len = P (every state on a path to
+// such a result is no larger), so runs at P = 1, 2, ... stop at the first P
+// with at least K results, or at limits.max_len.  The cap keeps each run's
+// levels to states of size <= P and lets the length-cap rule drop the states
+// that can no longer balance.  A run that overflows the frontier budget ends
+// the search uncertified (TRUNCATED).  The counters are the last run's; the
+// timings add up every run.  *depth: the P of the last run.  A seed set
+// (Prop. 1) starts the deepening at its own size.
+int run_first_k(efm_net *net, Work &w, const efm_limits &lim, int target, TargetOut &out, const efm_model *model,
+                int *depth, const int32_t *seedset = nullptr, int n_seedset = 0)
+{
+    double total_ms = 0.0, expand_ms = 0.0, expand_bytes = 0.0;
+    int64_t expand_launches = 0, kernel_launches = 0;
+    for (int P = std::max(1, n_seedset);; ++P) {
+        efm_limits l2 = lim;
+        l2.max_len = std::min(P, lim.max_len);
+        TargetOut o;
+        const int rc = run_target(net, w, l2, target, o, model, nullptr, seedset, n_seedset);
+        if (rc) {
+            dev_free(o.sup, net->stream);
+            return rc;
+        }
+        total_ms += o.total_ms;
+        expand_ms += o.expand_ms;
+        expand_bytes += o.expand_bytes;
+        expand_launches += o.expand_launches;
+        kernel_launches += o.kernel_launches;
+        if ((o.status & EFM_TRUNCATED) || o.n >= lim.first_k || P >= lim.max_len) {
+            out = o;
+            out.total_ms = total_ms;
+            out.expand_ms = expand_ms;
+            out.expand_bytes = expand_bytes;
+            out.expand_launches = expand_launches;
+            out.kernel_launches = kernel_launches;
+            if (depth) *depth = l2.max_len;
+            return EFM_OK;
+        }
+        dev_free(o.sup, net->stream);
+    }
+}
+
 }  // namespace
 
 extern "C" int efm_find_pathways(efm_net *net, const int32_t *targets, int32_t n_targets, const efm_limits *limits,
@@ -910,7 +963,8 @@ extern "C" int efm_find_pathways(efm_net *net, const int32_t *targets, int32_t n
     int rc = alloc_work(w, net, lim, total_warps, net->stream);
     int flags = 0;
     for (int i = 0; rc == EFM_OK && i < n_targets; ++i) {
-        rc = run_target(net, w, lim, targets[i], job->out[i], mdl);
+        rc = lim.first_k > 0 ? run_first_k(net, w, lim, targets[i], job->out[i], mdl, nullptr)
+                             : run_target(net, w, lim, targets[i], job->out[i], mdl);
         flags |= job->out[i].status;
     }
     free_work(w, net->stream);
@@ -958,7 +1012,9 @@ extern "C" int efm_find_pathways_from(efm_net *net, const int32_t *columns, int3
     if (rc == EFM_OK && !dev_alloc(cols, (size_t)n_columns * 4, s)) rc = EFM_ENOMEM;
     if (rc == EFM_OK && cudaMemcpyAsync(cols.p, columns, (size_t)n_columns * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
         rc = EFM_ECUDA;
-    if (rc == EFM_OK)
+    if (rc == EFM_OK && lim.first_k > 0)
+        rc = run_first_k(net, w, lim, -1, job->out[0], nullptr, nullptr, (const int32_t *)cols.p, n_columns);
+    else if (rc == EFM_OK)
         rc = run_target(net, w, lim, -1, job->out[0], nullptr, nullptr, (const int32_t *)cols.p, n_columns);
     free_work(w, s);
     dev_free(cols, s);
@@ -1805,7 +1861,8 @@ extern "C" int efm_model_trace(efm_model *m, efm_net *net, const int32_t *target
     int rc = alloc_work(w, net, lim, total_warps, net->stream);
     for (int i = 0; rc == EFM_OK && i < n_targets; ++i) {
         TargetOut ans;
-        rc = run_target(net, w, lim, targets[i], ans);  // the answer, then the traced rerun
+        int depth = lim.max_len;
+        rc = run_first_k(net, w, lim, targets[i], ans, nullptr, &depth);  // the answer, then the traced rerun
         if (rc == EFM_OK && ans.n > 0 && !(ans.status & EFM_TRUNCATED)) {
             Trace tr;
             tr.m = m;
@@ -1813,7 +1870,9 @@ extern "C" int efm_model_trace(efm_model *m, efm_net *net, const int32_t *target
             tr.n_ans = ans.n;
             tr.rows_per_level = rows_per_level;
             TargetOut again;
-            rc = run_target(net, w, lim, targets[i], again, nullptr, &tr);
+            efm_limits last = lim;  // the search the answer came from: its last deepening run
+            last.max_len = depth;
+            rc = run_target(net, w, last, targets[i], again, nullptr, &tr);
             dev_free(again.sup, net->stream);
         }
         dev_free(ans.sup, net->stream);

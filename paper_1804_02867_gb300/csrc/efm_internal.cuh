@@ -45,6 +45,7 @@ enum {
     C_ZERO = 28,  // subtractive steps discarded: no positive flux left on the reaction (Prop. 3)
     C_SLOW,       // narrow networks: children handed to the settle pass in this launch
     C_LIVE,       // surviving rows counted by the live-list pass
+    C_CAPDEAD,    // first-K: children at the length cap that can never balance
     C_COUNT = 32
 };
 
@@ -68,6 +69,9 @@ struct NetView {
     int o_keyr;                // per rank: positive key [64], then negative key [64]
     int o_hrow;                // per row: 64-bit row hash constant R[m]
     int o_colx;                // per column: suppP, suppN, suppR, HC (u64 each), smax, gcd1 (10 words)
+    // wide networks: per column, G lane masks of the rows it consumes, then
+    // (at o_fixp) of the rows it produces, G = min(32, 4 EPL); 0: absent
+    int o_fixc, o_fixp;
     const int32_t *metptr;     // full S rows over split columns (seeds), [n_met + 1]
     const uint32_t *metent;    // packed (column, coefficient)
     int n_met;
@@ -90,6 +94,10 @@ struct Arena {
     //   sum[6 s + 4] = rows with odd EF_m
     //   sum[6 s + 5] = an upper bound of max_m |EF_m| (saturating at 2^31 - 1)
     uint64_t *sum;
+    // first-K on wide networks: per state, 2G lane masks (G = min(32, 4 EPL)):
+    // the rows some column of U consumes, then the rows some column of U
+    // produces (null: not kept)
+    uint32_t *fx;
 };
 
 constexpr int kSumWords = 6;
@@ -126,6 +134,9 @@ struct LevelArgs {
     int64_t par_base;
     int fk_pc;                  // bound: |U| of the K-th smallest result found so far (0 = no bound)
     const uint64_t *fk_sup;     // bound: its support (W words)
+    // first-K: drop an unbalanced child at the length cap that no sequence of
+    // secondary steps can balance (0 = keep every child)
+    int cap_dead;
     // generate/dedup split (single-job traversal): every surviving child gets
     // a reserved row and a fingerprint; the dedup pass keeps one per state
     uint64_t *fp;               // [fp_cap] fingerprint per reserved row (kDeadFp: unused)

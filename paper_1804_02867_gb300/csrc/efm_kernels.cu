@@ -481,6 +481,11 @@ __device__ void seed_range(const NetView &nv, const LevelArgs &a, int target, in
             const uint32_t bkey = branch_key(bl, nv, key, a.sub);
             if (lane == 0) a.child.meta[idx] = pack_meta(bkey, 1);
             deg_sum += bkey >> 16;
+            if (a.child.fx) {  // the lane masks of {k}: column k's own
+                const int G = EPL >= 8 ? 32 : 4 * EPL;
+                for (int x = lane; x < 2 * G; x += 32)
+                    a.child.fx[(size_t)idx * (2 * G) + x] = bl[(x < G ? nv.o_fixc : nv.o_fixp) + k * G + x % G];
+            }
         }
         if (EPL <= 2 && nv.narrow && a.child.sum) {
             const NarrowSum sm = warp_summary<EPL>(bl, nv, t, lane);
@@ -720,6 +725,14 @@ __global__ void __launch_bounds__(32) seedset_kernel(NetView nv, LevelArgs a, co
     for (int x = lane; x < W; x += 32) a.child.U[x] = U[x];
 #pragma unroll
     for (int e = 0; e < EPL; ++e) a.child.B[lane + 32 * e] = t[e];
+    if (a.child.fx) {  // the lane masks of R_in: the union of its columns'
+        const int G = EPL >= 8 ? 32 : 4 * EPL;
+        for (int x = lane; x < 2 * G; x += 32) {
+            uint32_t f = 0;
+            for (int i = 0; i < n_cols; ++i) f |= nv.blob[(x < G ? nv.o_fixc : nv.o_fixp) + cols[i] * G + x % G];
+            a.child.fx[x] = f;
+        }
+    }
     const uint32_t bkey = branch_key(nv.blob, nv, key, a.sub);
     if (lane == 0) {
         a.child.meta[0] = pack_meta(bkey, n_cols);
@@ -1405,7 +1418,7 @@ __device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint
     const int4 *dcol = reinterpret_cast<const int4 *>(bl + nv.o_dcols);
     const int64_t row_cap = a.child.cap;
 
-    unsigned long long n_exp = 0, n_ovf = 0, n_bal = 0, n_pruned = 0, n_unwritten = 0, n_zero = 0;
+    unsigned long long n_exp = 0, n_ovf = 0, n_bal = 0, n_pruned = 0, n_unwritten = 0, n_zero = 0, n_capdead = 0;
     bool fatal = false;
     // this warp's reserved rows: [pool_next, pool_next + pool_left)
     uint64_t pool_next = 0;
@@ -1647,7 +1660,42 @@ __device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint
                 }
                 pr = group_or<G>(pr ? 1u : 0u) != 0;
                 if (pr && gl == 0) ++n_pruned;
-                const bool norm = grown && !pr;
+                bool norm = grown && !pr;
+                // first-K: the lane masks of the rows the child's support
+                // consumes and produces (the parent's, plus column k's)
+                uint32_t fxc = 0, fxp = 0;
+                if (a.child.fx && norm) {
+                    const size_t fo = (size_t)p * (2 * G);
+                    fxc = a.par.fx[fo + gl] | bl[nv.o_fixc + k * G + gl];
+                    fxp = a.par.fx[fo + G + gl] | bl[nv.o_fixp + k * G + gl];
+                }
+                // first-K at the length cap: the child can only take secondary
+                // steps, which add flux to columns of its support.  A row with a
+                // surplus (deficit) that no column of the support consumes
+                // (produces) keeps its sign under every such step, so the child
+                // never balances; with no secondary step left it cannot move.
+                if (a.cap_dead && __any_sync(FULL, norm && pc + (in_u ? 0 : 1) >= a.max_len)) {
+                    bool dead = false;
+                    const int pcc = pc + (in_u ? 0 : 1);
+                    if (norm && pcc >= a.max_len) {
+                        if (a.level - pcc + 1 >= a.max_sec) {
+                            dead = true;
+                        } else if (a.child.fx) {
+#pragma unroll
+                            for (int i = 0; i < CPL; ++i)
+#pragma unroll
+                                for (int jj = 0; jj < 4; ++jj) {
+                                    const int32_t v = t32[4 * i + jj];
+                                    const uint32_t fix = v > 0 ? fxc : fxp;
+                                    if (v != 0 && 4 * (gl + G * i) + jj < nv.M && !((fix >> (4 * i + jj)) & 1u))
+                                        dead = true;
+                                }
+                        }
+                    }
+                    dead = group_or<G>(dead ? 1u : 0u) != 0;
+                    if (dead && gl == 0) ++n_capdead;
+                    norm = norm && !dead;
+                }
 
                 // --- pivot key and fingerprint ---
                 uint32_t key = 0xFFFFFFFFu, hlo = 0, hhi = 0;
@@ -1701,6 +1749,10 @@ __device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint
                                 db[gl + G * i] = make_int4(t32[4 * i + 0], t32[4 * i + 1], t32[4 * i + 2], t32[4 * i + 3]);
                             uint64_t *du = a.child.U + (size_t)idx * W;
                             for (int w = gl; w < W; w += G) du[w] = child_word(pu, w, k);
+                            if (a.child.fx) {
+                                a.child.fx[(size_t)idx * (2 * G) + gl] = fxc;
+                                a.child.fx[(size_t)idx * (2 * G) + G + gl] = fxp;
+                            }
                             if (gl == 0) a.child.meta[idx] = pack_meta(branch_key(bl, nv, key, a.sub), pc + (in_u ? 0 : 1));
                         } else if (gl == 0) {
                             ++n_unwritten;
@@ -1733,6 +1785,7 @@ __device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint
     if (n_pruned) atomicAdd(&a.ctr[C_PRUNED], n_pruned);
     if (n_unwritten) atomicAdd(&a.ctr[C_UNWRITTEN], n_unwritten);
     if (n_zero) atomicAdd(&a.ctr[C_ZERO], n_zero);
+    if (n_capdead) atomicAdd(&a.ctr[C_CAPDEAD], n_capdead);
 }
 
 template <int G, int CPL>
@@ -2995,7 +3048,7 @@ __device__ void run_job(const BatchArgs &ba, const BatchJob &job, char *slice, u
     a.max_sec = ba.max_sec;
     a.ctr = ctr;
     auto arena = [&](int i) {
-        Arena r;
+        Arena r{};
         r.U = reinterpret_cast<uint64_t *>(slice + L.o_U[i]);
         r.B = reinterpret_cast<int32_t *>(slice + L.o_B[i]);
         r.meta = reinterpret_cast<uint32_t *>(slice + L.o_meta[i]);

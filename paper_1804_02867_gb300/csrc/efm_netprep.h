@@ -23,6 +23,8 @@
 //    per column the rank-space masks of its rows (positive and negative
 //    orders), its row-space mask, sum_m S_int[m][k] R[m], max |S_int[m][k]|
 //    and whether the gcd of its entries is 1;
+//  - wide networks: per column, the lane masks of the rows it consumes and
+//    of the rows it produces (the first-K length-cap rule);
 //  - a dense column-major copy of S_int: N rows of Mpad = 32 EPL int32,
 //    16-byte aligned.
 // Entries are packed as (index << 20) | (coefficient & 0xFFFFF).
@@ -72,6 +74,7 @@ struct NetPrep {
     int o_twin = 0, o_keypos = 0, o_keyneg = 0, o_hbits = 0, o_dcols = 0;
     bool narrow = false;                            // M <= kNarrowRows: the sections below exist
     int o_rank = 0, o_keyr = 0, o_hrow = 0, o_colx = 0;
+    int o_fixc = 0, o_fixp = 0;  // wide networks: per-column lane masks of consumed / produced rows (0: none)
     std::vector<int32_t> mptr;  // full S rows over split columns (seeds): [n_met + 1]
     std::vector<uint32_t> ment;  // packed (column, coefficient)
 };
@@ -238,6 +241,26 @@ inline int prepare_network(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr,
             blob.push_back(smax);
             blob.push_back(g == 1 ? 1u : 0u);
         }
+    }
+    // wide networks (not narrow, additive rows): the rows column k consumes
+    // and produces, as lane masks of the expansion's row layout.  Lane l of
+    // a group of G = min(32, 4 EPL) lanes holds the rows 4 (l + G i) + j for
+    // i < 8 EPL / G and j < 4, at bit 4 i + j of its mask word.
+    out.o_fixc = out.o_fixp = 0;
+    if (!out.narrow && !flux_rows) {
+        const int G = std::min(32, 4 * EPL);
+        const int CPL = EPL * 8 / G;
+        out.o_fixc = (int)blob.size();
+        blob.resize(blob.size() + (size_t)2 * N * G, 0u);
+        out.o_fixp = out.o_fixc + N * G;
+        for (int k = 0; k < N; ++k)
+            for (auto &e : col[k]) {
+                const int chunk = e.first / 4, j = e.first % 4;
+                const int l = chunk % G, i = chunk / G;
+                if (i >= CPL) continue;  // unreachable: rows < 32 EPL
+                const int o = (e.second < 0 ? out.o_fixc : out.o_fixp) + k * G + l;
+                blob[o] |= 1u << (4 * i + j);
+            }
     }
     while (blob.size() % 4) blob.push_back(0);
     // dense column-major copy of S_int (row k = column k over Mpad rows)

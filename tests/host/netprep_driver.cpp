@@ -73,6 +73,13 @@ int main()
         }
         std::printf("align64 %d %d\n", p.o_hrow % 2, p.o_colx % 2);
     }
+    std::printf("fixtab %d\n", p.o_fixc > 0 ? 1 : 0);
+    if (p.o_fixc > 0) {
+        const int G = p.EPL >= 8 ? 32 : 4 * p.EPL;
+        for (int k = 0; k < p.N; ++k)
+            for (int l = 0; l < G; ++l)
+                std::printf("fix %d %d %u %u\n", k, l, p.blob[p.o_fixc + k * G + l], p.blob[p.o_fixp + k * G + l]);
+    }
     std::printf("dense_offset_mod4 %d\n", p.o_dcols % 4);
     for (int k = 0; k < p.N; ++k) {
         std::printf("dense %d", k);

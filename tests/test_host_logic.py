@@ -84,6 +84,24 @@ def expected_static(net):
     exp["hbits"] = [(q - 1).bit_length() if q > 1 else 0 for q in nsq]  # ceil(log2(q))
     exp["dense"] = [list(Si[:, k]) + [0] * (32 * epl - M) for k in range(N)]
     exp["met"] = [[(k, int(Ss[m, k])) for k in range(N) if Ss[m, k]] for m in range(net.n_met)]
+    if M > 64:
+        # wide networks: lane masks in the expansion's row layout.  Lane l of a
+        # group of G lanes reads the 4-entry chunks l, l + G, ... of a row, so
+        # bit 4 i + j of its word stands for row 4 (l + G i) + j.
+        G = min(32, 4 * epl)
+        cpl = 8 * epl // G
+        exp["fix"] = []
+        for k in range(N):
+            for lane in range(G):
+                c = p = 0
+                for i in range(cpl):
+                    for j in range(4):
+                        r = 4 * (lane + G * i) + j
+                        if r < M and Si[r, k] < 0:
+                            c |= 1 << (4 * i + j)
+                        if r < M and Si[r, k] > 0:
+                            p |= 1 << (4 * i + j)
+                exp["fix"].append((k, lane, c, p))
     if M <= 64:
         # narrow networks: ranks in the key orders, keys by rank, row hash
         # constants (SplitMix64 finaliser of 0x9E3779B97F4A7C15 (m + 1)), and
@@ -122,14 +140,16 @@ def _pairs(fields):
     return [tuple(int(x) for x in f.split(":")) for f in fields]
 
 
-@pytest.mark.parametrize("which", ["tiny-0", "tiny-5", "core", "batched-7", "type1-3", "mid-40"])
+@pytest.mark.parametrize("which", ["tiny-0", "tiny-5", "core", "batched-7", "type1-3", "mid-40", "wide-150"])
 def test_network_preparation_matches_the_definitions(netprep, which):
     from paper_1804_02867_gb300 import synth
 
     net = {"tiny-0": lambda: synth.tiny(0), "tiny-5": lambda: synth.tiny(5), "core": synth.core,
            "batched-7": lambda: synth.batched_member(7), "type1-3": lambda: synth.type1(3),
            "mid-40": lambda: synth.generate(n_int=40, n_targets=3, n_hubs=2, n_substrates=1, n_rxn=70, n_rev=20,
-                                            coef_probs={1: 0.5, 3: 0.3, 524287: 0.2}, seed=7)}[which]()
+                                            coef_probs={1: 0.5, 3: 0.3, 524287: 0.2}, seed=7),
+           "wide-150": lambda: synth.generate(n_int=150, n_targets=3, n_hubs=4, n_substrates=2, n_rxn=260, n_rev=60,
+                                              seed=9)}[which]()
     status, got = run_netprep(netprep, net.n_met, net.n_rxn, net.row_ptr, net.col_idx, net.coef, net.reversible,
                               net.external)
     assert status == 0
@@ -152,6 +172,9 @@ def test_network_preparation_matches_the_definitions(netprep, which):
         assert [int(f[1]) for f in got["hrow"]] == exp["hrow"]
         assert [tuple(int(x) for x in f[1:]) for f in got["colx"]] == exp["colx"]
         assert got["align64"] == [["0", "0"]]
+    assert got["fixtab"] == [["1" if M > 64 else "0"]]
+    if M > 64:
+        assert [tuple(int(x) for x in f) for f in got["fix"]] == exp["fix"]
     assert [[int(x) for x in f[1:]] for f in got["dense"]] == exp["dense"]
     assert [_pairs(f[1:]) for f in got["met"]] == exp["met"]
 

@@ -229,6 +229,28 @@ def test_first_k_is_prefix_of_full_enumeration(oracle_lib):
                 assert np.array_equal(got, full[:k]), (seed, t, k)
 
 
+def test_budgeted_first_k_is_certified_only_when_exact(oracle_lib):
+    """first_k_within: a certified answer is the k smallest of the complete
+    enumeration; an answer is uncertified exactly when the deepening run it
+    stopped at overflowed the budget somewhere."""
+    seen_uncertified = seen_certified = 0
+    for seed in range(6):
+        net = synth.tiny(seed)
+        for t in list(net.targets) + [-1]:
+            full, _ = oracle_lib.enumerate_pathways(net, t, oracle_lib.Limits(9, 1, 0, 0))
+            for k in (1, 3, 10):
+                for budget in (2, 5, 40):
+                    got, P, ok = oracle_lib.first_k_within(net, t, k, 9, 1, budget)
+                    _, ctr = oracle_lib.enumerate_pathways(net, t, oracle_lib.Limits(P, 1, 0, budget))
+                    assert ok == (not ctr["status"] & oracle_lib.TRUNCATED), (seed, t, k, budget)
+                    if ok:
+                        assert np.array_equal(got, full[:k]), (seed, t, k, budget)
+                        seen_certified += 1
+                    else:
+                        seen_uncertified += 1
+    assert seen_certified > 0 and seen_uncertified > 0
+
+
 def test_splitmix_published_outputs(oracle_lib):
     """The walks' counter-based generator is SplitMix64: from state 0 its
     first outputs are the published 0xe220a8397b1dcdaf, 0x6e789e6aa1b965f4,
