@@ -1697,6 +1697,90 @@ __device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint
                     norm = norm && !dead;
                 }
 
+                // first-K one below the cap: the child's results have support U
+                // or U + {c} for one more column c.  Balance needs both signs in
+                // every row a support touches, and a row that U touches with one
+                // sign only (a surplus with no consumer, a deficit with no
+                // producer in U) is a row EF keeps nonzero under secondary
+                // steps.  With such rows, some column c must give each of them
+                // the missing sign and find the opposite sign in U for every
+                // row of its own (twin rule kept); the group tries the columns
+                // able to fix the one-sided row with the shortest fixer list.
+                if (a.cap_dead && a.child.fx && __any_sync(FULL, norm && pc + (in_u ? 0 : 1) == a.max_len - 1)) {
+                    const bool mine = norm && pc + (in_u ? 0 : 1) == a.max_len - 1;
+                    uint32_t dl = 0;            // this lane's one-sided rows, bits as in fxc / fxp
+                    uint32_t pick = 0xFFFFFFFFu;  // list length << 20 | surplus << 19 | row
+                    if (mine) {
+#pragma unroll
+                        for (int i = 0; i < CPL; ++i)
+#pragma unroll
+                            for (int jj = 0; jj < 4; ++jj) {
+                                const int r = 4 * (gl + G * i) + jj;
+                                const int32_t v = t32[4 * i + jj];
+                                const uint32_t fix = v > 0 ? fxc : fxp;
+                                if (v != 0 && r < nv.M && !((fix >> (4 * i + jj)) & 1u)) {
+                                    dl |= 1u << (4 * i + jj);
+                                    const int lp = (v > 0 ? nv.o_consptr : nv.o_prodptr) + r;
+                                    const uint32_t len = min(bl[lp + 1] - bl[lp], 4095u);
+                                    const uint32_t cand = (len << 20) | (v > 0 ? 1u << 19 : 0u) | (uint32_t)r;
+                                    pick = cand < pick ? cand : pick;
+                                }
+                            }
+                    }
+                    const uint32_t nd = group_add<G>((uint32_t)__popc(dl));
+                    pick = group_min<G>(pick);
+                    bool open = mine && nd > 0;  // still looking for a completing column
+                    const int r0 = (int)(pick & 0x7FFFFu);
+                    const bool sur0 = (pick >> 19) & 1u;
+                    const int lp0 = open ? (sur0 ? nv.o_consptr : nv.o_prodptr) + r0 : 0;
+                    const int b0 = open ? (int)bl[lp0] : 0;
+                    const int n0 = open ? (int)bl[lp0 + 1] - b0 : 0;
+                    const int eo0 = sur0 ? nv.o_consent : nv.o_prodent;
+                    bool found = false;
+                    for (int c0 = 0; __any_sync(FULL, open && c0 < n0); c0 += G) {
+                        const bool act = open && c0 < n0;
+                        const int ci = c0 + gl;
+                        int kc = -1;
+                        if (act && ci < n0) kc = ent_index(bl[eo0 + b0 + ci]);
+                        bool ok2 = kc >= 0;
+                        if (ok2) {
+                            const int tw = (int)bl[nv.o_twin + kc];
+                            ok2 = !(tw >= 0 && (tw == k || ((pu[tw >> 6] >> (tw & 63)) & 1ull)));
+                        }
+                        const int cb = ok2 ? (int)bl[nv.o_colptr + kc] : 0;
+                        const int cn = ok2 ? (int)bl[nv.o_colptr + kc + 1] - cb : 0;
+                        const int cmax = (int)__reduce_max_sync(FULL, (unsigned)cn);
+                        uint32_t hit = 0;  // one-sided rows of U the column fixes
+                        for (int q = 0; q < cmax; ++q) {
+                            int r = 0, sg = 0;
+                            if (q < cn) {
+                                const uint32_t ent = bl[nv.o_colent + cb + q];
+                                r = ent_index(ent);
+                                sg = ent_coef(ent) > 0 ? 1 : -1;
+                            }
+                            const int src = lead + ((r >> 2) % G);
+                            const int bit = 4 * ((r >> 2) / G) + (r & 3);
+                            const uint32_t wc = __shfl_sync(FULL, fxc, src);
+                            const uint32_t wp = __shfl_sync(FULL, fxp, src);
+                            const uint32_t wd = __shfl_sync(FULL, dl, src);
+                            if (q < cn) {
+                                // the column produces r: U must consume it, and the reverse
+                                if (!(((sg > 0 ? wc : wp) >> bit) & 1u)) ok2 = false;
+                                hit += (wd >> bit) & 1u;
+                            }
+                        }
+                        ok2 = ok2 && hit == nd;
+                        const bool any2 = group_or<G>(ok2 ? 1u : 0u) != 0;
+                        if (act && any2) {
+                            found = true;
+                            open = false;
+                        }
+                    }
+                    const bool dead = mine && nd > 0 && !found;
+                    if (dead && gl == 0) ++n_capdead;
+                    norm = norm && !dead;
+                }
+
                 // --- pivot key and fingerprint ---
                 uint32_t key = 0xFFFFFFFFu, hlo = 0, hhi = 0;
                 if (norm) {
