@@ -787,9 +787,11 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
                     out.expand_bytes += state_bytes * (n_par + n_new) + 16.0 * n_child;
                     if (getenv("EFM_DEBUG"))
                         fprintf(stderr,
-                                "efm: level %d parents %lld items %llu children %.0f new %.0f rows %llu bytes %.0f ms %.3f\n",
+                                "efm: level %d parents %lld items %llu children %.0f new %.0f rows %llu settled %llu "
+                                "pruned %llu bytes %.0f ms %.3f\n",
                                 level, (long long)cn, (unsigned long long)(c0 == 0 && chunk >= n_rows ? deg_sum : 0),
-                                n_child, n_new, h[C_WRITTEN], state_bytes * (n_par + n_new) + 16.0 * n_child, ms);
+                                n_child, n_new, h[C_WRITTEN], h[C_SLOW], h[C_PRUNED],
+                                state_bytes * (n_par + n_new) + 16.0 * n_child, ms);
                     exp_before = h[C_EXP];
                     next_before = next_now;
                 }
