@@ -116,10 +116,14 @@ def profile_figure(name, key):
     return float(m_val.group(1))
 
 
-def profile_traffic():
-    """Per-launch DRAM traffic of the core network's expansion kernel at full
-    scale (ncu), or None."""
-    return profile_figure("expand_kernel_core.md", "dram_bytes_per_launch_full_scale")
+def profile_traffic(alg_bytes_per_launch):
+    """Per-launch DRAM traffic of the core network's level pass (generate,
+    settle and dedup kernels of one expansion launch): the DRAM-to-algorithmic
+    ratio ncu measured on a smaller case of the same kernels (traffic grows
+    with the states read and written), applied to this run's algorithmic
+    bytes per launch; None without a summary for the current source."""
+    ratio = profile_figure("level_pass_core.md", "dram_to_algorithmic_ratio")
+    return ratio * alg_bytes_per_launch if ratio else None
 
 
 class ClockSampler:
@@ -355,7 +359,7 @@ def run_ours(args):
         return
     peaks, peak_kind = measured_peaks()
     achieved = (tot_eb / (tot_ems * 1e-3)) / 1e9 if tot_ems > 0 else 0.0
-    traffic = profile_traffic()
+    traffic = profile_traffic(tot_eb / max(tot_el, 1))
     line = {
         "metric": METRIC,
         "value": tot_exp / (tot_ms * 1e-3),
@@ -374,7 +378,7 @@ def run_ours(args):
         "expansions_per_step": tot_exp / args.steps / max(ws, 1),
         "results_per_step": tot_res / args.steps / max(ws, 1),
         "roofline": {
-            "kernel": "expand_kernel<8,2>",
+            "kernel": "level pass: generate_narrow_kernel<8> + settle_kernel<8> + dedup_kernel",
             "bound": "hbm",
             "achieved": achieved,
             "peak": float(peaks["hbm_gbs"]),
@@ -411,7 +415,7 @@ def run_secondary(args):
     b = run_batched(SimpleNamespace(steps=2, warmup=1, jobs=4096))
     out["batched"] = {"jobs": 4096, "ms_per_launch": b["ms_per_step"], "expansions_per_s": b["value"],
                       "sequential_ms": b["sequential"]["ms"], "speedup_vs_sequential": b["speedup_vs_sequential"],
-                      "autotuner": b["autotuner"]}
+                      "untuned_ms": b["untuned_ms"], "tuned_speedup": b["tuned_speedup"], "autotuner": b["autotuner"]}
     g = run_genome(SimpleNamespace(steps=1, warmup=1, jobs=32, budget=BUDGET))
     out["genome"] = {"targets": 32, "max_frontier": GENOME_BUDGET, "expansions_per_s": g["value"],
                      "ms_per_step": g["ms_per_step"], "roofline_frac": g["roofline"]["frac"],
@@ -486,7 +490,7 @@ def run_genome(args):
     achieved = eb / (ems * 1e-3) / 1e9 if ems else 0.0
     # DRAM traffic: the ratio ncu measured on one launch of this kernel,
     # applied to this run's algorithmic bytes per launch
-    ratio = profile_figure("expand_kernel_genome.md", "dram_to_algorithmic_ratio")
+    ratio = profile_figure("level_pass_genome.md", "dram_to_algorithmic_ratio")
     traffic = ratio * eb / el if ratio and el else None
     line = {
         "metric": METRIC, "value": exp / (tot_ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -495,7 +499,7 @@ def run_genome(args):
         "config": {"workload": f"genome-1000x2500 (850 internal, 3125 split columns), {n_t} targets",
                    "max_len": 40, "max_secondary": MAX_SEC, "max_frontier": budget, "support_bits": 3136},
         "balanced_pathways_per_s": res / (tot_ms * 1e-3),
-        "roofline": {"kernel": "expand_kernel<32,7>", "bound": "hbm", "achieved": achieved,
+        "roofline": {"kernel": "level pass: generate_kernel<32,7> + dedup_kernel", "bound": "hbm", "achieved": achieved,
                      "peak": float(peaks["hbm_gbs"]), "unit": "GB/s", "frac": achieved / float(peaks["hbm_gbs"]),
                      "traffic": traffic, "peak_kind": f"{kind} HBM copy bandwidth", "launches": el,
                      "avg_launch_ms": ems / max(el, 1), "alg_bytes_per_launch": eb / max(el, 1)},
@@ -548,6 +552,22 @@ def run_batched(args):
         tot_ms += ev0.elapsed_time(ev1)
         exp += e
         res += r
+    tune = efmgraph.efm_batch_tuning()
+    # the same batch in the untuned launch configuration (8 warps per job,
+    # every CTA an SM holds, input order, tile 32, queue chunk 1)
+    efmgraph.efm_batch_set_tuning(ctas_per_sm=0, largest_first=0, warps_per_job=8, tile=32, queue_chunk=1)
+    try:
+        batch_once()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            batch_once()
+        ev1.record(stream)
+        ev1.synchronize()
+        default_ms = ev0.elapsed_time(ev1) / args.steps
+    finally:
+        efmgraph.efm_batch_set_tuning(None)
     # the same jobs as sequential single-job calls (one pass)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -563,7 +583,6 @@ def run_batched(args):
     seq_ms = ev0.elapsed_time(ev1)
     for h in loaded:
         h.close()
-    tune = efmgraph.efm_batch_tuning()
     value = exp / (tot_ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -576,7 +595,9 @@ def run_batched(args):
         "expansions_per_step": exp / args.steps,
         "sequential": {"ms": seq_ms, "value": seq_exp / (seq_ms * 1e-3), "calls": len(nets)},
         "speedup_vs_sequential": (seq_ms / (tot_ms / args.steps)),
-        "autotuner": {"ctas_per_sm": tune[0], "largest_first": bool(tune[1])} if tune else None,
+        "autotuner": tune,
+        "untuned_ms": default_ms,
+        "tuned_speedup": default_ms / (tot_ms / args.steps),
     }
     return line
 

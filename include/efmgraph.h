@@ -264,9 +264,34 @@ int efm_sample_pathways(efm_net *net, int32_t target, const efm_limits *limits, 
 int efm_find_pathways_batch(efm_net *const *nets, const int32_t *targets, int32_t n_jobs, const efm_limits *limits,
                             const efm_model *model, efm_job **out);
 
-/* The autotuner's last choice: CTAs per SM and whether the queue runs the
- * largest networks first.  EFM_EINVAL before any batch ran. */
-int efm_batch_tuning(int32_t *ctas_per_sm, int32_t *largest_first);
+/* Launch configuration of the batched traversal (no counterpart in the
+ * paper, whose runs are single networks). */
+typedef struct {
+    int32_t ctas_per_sm;     /* persistent CTAs launched per SM, at most what the SM holds; when
+                                pinning, 0 = as many as the SM holds */
+    int32_t largest_first;   /* 1: the queue runs the networks with the most columns x internal
+                                metabolites first; 0: input order */
+    int32_t warps_per_job;   /* warps of the CTA that runs one job: 4 or 8 */
+    int32_t tile;            /* most parents a warp expands per pass, 1..32 */
+    int32_t queue_chunk;     /* queue positions a CTA claims per atomic, 1..64 */
+    int32_t pinned;          /* output only: 1 when efm_batch_set_tuning chose it */
+    float sample_default_ms; /* output only: the tuning sample (up to 256 jobs, strided) in the untuned
+                                configuration (8 warps, every CTA an SM holds, input order, tile 32,
+                                chunk 1); 0 when no search ran */
+    float sample_tuned_ms;   /* output only: the same sample in the chosen configuration */
+} efm_batch_tune;
+
+/* The configuration the last batch ran with.  A batch of at least 64 jobs
+ * whose shape (log2 jobs, largest row class, SM count) has not been seen
+ * times a sample of its jobs: CTAs per SM and queue order, then warps per
+ * job, then the tile, then the queue chunk, each keeping the fastest.
+ * EFM_EINVAL before any batch ran or for a null pointer. */
+int efm_batch_tuning(efm_batch_tune *out);
+
+/* Pin the configuration of later batches (the output-only fields are
+ * ignored), or, with NULL, return to the search.  EFM_EINVAL for a value
+ * outside the ranges above. */
+int efm_batch_set_tuning(const efm_batch_tune *cfg);
 
 /* Copy the results of target number `job_target_idx` (0-based position in
  * the targets array) into `supports` (host memory, capacity rows of W

@@ -1282,9 +1282,18 @@ BatchLayout batch_layout(int64_t cap, int Wmax, int Mpad_max, int Nmax, int max_
     return L;
 }
 
-// Autotuner cache: (log2 jobs, largest row class, SMs) -> (CTAs per SM, largest-first order)
+// Autotuner: a launch configuration of the batched traversal, and its cache
+// keyed by (log2 jobs, largest row class, SMs).  A pinned configuration
+// (efm_batch_set_tuning) replaces the search.
+struct TuneChoice {
+    int per_sm = 1, big = 1, warps = 8, tile = 32, chunk = 1;
+    float default_ms = 0.f, best_ms = 0.f;  // the sample's time: untuned and chosen configuration
+};
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune;
+std::map<std::tuple<int, int, int>, TuneChoice> g_tune;
+TuneChoice g_last;
+bool g_have_last = false, g_pinned = false;
+TuneChoice g_pin;
 
 }  // namespace
 
@@ -1312,7 +1321,8 @@ extern "C" int efm_find_pathways_batch(efm_net *const *nets, const int32_t *targ
     efm_net *net0 = nets[0];
     cudaStream_t s = net0->stream;
     const BatchLayout L = batch_layout(lim.max_frontier + 1, Wmax, Mpad_max, Nmax, Lmax);
-    const int occ = batch_blocks_per_sm();
+    const int occ8 = batch_blocks_per_sm(8), occ4 = batch_blocks_per_sm(4);
+    const int occ = std::max(occ8, occ4);  // slices for the largest grid any configuration launches
     const int sms = net0->sm_count;
 
     auto *job = new (std::nothrow) efm_job();
@@ -1330,7 +1340,7 @@ extern "C" int efm_find_pathways_batch(efm_net *const *nets, const int32_t *targ
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     float ms = 0.f;
-    int best_per_sm = 1, best_big = 1;
+    TuneChoice best;
     BatchArgs ba{};
 
     if (!dev_alloc(pool, (size_t)sms * occ * L.slice_bytes, s) ||
@@ -1369,55 +1379,111 @@ extern "C" int efm_find_pathways_batch(efm_net *const *nets, const int32_t *targ
     ba.max_frontier = lim.max_frontier;
     ba.max_results = lim.max_results;
     {
-        // autotune (CTAs per SM, queue order) on a sample of the jobs, cached per shape
+        // autotune on a sample of the jobs, cached per shape: CTAs per SM and
+        // the queue order, then warps per job, then the parents a warp takes
+        // per pass, then the queue positions a CTA claims at a time
         int lg = 0;
         while ((1 << lg) < n_jobs) ++lg;
         const auto key = std::make_tuple(lg, max_epl, sms);
         bool have = false;
         {
             std::lock_guard<std::mutex> lock(g_tune_mu);
-            auto it = g_tune.find(key);
-            if (it != g_tune.end()) {
-                best_per_sm = it->second.first;
-                best_big = it->second.second;
+            if (g_pinned) {
+                best = g_pin;
+                if (best.per_sm == 0) best.per_sm = best.warps == 8 ? occ8 : occ4;  // every CTA the SM holds
                 have = true;
+            } else {
+                auto it = g_tune.find(key);
+                if (it != g_tune.end()) {
+                    best = it->second;
+                    have = true;
+                }
             }
         }
         if (!have && n_jobs >= 64) {
             const int sample = std::min(n_jobs, 256);
-            float best = 1e30f;
-            for (int big = 0; big < 2 && rc == EFM_OK; ++big) {
-                const std::vector<int> &ord = big ? order_big : order_in;
+            auto time_cfg = [&](const TuneChoice &c, float &t) -> bool {
+                const std::vector<int> &ord = c.big ? order_big : order_in;
                 // a strided sample keeps the size mix of the whole batch
                 std::vector<int> samp(sample);
                 for (int i = 0; i < sample; ++i) samp[i] = ord[(size_t)i * n_jobs / sample];
-                for (int per_sm = 1; per_sm <= occ && rc == EFM_OK; ++per_sm) {
-                    ba.n_jobs = sample;
-                    if (cudaMemcpyAsync(dorder.p, samp.data(), 4 * sample, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-                        cudaMemsetAsync(dctr.p, 0, 8 * (size_t)C_COUNT * n_jobs, s) != cudaSuccess ||
-                        cudaMemsetAsync(dqueue.p, 0, 16, s) != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess ||
-                        launch_batch(ba, sms * per_sm, s) != cudaSuccess || cudaEventRecord(e1, s) != cudaSuccess ||
-                        cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-                        if (getenv("EFM_DEBUG"))
-                            fprintf(stderr, "efm: batch tuning run failed: %s\n", cudaGetErrorString(cudaGetLastError()));
-                        rc = EFM_ECUDA;
-                        break;
-                    }
-                    if (ms < best) {
-                        best = ms;
-                        best_per_sm = per_sm;
-                        best_big = big;
-                    }
+                ba.n_jobs = sample;
+                ba.tile = c.tile;
+                ba.chunk = c.chunk;
+                if (cudaMemcpyAsync(dorder.p, samp.data(), 4 * sample, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                    cudaMemsetAsync(dctr.p, 0, 8 * (size_t)C_COUNT * n_jobs, s) != cudaSuccess ||
+                    cudaMemsetAsync(dqueue.p, 0, 16, s) != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess ||
+                    launch_batch(ba, sms * c.per_sm, c.warps, s) != cudaSuccess || cudaEventRecord(e1, s) != cudaSuccess ||
+                    cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+                    if (getenv("EFM_DEBUG"))
+                        fprintf(stderr, "efm: batch tuning run failed: %s\n", cudaGetErrorString(cudaGetLastError()));
+                    return false;
                 }
+                if (getenv("EFM_DEBUG"))
+                    fprintf(stderr, "efm: tune per_sm %d big %d warps %d tile %d chunk %d: %.3f ms\n", c.per_sm, c.big,
+                            c.warps, c.tile, c.chunk, t);
+                return true;
+            };
+            // the untuned configuration: 8 warps, every CTA the SM holds, queue in input order
+            TuneChoice cur;
+            cur.per_sm = occ8;
+            cur.big = 0;
+            float t = 0.f, best_t = 0.f;
+            bool ok = time_cfg(cur, t);
+            best = cur;
+            best_t = t;
+            const float def_t = t;
+            auto consider = [&](const TuneChoice &c) {
+                if (ok && (ok = time_cfg(c, t)) && t < best_t) {
+                    best = c;
+                    best_t = t;
+                }
+            };
+            for (int big = 0; big < 2; ++big)
+                for (int per_sm = 1; per_sm <= occ8; ++per_sm) {
+                    cur = best;
+                    cur.big = big;
+                    cur.per_sm = per_sm;
+                    cur.warps = 8;
+                    if (!(big == 0 && per_sm == occ8)) consider(cur);
+                }
+            for (int per_sm = 1; per_sm <= occ4; ++per_sm) {
+                cur = best;
+                cur.warps = 4;
+                cur.per_sm = per_sm;
+                consider(cur);
             }
+            for (int tile : {8, 16}) {
+                cur = best;
+                cur.tile = tile;
+                consider(cur);
+            }
+            for (int chunk : {2, 4}) {
+                cur = best;
+                cur.chunk = chunk;
+                consider(cur);
+            }
+            if (!ok) {
+                rc = EFM_ECUDA;
+            } else {
+                best.default_ms = def_t;
+                best.best_ms = best_t;
+                std::lock_guard<std::mutex> lock(g_tune_mu);
+                g_tune[key] = best;
+            }
+        }
+        if (rc == EFM_OK) {
             std::lock_guard<std::mutex> lock(g_tune_mu);
-            g_tune[key] = std::make_pair(best_per_sm, best_big);
+            g_last = best;
+            g_have_last = true;
         }
     }
     if (rc != EFM_OK) goto done;
     // the batch: one persistent launch, captured in a CUDA graph with its resets
     ba.n_jobs = n_jobs;
-    if (cudaMemcpyAsync(dorder.p, (best_big ? order_big : order_in).data(), 4 * (size_t)n_jobs,
+    ba.tile = best.tile;
+    ba.chunk = best.chunk;
+    if (cudaMemcpyAsync(dorder.p, (best.big ? order_big : order_in).data(), 4 * (size_t)n_jobs,
                         cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         rc = EFM_ECUDA;
@@ -1435,7 +1501,7 @@ extern "C" int efm_find_pathways_batch(efm_net *const *nets, const int32_t *targ
         if (ok) {
             ok = cudaMemsetAsync(dctr.p, 0, 8 * (size_t)C_COUNT * n_jobs, cs) == cudaSuccess &&
                  cudaMemsetAsync(dqueue.p, 0, 16, cs) == cudaSuccess &&
-                 launch_batch(ba, sms * best_per_sm, cs) == cudaSuccess;
+                 launch_batch(ba, sms * best.per_sm, best.warps, cs) == cudaSuccess;
             ok = (cudaStreamEndCapture(cs, &graph) == cudaSuccess) && ok;
         }
         ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
@@ -1499,13 +1565,42 @@ done:
     return flags;
 }
 
-extern "C" int efm_batch_tuning(int32_t *ctas_per_sm, int32_t *largest_first)
+extern "C" int efm_batch_tuning(efm_batch_tune *out)
 {
+    if (!out) return EFM_EINVAL;
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    if (g_tune.empty()) return EFM_EINVAL;
-    const auto &v = g_tune.rbegin()->second;
-    if (ctas_per_sm) *ctas_per_sm = v.first;
-    if (largest_first) *largest_first = v.second;
+    if (!g_have_last) return EFM_EINVAL;
+    const TuneChoice &v = g_last;
+    out->ctas_per_sm = v.per_sm;
+    out->largest_first = v.big;
+    out->warps_per_job = v.warps;
+    out->tile = v.tile;
+    out->queue_chunk = v.chunk;
+    out->pinned = g_pinned ? 1 : 0;
+    out->sample_default_ms = v.default_ms;
+    out->sample_tuned_ms = v.best_ms;
+    return EFM_OK;
+}
+
+extern "C" int efm_batch_set_tuning(const efm_batch_tune *cfg)
+{
+    if (!cfg) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_pinned = false;
+        return EFM_OK;
+    }
+    if ((cfg->warps_per_job != 4 && cfg->warps_per_job != 8) || cfg->largest_first < 0 || cfg->largest_first > 1 ||
+        cfg->tile < 1 || cfg->tile > 32 || cfg->queue_chunk < 1 || cfg->queue_chunk > 64 || cfg->ctas_per_sm < 0)
+        return EFM_EINVAL;
+    if (cfg->ctas_per_sm > batch_blocks_per_sm(cfg->warps_per_job)) return EFM_EINVAL;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_pin = TuneChoice{};
+    g_pin.per_sm = cfg->ctas_per_sm;
+    g_pin.big = cfg->largest_first;
+    g_pin.warps = cfg->warps_per_job;
+    g_pin.tile = cfg->tile;
+    g_pin.chunk = cfg->queue_chunk;
+    g_pinned = true;
     return EFM_OK;
 }
 

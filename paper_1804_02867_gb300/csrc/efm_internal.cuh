@@ -198,6 +198,8 @@ struct BatchArgs {
     BatchLayout layout;
     int max_sec;
     int64_t max_frontier, max_results;
+    int tile;                 // most parents a warp takes per pass (1..32)
+    int chunk;                // queue positions a CTA claims at a time (>= 1)
 };
 
 // Learned proposal: MLP 128 -> 256 (ReLU) -> 1.  FP32 parameters in one
@@ -282,8 +284,9 @@ cudaError_t launch_flux(const NetView &nv, const uint64_t *sup, int64_t n, int64
                         cudaStream_t s);
 cudaError_t launch_walks(const NetView &nv, const LevelArgs &a, int target, uint64_t seed, int64_t n_walks, int sm_count,
                          cudaStream_t s);
-cudaError_t launch_batch(const BatchArgs &ba, int grid, cudaStream_t s);
-int batch_blocks_per_sm();
-size_t batch_smem_bytes();
+// the batched traversal runs `warps` warps per CTA (4 or 8), one job at a time
+cudaError_t launch_batch(const BatchArgs &ba, int grid, int warps, cudaStream_t s);
+int batch_blocks_per_sm(int warps);
+size_t batch_smem_bytes(int warps);
 
 }  // namespace efm

@@ -1962,15 +1962,7 @@ __device__ void generate_narrow(const NetView &nv, const LevelArgs &a, const uin
         const int64_t pl = p0 + lane;
         const bool pin = lane < cpw && pl < a.n_par;
         const int64_t pid = pin ? (a.perm ? (int64_t)a.perm[pl] : a.par_base + pl) : 0;
-        const int64_t pn = pl + wstride;
-        if (lane < cpw && pn < a.n_par) {
-            const int64_t nid = a.perm ? (int64_t)a.perm[pn] : a.par_base + pn;
-            const char *rp = reinterpret_cast<const char *>(a.par.B + (size_t)nid * Mpad);
-            for (int off = 0; off < Mpad * 4; off += 128) prefetch_l2(rp + off);
-            prefetch_l2(a.par.U + (size_t)nid * W);
-            prefetch_l2(a.par.meta + nid);
-            prefetch_l2(a.par.sum + (size_t)nid * kSumWords);
-        }
+        // (no L2 prefetch of the next chunk's parents: measured slower here)
         const uint32_t mj = pin ? a.par.meta[pid] : 0u;
         int dj = pin ? (int)((mj >> 10) & 0x1FFFu) : 0;
         if (a.fk_pc > 0 && (int)((mj >> 23) & 0x7Fu) > a.fk_pc) dj = 0;
@@ -3259,7 +3251,7 @@ __device__ void run_job(const BatchArgs &ba, const BatchJob &job, char *slice, u
         a.child = arena(cur ^ 1);
         a.slot_mask = nslots - 1;
         a.level = level;
-        a.cpw = (int)min((int64_t)32, max((int64_t)1, (n_front + nwarps - 1) / nwarps));
+        a.cpw = (int)min((int64_t)ba.tile, max((int64_t)1, (n_front + nwarps - 1) / nwarps));
         expand_range<G, CPL>(nv, a, nv.blob, reinterpret_cast<char *>(sm) + (size_t)wid * BatchShape<G, CPL>::BYTES,
                              wid, nwarps);
         read_ctr();
@@ -3306,23 +3298,26 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(BatchArgs ba)
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ int s_job;
     char *slice = ba.pool + (size_t)blockIdx.x * ba.layout.slice_bytes;
+    const int chunk = ba.chunk > 0 ? ba.chunk : 1;
     for (;;) {
-        if (threadIdx.x == 0) s_job = (int)atomicAdd(ba.queue, 1u);
+        if (threadIdx.x == 0) s_job = (int)atomicAdd(ba.queue, (unsigned)chunk);
         __syncthreads();
-        const int qi = s_job;
+        const int q0 = s_job;
         __syncthreads();
-        if (qi >= ba.n_jobs) break;
-        const BatchJob &job = ba.jobs[ba.order[qi]];
-        switch (job.nv.EPL) {
-        case 1: run_job<4, 2>(ba, job, slice, smem); break;
-        case 2: run_job<8, 2>(ba, job, slice, smem); break;
-        case 4: run_job<16, 2>(ba, job, slice, smem); break;
-        case 8: run_job<32, 2>(ba, job, slice, smem); break;
-        default:
-            if (threadIdx.x == 0) atomicOr(&job.ctr[C_ERR], (unsigned long long)ERR_LEN);
-            break;
+        if (q0 >= ba.n_jobs) break;
+        for (int qi = q0; qi < q0 + chunk && qi < ba.n_jobs; ++qi) {
+            const BatchJob &job = ba.jobs[ba.order[qi]];
+            switch (job.nv.EPL) {
+            case 1: run_job<4, 2>(ba, job, slice, smem); break;
+            case 2: run_job<8, 2>(ba, job, slice, smem); break;
+            case 4: run_job<16, 2>(ba, job, slice, smem); break;
+            case 8: run_job<32, 2>(ba, job, slice, smem); break;
+            default:
+                if (threadIdx.x == 0) atomicOr(&job.ctr[C_ERR], (unsigned long long)ERR_LEN);
+                break;
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
@@ -3660,12 +3655,12 @@ cudaError_t launch_sort_results(const uint64_t *res, int64_t n, int W, uint32_t 
     return cudaGetLastError();
 }
 
-int batch_blocks_per_sm()
+int batch_blocks_per_sm(int warps)
 {
     int per_sm = 0;
-    const size_t sm = batch_smem_bytes();
-    cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBatchThreads, sm) != cudaSuccess ||
+    const size_t sm = batch_smem_bytes(warps);
+    cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes(kBatchThreads / 32));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, warps * 32, sm) != cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
@@ -3673,7 +3668,7 @@ int batch_blocks_per_sm()
     return per_sm;
 }
 
-size_t batch_smem_bytes()
+size_t batch_smem_bytes(int warps)
 {
     // union of the expansion batches of all warps (largest row class) and the
     // minimality scratch of kAcceptWarps warps
@@ -3681,16 +3676,17 @@ size_t batch_smem_bytes()
     ex = ex > (size_t)BatchShape<8, 2>::BYTES ? ex : (size_t)BatchShape<8, 2>::BYTES;
     ex = ex > (size_t)BatchShape<16, 2>::BYTES ? ex : (size_t)BatchShape<16, 2>::BYTES;
     ex = ex > (size_t)BatchShape<32, 2>::BYTES ? ex : (size_t)BatchShape<32, 2>::BYTES;
-    ex *= (size_t)(kBatchThreads / 32);
+    ex *= (size_t)warps;
     const size_t ac = (size_t)kAcceptWarps * kAcceptWarpWords * 4;
     return ex > ac ? ex : ac;
 }
 
-cudaError_t launch_batch(const BatchArgs &ba, int grid, cudaStream_t s)
+cudaError_t launch_batch(const BatchArgs &ba, int grid, int warps, cudaStream_t s)
 {
-    const size_t sm = batch_smem_bytes();
-    cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    batch_kernel<<<grid, kBatchThreads, sm, s>>>(ba);
+    if (warps < kAcceptWarps || warps > kBatchThreads / 32) return cudaErrorInvalidValue;
+    const size_t sm = batch_smem_bytes(warps);
+    cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes(kBatchThreads / 32));
+    batch_kernel<<<grid, warps * 32, sm, s>>>(ba);
     return cudaGetLastError();
 }
 

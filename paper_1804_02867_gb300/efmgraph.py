@@ -21,13 +21,20 @@ COUNTER_FIELDS = ("levels", "seeds", "expansions", "overflow", "balanced", "cand
                   "frontier", "frontier_max", "status", "zero_flux")
 EXPORTS = ("efm_load_network", "efm_network_shape", "efm_column_map", "efm_find_pathways", "efm_fetch_results",
            "efm_job_timing", "efm_free_job", "efm_free_net", "efm_status_str", "efm_set_allocator",
-           "efm_sort_supports_noalloc", "efm_find_pathways_batch", "efm_batch_tuning", "efm_model_create",
+           "efm_sort_supports_noalloc", "efm_find_pathways_batch", "efm_batch_tuning", "efm_batch_set_tuning",
+           "efm_model_create",
            "efm_model_params", "efm_model_add_rows", "efm_model_rows", "efm_model_clear_rows", "efm_model_forward",
            "efm_model_gradient", "efm_model_train", "efm_model_trace", "efm_model_free", "efm_sample_pathways",
            "efm_flux_vectors", "efm_find_pathways_from", "efm_dependent_reactions", "efm_check_bounded_wait")
 EFM_NOALLOC_MAX_ROWS = 1 << 20
 EFM_MLP_FEATURES, EFM_MLP_HIDDEN = 128, 256
 EFM_MLP_PARAMS = 256 * 128 + 256 + 1
+
+
+class efm_batch_tune(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_int32), ("largest_first", ctypes.c_int32), ("warps_per_job", ctypes.c_int32),
+                ("tile", ctypes.c_int32), ("queue_chunk", ctypes.c_int32), ("pinned", ctypes.c_int32),
+                ("sample_default_ms", ctypes.c_float), ("sample_tuned_ms", ctypes.c_float)]
 
 
 class efm_limits(ctypes.Structure):
@@ -95,8 +102,10 @@ def load_library(path: str | None = None):
     lib.efm_find_pathways_batch.argtypes = [_P(ctypes.c_void_p), _P(ctypes.c_int32), ctypes.c_int32, _P(efm_limits),
                                             ctypes.c_void_p, _P(ctypes.c_void_p)]
     lib.efm_find_pathways_batch.restype = ctypes.c_int
-    lib.efm_batch_tuning.argtypes = [_P(ctypes.c_int32), _P(ctypes.c_int32)]
+    lib.efm_batch_tuning.argtypes = [_P(efm_batch_tune)]
     lib.efm_batch_tuning.restype = ctypes.c_int
+    lib.efm_batch_set_tuning.argtypes = [_P(efm_batch_tune)]
+    lib.efm_batch_set_tuning.restype = ctypes.c_int
     F = _P(ctypes.c_float)
     lib.efm_model_create.argtypes = [ctypes.c_uint64, ctypes.c_size_t, _P(ctypes.c_void_p)]
     lib.efm_model_params.argtypes = [ctypes.c_void_p, F, ctypes.c_int32]
@@ -315,10 +324,30 @@ def efm_find_pathways_batch(nets, targets, max_len, max_secondary, max_results=0
     return job.value, rc
 
 
+TUNE_FIELDS = ("ctas_per_sm", "largest_first", "warps_per_job", "tile", "queue_chunk", "pinned", "sample_default_ms",
+               "sample_tuned_ms")
+
+
 def efm_batch_tuning():
-    a, b = ctypes.c_int32(), ctypes.c_int32()
-    rc = load_library().efm_batch_tuning(ctypes.byref(a), ctypes.byref(b))
-    return (a.value, b.value) if rc == 0 else None
+    """The configuration the last batch ran with, as a dict (None before any)."""
+    t = efm_batch_tune()
+    rc = load_library().efm_batch_tuning(ctypes.byref(t))
+    return {f: getattr(t, f) for f in TUNE_FIELDS} if rc == 0 else None
+
+
+def efm_batch_set_tuning(cfg=None, **kw):
+    """Pin the batched launch configuration (ctas_per_sm, largest_first,
+    warps_per_job, tile, queue_chunk), or return to the search with None."""
+    if cfg is None and not kw:
+        rc = load_library().efm_batch_set_tuning(None)
+    else:
+        t = efm_batch_tune()
+        for f, v in {**(cfg or {}), **kw}.items():
+            if f in TUNE_FIELDS[:5]:
+                setattr(t, f, int(v))
+        rc = load_library().efm_batch_set_tuning(ctypes.byref(t))
+    if rc < 0:
+        raise EfmError(rc, "efm_batch_set_tuning")
 
 
 def efm_fetch_results(job, idx, copy=True, out=None):

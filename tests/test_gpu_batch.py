@@ -60,10 +60,46 @@ def test_batch_matches_single_job_path(efm):
 
 
 def test_batch_autotuner_reports_choice(efm):
+    efm.efm_batch_set_tuning(None)
     nets = [synth.batched_member(2000 + i) for i in range(80)]
     _batch(efm, nets, 20, 2, 2**9)
-    tune = efm.efm_batch_tuning()
-    assert tune is not None and tune[0] >= 1 and tune[1] in (0, 1)
+    t = efm.efm_batch_tuning()
+    assert t is not None and t["ctas_per_sm"] >= 1 and t["largest_first"] in (0, 1) and t["pinned"] == 0
+    assert t["warps_per_job"] in (4, 8) and 1 <= t["tile"] <= 32 and t["queue_chunk"] >= 1
+    # the search keeps the untuned configuration unless something beat it
+    assert 0 < t["sample_tuned_ms"] <= t["sample_default_ms"]
+
+
+@pytest.mark.parametrize("cfg", [dict(ctas_per_sm=0, largest_first=0, warps_per_job=8, tile=32, queue_chunk=1),
+                                 dict(ctas_per_sm=1, largest_first=1, warps_per_job=4, tile=8, queue_chunk=4),
+                                 dict(ctas_per_sm=0, largest_first=1, warps_per_job=4, tile=1, queue_chunk=3),
+                                 dict(ctas_per_sm=2, largest_first=0, warps_per_job=8, tile=16, queue_chunk=64)])
+def test_every_launch_configuration_gives_the_oracle_answers(oracle_lib, efm, cfg):
+    """The autotuner's search space (CTAs per SM, queue order, warps per job,
+    tile, queue chunk) changes only the schedule: pinned to any point of it,
+    the batch gives the oracle's supports and counters."""
+    nets = [synth.batched_member(4000 + i) for i in range(70)] + [synth.tiny(i) for i in range(4)]
+    efm.efm_batch_set_tuning(cfg)
+    try:
+        got = _batch(efm, nets, 30, 4, 2**10)
+        t = efm.efm_batch_tuning()
+        assert t["pinned"] == 1 and t["warps_per_job"] == cfg["warps_per_job"] and t["tile"] == cfg["tile"]
+    finally:
+        efm.efm_batch_set_tuning(None)
+    for net, (sup, ctr) in zip(nets, got):
+        L = min(30, net.split_columns())
+        osup, octr = oracle_lib.enumerate_pathways(net, net.targets[0], oracle_lib.Limits(L, 4, 0, 2**10))
+        assert np.array_equal(sup, osup), net.name
+        assert ctr == octr, (net.name, ctr, octr)
+
+
+def test_tuning_pin_is_validated(efm):
+    for bad in (dict(warps_per_job=6), dict(tile=0), dict(tile=33), dict(queue_chunk=0), dict(largest_first=2),
+                dict(ctas_per_sm=-1), dict(ctas_per_sm=10_000)):
+        cfg = dict(ctas_per_sm=1, largest_first=0, warps_per_job=8, tile=32, queue_chunk=1, **{})
+        cfg.update(bad)
+        with pytest.raises(efm.EfmError):
+            efm.efm_batch_set_tuning(cfg)
 
 
 def wide_member(i):
