@@ -244,7 +244,6 @@ size_t mlp_train_smem();
 
 // kernels (efm_kernels.cu)
 cudaError_t launch_seed(const NetView &nv, const LevelArgs &a, int target, cudaStream_t s);
-cudaError_t launch_expand(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s);
 // generate/dedup split of one expansion: children with rows and fingerprints,
 // then one pass that keeps the first row of every distinct state
 cudaError_t launch_generate(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s);
@@ -270,7 +269,6 @@ cudaError_t launch_sentinel_index(const NetView &nv, const uint64_t *res, int64_
                                   uint32_t *csingle, cudaStream_t s);
 cudaError_t launch_sort_results(const uint64_t *res, int64_t n, int W, uint32_t *idx, int64_t n_pow2,
                                 uint64_t *out, int64_t n_keep, cudaStream_t s);
-int expand_grid(const NetView &nv, int sm_count);
 cudaError_t launch_iota(uint32_t *perm, int64_t n, cudaStream_t s);
 cudaError_t launch_seedset(const NetView &nv, const LevelArgs &a, const int32_t *cols, int n_cols, cudaStream_t s);
 cudaError_t launch_step_count(const NetView &nv, unsigned *r, cudaStream_t s);

@@ -1370,18 +1370,6 @@ __device__ void expand_range(const NetView &nv, const LevelArgs &a, const uint32
     if (deg_sum) atomicAdd(&a.ctr[C_DEGSUM], deg_sum);
 }
 
-template <int G, int CPL>
-__global__ void __launch_bounds__(kExpandWarps * 32, (CPL <= 2 ? 3 : 2)) expand_kernel(NetView nv, LevelArgs a, int staged)
-{
-    extern __shared__ __align__(16) uint32_t smem[];
-    const int wid = threadIdx.x >> 5;
-    const int blob_words = staged ? nv.blob_words : 0;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + blob_words);
-    char *wbase = reinterpret_cast<char *>(smem + blob_words + 4) + (size_t)wid * BatchShape<G, CPL>::BYTES;
-    const uint32_t *bl = stage_blob(nv, smem, mbar, staged != 0, a.ctr);
-    if (bl == nullptr) return;
-    expand_range<G, CPL>(nv, a, bl, wbase, (int64_t)blockIdx.x * kExpandWarps + wid, (int64_t)gridDim.x * kExpandWarps);
-}
 
 // ---------------------------------------------------------------------------
 // a1-a5 as two passes (single-job traversal): generate, then deduplicate.
@@ -3331,20 +3319,6 @@ cudaError_t launch_seed_t(const NetView &nv, const LevelArgs &a, int target, cud
     return cudaGetLastError();
 }
 
-template <int G, int CPL>
-cudaError_t launch_expand_t(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s)
-{
-    const bool staged = nv.blob_words * 4 <= kStageLimitBytes;
-    const size_t sm = (size_t)(staged ? nv.blob_words : 0) * 4 + 16 + (size_t)kExpandWarps * BatchShape<G, CPL>::BYTES;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(expand_kernel<G, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kStageLimitBytes + 16 + kExpandWarps * BatchShape<G, CPL>::BYTES);
-        attr_set = true;
-    }
-    expand_kernel<G, CPL><<<grid, kExpandWarps * 32, sm, s>>>(nv, a, staged ? 1 : 0);
-    return cudaGetLastError();
-}
 
 // The narrow kernel reads the static network through L1 rather than staging
 // it: at four blocks per SM a staged copy per block would take shared memory
@@ -3413,22 +3387,6 @@ int generate_grid_t(const NetView &nv, int sm_count)
     return sm_count * per_sm;
 }
 
-template <int G, int CPL>
-int expand_grid_t(const NetView &nv, int sm_count)
-{
-    const bool staged = nv.blob_words * 4 <= kStageLimitBytes;
-    const size_t sm = (size_t)(staged ? nv.blob_words : 0) * 4 + 16 + (size_t)kExpandWarps * BatchShape<G, CPL>::BYTES;
-    cudaFuncSetAttribute(expand_kernel<G, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kStageLimitBytes + 16 + kExpandWarps * BatchShape<G, CPL>::BYTES);
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expand_kernel<G, CPL>, kExpandWarps * 32, sm) !=
-            cudaSuccess ||
-        per_sm < 1) {
-        cudaGetLastError();
-        per_sm = 1;
-    }
-    return sm_count * per_sm;
-}
 
 }  // namespace
 
@@ -3464,13 +3422,6 @@ cudaError_t launch_seed(const NetView &nv, const LevelArgs &a, int target, cudaS
     default: break;                    \
     }
 
-cudaError_t launch_expand(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s)
-{
-#define CALL_EXP(G, C) launch_expand_t<G, C>(nv, a, grid, s)
-    EFM_GROUP_DISPATCH(nv.EPL, CALL_EXP)
-#undef CALL_EXP
-    return cudaErrorInvalidValue;
-}
 
 cudaError_t launch_generate(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s)
 {
@@ -3521,14 +3472,6 @@ cudaError_t launch_dedup(const LevelArgs &a, int Mpad, int W, int sm_count, cuda
     return cudaGetLastError();
 }
 
-int expand_grid(const NetView &nv, int sm_count)
-{
-    // persistent grid: as many CTAs as can be resident (grid-stride inside)
-#define CALL_GRID(G, C) expand_grid_t<G, C>(nv, sm_count)
-    EFM_GROUP_DISPATCH(nv.EPL, CALL_GRID)
-#undef CALL_GRID
-    return sm_count;
-}
 
 cudaError_t launch_accept_new(const NetView &nv, const AcceptArgs &a, int sm_count, cudaStream_t s)
 {
