@@ -18,7 +18,8 @@ firstk   first-K = 1000 on FIRSTK_TARGETS of the genome network, max_len 40,
          max_secondary 4, by the oracle's deepening under GENOME_BUDGET (the
          complete levels of a genome traversal do not fit the host); a record
          is the definition's answer only where "certified" is true
-Records already present are kept unless their section is named again.
+Records already present are kept unless their section is named again
+(first-K records of targets already computed at the same budget are kept).
 """
 from __future__ import annotations
 
@@ -39,7 +40,7 @@ GENOME_BUDGET = 2**20
 GENOME_TARGETS = 32
 BATCH_BUDGET = 2**12
 FIRSTK = 1000
-FIRSTK_TARGETS = tuple(range(32))  # positions in the genome network's target list
+FIRSTK_TARGETS = tuple(range(80))  # positions in the genome network's target list
 
 
 def digest(supports) -> str:
@@ -131,8 +132,13 @@ def main(argv):
         json.dump(rec, open(OUT, "w"), indent=1)
         print("batched done", flush=True)
     if "firstk" in sections:
+        net = synth.genome()
+        have = {r["target"]: r for r in rec.get("firstk", []) if r.get("max_frontier") == GENOME_BUDGET}
+        todo = [p for p in FIRSTK_TARGETS if int(net.targets[p]) not in have]
         with ctx.Pool(min(threads, 2)) as pool:  # ~14 GB of host memory per traversal
-            rec["firstk"] = pool.map(_firstk_one, list(FIRSTK_TARGETS))
+            new = pool.map(_firstk_one, todo)
+        order = {int(net.targets[p]): i for i, p in enumerate(FIRSTK_TARGETS)}
+        rec["firstk"] = sorted(list(have.values()) + new, key=lambda r: order.get(r["target"], len(order)))
         json.dump(rec, open(OUT, "w"), indent=1)
         print("firstk done", flush=True)
 
