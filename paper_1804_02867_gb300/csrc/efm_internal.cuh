@@ -17,6 +17,7 @@ constexpr uint32_t kPending = 0xFFFFFFFFu;
 constexpr uint32_t kOverflowIdx = 0xFFFFFFFEu;
 constexpr int kNumPrimes = 24;
 constexpr int kStageLimitBytes = 72 * 1024;  // static network staged in smem up to this size
+constexpr int kStageSparseLimitBytes = 100 * 1024;  // generic kernel: its sparse tables staged up to this size
 constexpr int64_t kFirstKChunkMin = 8192;     // first-K search: fewest parents per expansion launch
 constexpr int64_t kFirstKChunks = 32;         // first-K search: launches per level, at most
 constexpr int64_t kResultWindow = 256;        // first-K search: new results fetched with the counters

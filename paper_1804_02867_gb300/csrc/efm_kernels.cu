@@ -130,11 +130,22 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p)
 
 // Returns the blob pointer to use (shared if staged, else global).  On a
 // wait that does not finish, flags ERR_TIMEOUT and returns nullptr.
+__device__ const uint32_t *stage_words(const NetView &nv, uint32_t *sblob, uint64_t *mbar, int w0, int nwords,
+                                       unsigned long long *ctr);
+
 __device__ const uint32_t *stage_blob(const NetView &nv, uint32_t *sblob, uint64_t *mbar, bool staged,
                                       unsigned long long *ctr)
 {
     if (!staged) return nv.blob;
-    const uint32_t bytes = (uint32_t)nv.blob_words * 4u;
+    return stage_words(nv, sblob, mbar, 0, nv.blob_words, ctr);
+}
+
+// words [w0, w0 + nwords) of the blob into shared memory (w0 and nwords
+// multiples of 4: 16-byte aligned bulk copies), one mbarrier, bounded wait
+__device__ const uint32_t *stage_words(const NetView &nv, uint32_t *sblob, uint64_t *mbar, int w0, int nwords,
+                                       unsigned long long *ctr)
+{
+    const uint32_t bytes = (uint32_t)nwords * 4u;
     const uint32_t bar = smem_addr(mbar);
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1) : "memory");
@@ -149,7 +160,7 @@ __device__ const uint32_t *stage_blob(const NetView &nv, uint32_t *sblob, uint64
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                     smem_addr(sblob) + off),
-                "l"((const char *)nv.blob + off), "r"(n), "r"(bar)
+                "l"((const char *)(nv.blob + w0) + off), "r"(n), "r"(bar)
                 : "memory");
         }
     }
@@ -1392,7 +1403,8 @@ __device__ void expand_range(const NetView &nv, const LevelArgs &a, const uint32
 // ---------------------------------------------------------------------------
 
 template <int G, int CPL>
-__device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint32_t *bl, int64_t worker,
+__device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint32_t *bl, const uint32_t *blg,
+                               int64_t worker,
                                int64_t nworkers)
 {
     constexpr int NG = 32 / G;    // children per warp round
@@ -1403,7 +1415,9 @@ __device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint
     const int lead = gi * G;  // group leader lane
     const int W = nv.W;
     const int Mpad = nv.Mpad;
-    const int4 *dcol = reinterpret_cast<const int4 *>(bl + nv.o_dcols);
+    // bl: the static network (its sparse tables possibly in shared memory);
+    // blg: the same words, for the dense columns and the first-K tables
+    const int4 *dcol = reinterpret_cast<const int4 *>(blg + nv.o_dcols);
     const int64_t row_cap = a.child.cap;
 
     unsigned long long n_exp = 0, n_ovf = 0, n_bal = 0, n_pruned = 0, n_unwritten = 0, n_zero = 0, n_capdead = 0;
@@ -1654,8 +1668,8 @@ __device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint
                 uint32_t fxc = 0, fxp = 0;
                 if (a.child.fx && norm) {
                     const size_t fo = (size_t)p * (2 * G);
-                    fxc = a.par.fx[fo + gl] | bl[nv.o_fixc + k * G + gl];
-                    fxp = a.par.fx[fo + G + gl] | bl[nv.o_fixp + k * G + gl];
+                    fxc = a.par.fx[fo + gl] | blg[nv.o_fixc + k * G + gl];
+                    fxp = a.par.fx[fo + G + gl] | blg[nv.o_fixp + k * G + gl];
                 }
                 // first-K at the length cap: the child can only take secondary
                 // steps, which add flux to columns of its support.  A row with a
@@ -1735,14 +1749,14 @@ __device__ void generate_range(const NetView &nv, const LevelArgs &a, const uint
                             const int tw = (int)bl[nv.o_twin + kc];
                             ok2 = !(tw >= 0 && (tw == k || ((pu[tw >> 6] >> (tw & 63)) & 1ull)));
                         }
-                        const int cb = ok2 ? (int)bl[nv.o_colptr + kc] : 0;
-                        const int cn = ok2 ? (int)bl[nv.o_colptr + kc + 1] - cb : 0;
+                        const int cb = ok2 ? (int)blg[nv.o_colptr + kc] : 0;
+                        const int cn = ok2 ? (int)blg[nv.o_colptr + kc + 1] - cb : 0;
                         const int cmax = (int)__reduce_max_sync(FULL, (unsigned)cn);
                         uint32_t hit = 0;  // one-sided rows of U the column fixes
                         for (int q = 0; q < cmax; ++q) {
                             int r = 0, sg = 0;
                             if (q < cn) {
-                                const uint32_t ent = bl[nv.o_colent + cb + q];
+                                const uint32_t ent = blg[nv.o_colent + cb + q];
                                 r = ent_index(ent);
                                 sg = ent_coef(ent) > 0 ? 1 : -1;
                             }
@@ -1866,11 +1880,19 @@ __global__ void __launch_bounds__(kExpandWarps * 32, (CPL <= 2 ? 3 : 2)) generat
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const int wid = threadIdx.x >> 5;
-    const int blob_words = staged ? nv.blob_words : 0;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + blob_words);
-    const uint32_t *bl = stage_blob(nv, smem, mbar, staged != 0, a.ctr);
-    if (bl == nullptr) return;
-    generate_range<G, CPL>(nv, a, bl, (int64_t)blockIdx.x * kExpandWarps + wid, (int64_t)gridDim.x * kExpandWarps);
+    // staged: 0 nothing, 1 the whole blob, 2 its sparse tables [o_consptr, o_hbits)
+    const int w0 = staged == 2 ? nv.o_consptr : 0;
+    const int nw = staged == 1 ? nv.blob_words : (staged == 2 ? nv.o_hbits - nv.o_consptr : 0);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + nw);
+    const uint32_t *bl = nv.blob;
+    if (staged) {
+        const uint32_t *sb = stage_words(nv, smem, mbar, w0, nw, a.ctr);
+        if (sb == nullptr) return;
+        // offsets index the blob: the staged range answers for [w0, w0 + nw)
+        bl = reinterpret_cast<const uint32_t *>(reinterpret_cast<uintptr_t>(sb) - (uintptr_t)w0 * 4u);
+    }
+    generate_range<G, CPL>(nv, a, bl, staged == 2 ? nv.blob : bl, (int64_t)blockIdx.x * kExpandWarps + wid,
+                           (int64_t)gridDim.x * kExpandWarps);
 }
 
 // ---------------------------------------------------------------------------
@@ -3356,27 +3378,41 @@ int generate_narrow_grid_t(const NetView &nv, int sm_count)
     return sm_count * per_sm;
 }
 
+// the generic kernel stages the whole static network when it fits, else its
+// sparse tables when those fit (the dense columns stay in global memory)
+inline int generic_staging(const NetView &nv)
+{
+    if (nv.blob_words * 4 <= kStageLimitBytes) return 1;
+    if ((nv.o_hbits - nv.o_consptr) * 4 <= kStageSparseLimitBytes && nv.o_consptr % 4 == 0 && nv.o_hbits % 4 == 0)
+        return 2;
+    return 0;
+}
+inline size_t generic_smem(const NetView &nv, int mode)
+{
+    return (size_t)(mode == 1 ? nv.blob_words : (mode == 2 ? nv.o_hbits - nv.o_consptr : 0)) * 4 + 16;
+}
+
 template <int G, int CPL>
 cudaError_t launch_generate_t(const NetView &nv, const LevelArgs &a, int grid, cudaStream_t s)
 {
-    const bool staged = nv.blob_words * 4 <= kStageLimitBytes;
-    const size_t sm = (size_t)(staged ? nv.blob_words : 0) * 4 + 16;
+    const int mode = generic_staging(nv);
+    const size_t sm = generic_smem(nv, mode);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(generate_kernel<G, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kStageLimitBytes + 16);
+                             (kStageLimitBytes > kStageSparseLimitBytes ? kStageLimitBytes : kStageSparseLimitBytes) + 16);
         attr_set = true;
     }
-    generate_kernel<G, CPL><<<grid, kExpandWarps * 32, sm, s>>>(nv, a, staged ? 1 : 0);
+    generate_kernel<G, CPL><<<grid, kExpandWarps * 32, sm, s>>>(nv, a, mode);
     return cudaGetLastError();
 }
 
 template <int G, int CPL>
 int generate_grid_t(const NetView &nv, int sm_count)
 {
-    const bool staged = nv.blob_words * 4 <= kStageLimitBytes;
-    const size_t sm = (size_t)(staged ? nv.blob_words : 0) * 4 + 16;
-    cudaFuncSetAttribute(generate_kernel<G, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageLimitBytes + 16);
+    const size_t sm = generic_smem(nv, generic_staging(nv));
+    cudaFuncSetAttribute(generate_kernel<G, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (kStageLimitBytes > kStageSparseLimitBytes ? kStageLimitBytes : kStageSparseLimitBytes) + 16);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, generate_kernel<G, CPL>, kExpandWarps * 32, sm) !=
             cudaSuccess ||

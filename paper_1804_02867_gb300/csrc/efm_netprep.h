@@ -170,6 +170,9 @@ inline int prepare_network(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr,
             for (auto &e : l) blob.push_back(ent_pack(e.first, e.second));
     };
     put_csr(col, out.o_colptr, out.o_colent);
+    // [o_consptr, o_hbits): the expansion's sparse tables (branch lists, twins,
+    // keys), 16-byte aligned so that one bulk copy can stage them
+    while (blob.size() % 4) blob.push_back(0);
     put_csr(cons, out.o_consptr, out.o_consent);
     put_csr(prod, out.o_prodptr, out.o_prodent);
     out.o_twin = (int)blob.size();
@@ -183,6 +186,7 @@ inline int prepare_network(int32_t n_met, int32_t n_rxn, const int32_t *row_ptr,
     for (int r = 0; r < M; ++r) blob.push_back(((uint32_t)cons[r].size() << 16) | (uint32_t)r);
     out.o_keyneg = (int)blob.size();
     for (int r = 0; r < M; ++r) blob.push_back(((uint32_t)prod[r].size() << 16) | (uint32_t)r);
+    while (blob.size() % 4) blob.push_back(0);
     out.o_hbits = (int)blob.size();
     for (int k = 0; k < N; ++k) blob.push_back(hbits[k]);
     out.narrow = M <= kNarrowRows && !flux_rows;
