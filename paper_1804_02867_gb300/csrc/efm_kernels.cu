@@ -2268,7 +2268,7 @@ __device__ void generate_narrow(const NetView &nv, const LevelArgs &a, const uin
 }
 
 template <int G>
-__global__ void __launch_bounds__(kExpandWarps * 32, 5) generate_narrow_kernel(NetView nv, LevelArgs a, int staged)
+__global__ void __launch_bounds__(kExpandWarps * 32, 6) generate_narrow_kernel(NetView nv, LevelArgs a, int staged)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const int wid = threadIdx.x >> 5;
