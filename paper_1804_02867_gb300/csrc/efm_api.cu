@@ -301,6 +301,7 @@ struct Work {
     int fx_words = 0;  // lane-mask words per state (0: not kept)
     DevBuf slots, cslots, cand, res, bcnt, bfill, bptr, bres, ctr, sortidx, rcols;
     DevBuf fp;         // fingerprints of one level's reserved child rows
+    DevBuf wrec;       // narrow networks: the row pass's record per reserved row (16 B)
     DevBuf slow;       // narrow networks: records of the children the settle pass decides
     int64_t slow_cap = 0;
     DevBuf perm, fkb;  // first-K search: parent order of a level, bound support
@@ -331,7 +332,7 @@ void free_work(Work &w, cudaStream_t s)
     for (int i = 0; i < 2; ++i) free_arena(w, i, s);
     DevBuf *bufs[] = {&w.slots, &w.cslots, &w.cand, &w.res, &w.bcnt,    &w.bfill, &w.bptr,
                       &w.bres,  &w.ctr,    &w.sortidx, &w.rcols, &w.perm, &w.fkb,
-                      &w.lx,    &w.lscore, &w.lhist,   &w.lerr, &w.band, &w.fp, &w.slow,
+                      &w.lx,    &w.lscore, &w.lhist,   &w.lerr, &w.band, &w.fp, &w.slow, &w.wrec,
                       &w.ccnt,  &w.cfill,  &w.cptr,    &w.cne,  &w.csingle, &w.cent};
     for (DevBuf *b : bufs) dev_free(*b, s);
     for (auto &e : w.ev)
@@ -356,8 +357,9 @@ bool ensure_level_tables(Work &w, uint64_t reserved, cudaStream_t s)
 {
     if ((int64_t)reserved > w.fp_cap) {
         dev_free(w.fp, s);
+        dev_free(w.wrec, s);
         const int64_t cap = std::max<int64_t>((int64_t)reserved, w.fp_cap + w.fp_cap / 2);
-        if (!dev_alloc(w.fp, (size_t)cap * 8, s)) return false;
+        if (!dev_alloc(w.fp, (size_t)cap * 8, s) || !dev_alloc(w.wrec, (size_t)cap * 16, s)) return false;
         w.fp_cap = cap;
     }
     const uint64_t need = next_pow2(2 * reserved + 64);
@@ -742,6 +744,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
             a.slot_mask = nslots - 1;
             a.fp = (uint64_t *)w.fp.p;
             a.fp_cap = w.fp_cap;
+            a.wrec = (uint4 *)w.wrec.p;
             a.blk = blk;
             a.slow = nv.narrow ? (uint64_t *)w.slow.p : nullptr;
             a.slow_cap = nv.narrow ? w.slow_cap : 0;
@@ -760,6 +763,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
                 CK(cudaEventRecord(w.ev[2], s));
                 CK(cudaMemsetAsync(ctr + C_SLOW, 0, 8, s));
                 CK(launch_generate(nv, a, grid, s));
+                CK(launch_write_rows(nv, a, net->sm_count, s));
                 CK(launch_settle(nv, a, net->sm_count, s));
                 CK(launch_dedup(a, nv.Mpad, nv.W, net->sm_count, s));
                 CK(cudaEventRecord(w.ev[3], s));
@@ -775,7 +779,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
                 CK(cudaEventElapsedTime(&ms, w.ev[2], w.ev[3]));
                 out.expand_ms += ms;
                 out.expand_launches += 1;
-                out.kernel_launches += nv.narrow ? 6 : 5;
+                out.kernel_launches += nv.narrow ? 7 : 5;
                 {
                     const double state_bytes = 8.0 * nv.W + 4.0 * nv.M + 4.0;
                     const uint64_t next_now = h[C_NEXT];

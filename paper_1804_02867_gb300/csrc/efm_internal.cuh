@@ -152,7 +152,12 @@ struct LevelArgs {
     // the summaries, kSlowWords words each, for the settle pass
     uint64_t *slow;
     int64_t slow_cap;
+    // narrow networks: per reserved row, the row writer's record (parent row,
+    // column | flags | |U| << 14, A, C); x = kNoRecord: nothing to write
+    uint4 *wrec;
 };
+
+constexpr uint32_t kNoRecord = 0xFFFFFFFFu;
 
 constexpr int kSlowWords = 8;
 
@@ -252,6 +257,8 @@ cudaError_t launch_dedup(const LevelArgs &a, int Mpad, int W, int sm_count, cuda
 // narrow networks: settle the children the generate pass listed (exact gcd,
 // int32 range, superset rule), then write their rows; a no-op otherwise
 cudaError_t launch_settle(const NetView &nv, const LevelArgs &a, int sm_count, cudaStream_t s);
+// narrow networks: write the extra-flux rows of the generate pass's children
+cudaError_t launch_write_rows(const NetView &nv, const LevelArgs &a, int sm_count, cudaStream_t s);
 // the surviving rows (meta != 0) of [0, n) appended to live; *count must be 0
 cudaError_t launch_live_list(const uint32_t *meta, int64_t n, uint32_t *live, unsigned long long *count,
                              int sm_count, cudaStream_t s);

@@ -2142,79 +2142,17 @@ __device__ void generate_narrow(const NetView &nv, const LevelArgs &a, const uin
                         uint64_t f = sm.rh ^ mix64(support_hash(pu_l, W, kl) + 0x632BE59BD9B4E019ull);
                         if (f == kDeadFp) f = kDeadFp - 1;
                         a.fp[myidx] = f;
+                        // the row itself is written by the row pass
+                        a.wrec[myidx] = make_uint4((uint32_t)pl_, (uint32_t)kl | (vfyl ? 1u << 12 : 0u) |
+                                                                      (inl ? 1u << 13 : 0u) | ((uint32_t)pcl << 14),
+                                                   (uint32_t)Al, (uint32_t)Cl);
                     } else {
                         record_diag(a.ctr, ERR_BOUNDS, 7, (long long)myidx, a.fp_cap, a.level);
                         fatal = true;
                     }
                 }
             }
-            // === phase B: lane groups write the extra-flux rows of the ready
-            // children NG at a time (t = A p + C s in 32 bits, coalesced) ===
-            const uint32_t infol = (uint32_t)kl | ((uint32_t)pcl << 12) | (inl ? 1u << 19 : 0u) | (fast ? 1u << 20 : 0u) |
-                                   (vfyl ? 1u << 21 : 0u);
             const uint32_t pl32 = (uint32_t)pl_;
-            unsigned vmask = __ballot_sync(FULL, ready);
-            bool badl = false;  // this lane's item: the row's gcd is above 1
-            while (vmask) {
-                const int src = gi < __popc(vmask) ? (int)__fns(vmask, 0, gi + 1) : -1;
-#pragma unroll
-                for (int t = 0; t < NG; ++t) vmask &= vmask - 1;
-                const int sl = src < 0 ? 0 : src;
-                const uint32_t info_i = __shfl_sync(FULL, infol, sl);
-                const int k = (int)(info_i & 0xFFFu);
-                const int32_t A = __shfl_sync(FULL, Al, sl);
-                const int32_t C = __shfl_sync(FULL, Cl, sl);
-                const int64_t p = (int64_t)__shfl_sync(FULL, pl32, sl);
-                const uint64_t ridx = __shfl_sync(FULL, myidx, sl);
-                const uint32_t gti = __shfl_sync(FULL, gtl, sl);
-                const bool vfy = src >= 0 && ((info_i >> 21) & 1u);
-                int4 t4[CPL];
-                uint32_t gg = 1;
-                if (src >= 0) {
-                    const int4 *prow4 = reinterpret_cast<const int4 *>(a.par.B + (size_t)p * Mpad);
-                    const int4 *col4 = dcol + (size_t)k * (Mpad >> 2);
-#pragma unroll
-                    for (int i = 0; i < CPL; ++i) {
-                        const int4 v = prow4[gl + G * i];
-                        const int4 w = col4[gl + G * i];
-                        t4[i] = make_int4(A * v.x + C * w.x, A * v.y + C * w.y, A * v.z + C * w.z, A * v.w + C * w.w);
-                    }
-                    if (vfy) {
-                        // every common divisor of the row divides gt (gcd32(0, x) = x)
-                        gg = gti;
-#pragma unroll
-                        for (int i = 0; i < CPL; ++i) {
-                            const int32_t xs[4] = {t4[i].x, t4[i].y, t4[i].z, t4[i].w};
-#pragma unroll
-                            for (int jj = 0; jj < 4; ++jj)
-                                if (gg != 1u && xs[jj] != 0) gg = gcd32(gg, (uint32_t)(xs[jj] < 0 ? -xs[jj] : xs[jj]));
-                        }
-                    }
-                }
-#pragma unroll
-                for (int off = G / 2; off > 0; off >>= 1) {
-                    const uint32_t og = __shfl_xor_sync(FULL, gg, off);
-                    if (gg != 1u || og != 1u) gg = gcd32(gg, og);
-                }
-                const bool bad = vfy && gg > 1u;
-                if (src >= 0 && !bad && (int64_t)ridx < row_cap) {
-                    int4 *db = reinterpret_cast<int4 *>(a.child.B + (size_t)ridx * Mpad);
-#pragma unroll
-                    for (int i = 0; i < CPL; ++i) db[gl + G * i] = t4[i];
-                }
-                // the item's lane learns that its child goes to the settle pass
-#pragma unroll
-                for (int t = 0; t < NG; ++t) {
-                    const int bsrc = __shfl_sync(FULL, bad ? src : -1, t * G);
-                    if (bsrc == lane) badl = true;
-                }
-            }
-            if (badl) {
-                // its reserved row carries no state after all
-                if ((int64_t)myidx < row_cap) a.child.meta[myidx] = 0u;
-                if ((int64_t)myidx < a.fp_cap) a.fp[myidx] = kDeadFp;
-                slowl = true;
-            }
             // === the slow children (no gcd certificate or a possible overflow)
             // go to the settle pass as records ===
             const unsigned smask = __ballot_sync(FULL, slowl);
@@ -2255,7 +2193,10 @@ __device__ void generate_narrow(const NetView &nv, const LevelArgs &a, const uin
         if (__any_sync(FULL, fatal)) break;
     }
     for (int x = lane; x < pool_left; x += 32) {
-        if ((int64_t)(pool_next + x) < a.fp_cap) a.fp[pool_next + x] = kDeadFp;
+        if ((int64_t)(pool_next + x) < a.fp_cap) {
+            a.fp[pool_next + x] = kDeadFp;
+            a.wrec[pool_next + x].x = kNoRecord;
+        }
         if ((int64_t)(pool_next + x) < row_cap) a.child.meta[pool_next + x] = 0u;
     }
     // settle-record slots left unused: marked so that the settle pass skips them
@@ -2277,6 +2218,96 @@ __global__ void __launch_bounds__(kExpandWarps * 32, 6) generate_narrow_kernel(N
     const uint32_t *bl = stage_blob(nv, smem, mbar, staged != 0, a.ctr);
     if (bl == nullptr) return;
     generate_narrow<G>(nv, a, bl, (int64_t)blockIdx.x * kExpandWarps + wid, (int64_t)gridDim.x * kExpandWarps);
+}
+
+// ---------------------------------------------------------------------------
+// Row pass (narrow networks): one lane group per reserved row of the level,
+// in row order.  A row with a record gets t = A p + C s (32 bits: the
+// generate pass recorded only children that cannot overflow); when the
+// summaries did not certify its gcd, the group folds the row into its gcd
+// first, and a row with a gcd above 1 (rare) is withdrawn and handed to the
+// settle pass with its phase-A summaries.
+// ---------------------------------------------------------------------------
+template <int G>
+__global__ void __launch_bounds__(256) write_rows_kernel(NetView nv, LevelArgs a)
+{
+    constexpr int CPL = 2;
+    constexpr int NG = 32 / G;
+    const int lane = threadIdx.x & 31;
+    const int gi = lane / G;
+    const int gl = lane % G;
+    const int Mpad = nv.Mpad;
+    const int4 *dcol = reinterpret_cast<const int4 *>(nv.blob + nv.o_dcols);
+    const uint64_t begin = a.ctr[C_DEDUP_BEGIN];
+    uint64_t end = a.ctr[C_WRITTEN];
+    end = end < (uint64_t)a.fp_cap ? end : (uint64_t)a.fp_cap;
+    end = end < (uint64_t)a.child.cap ? end : (uint64_t)a.child.cap;
+    const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t r0 = begin + wid * NG; r0 < end; r0 += nwarps * NG) {
+        const uint64_t idx = r0 + gi;
+        uint4 rc = make_uint4(kNoRecord, 0u, 0u, 0u);
+        if (idx < end) rc = a.wrec[idx];
+        const bool has = rc.x != kNoRecord;
+        const int k = (int)(rc.y & 0xFFFu);
+        const bool vfy = has && ((rc.y >> 12) & 1u);
+        const int32_t A = (int32_t)rc.z, C = (int32_t)rc.w;
+        int4 t4[CPL];
+        uint32_t gg = vfy ? 0u : 1u;
+        if (has) {
+            const int4 *prow4 = reinterpret_cast<const int4 *>(a.par.B + (size_t)rc.x * Mpad);
+            const int4 *col4 = dcol + (size_t)k * (Mpad >> 2);
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) {
+                const int4 v = prow4[gl + G * i];
+                const int4 w = col4[gl + G * i];
+                t4[i] = make_int4(A * v.x + C * w.x, A * v.y + C * w.y, A * v.z + C * w.z, A * v.w + C * w.w);
+            }
+            if (vfy) {
+#pragma unroll
+                for (int i = 0; i < CPL; ++i) {
+                    const int32_t xs[4] = {t4[i].x, t4[i].y, t4[i].z, t4[i].w};
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj)
+                        if (gg != 1u && xs[jj] != 0) gg = gcd32(gg, (uint32_t)(xs[jj] < 0 ? -xs[jj] : xs[jj]));
+                }
+            }
+        }
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) {
+            const uint32_t og = __shfl_xor_sync(FULL, gg, off);
+            if (gg != 1u || og != 1u) gg = gcd32(gg, og);
+        }
+        const bool bad = vfy && gg != 1u;
+        if (has && !bad) {
+            int4 *db = reinterpret_cast<int4 *>(a.child.B + (size_t)idx * Mpad);
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) db[gl + G * i] = t4[i];
+        }
+        if (bad && gl == 0) {
+            // withdrawn: the row carries no state; the settle pass makes the child
+            a.child.meta[idx] = 0u;
+            a.fp[idx] = kDeadFp;
+            const uint64_t si = atomicAdd(&a.ctr[C_SLOW], 1ull);
+            if ((int64_t)si < a.slow_cap) {
+                const uint64_t *sm = a.child.sum + (size_t)idx * kSumWords;
+                uint64_t *r = a.slow + (size_t)si * kSlowWords;
+                const uint64_t w0 = (uint64_t)rc.x | ((uint64_t)k << 32) | ((uint64_t)((rc.y >> 14) & 0x7Fu) << 44) |
+                                    (((rc.y >> 13) & 1u) ? 1ull << 51 : 0ull) | (1ull << 52);
+                const uint64_t w1 = (uint64_t)rc.z | ((uint64_t)rc.w << 32);
+                r[0] = w0;
+                r[1] = w1;
+                r[2] = sm[0];  // row hash
+                r[3] = sm[1];  // positive entries (key-rank order)
+                r[4] = sm[2];  // negative entries
+                r[5] = sm[3];  // +-1 rows
+                r[6] = sm[4];  // odd rows
+                r[7] = 0ull;
+            } else {
+                record_diag(a.ctr, ERR_BOUNDS, 11, (long long)si, a.slow_cap, a.level);
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -3498,6 +3529,16 @@ cudaError_t launch_settle(const NetView &nv, const LevelArgs &a, int sm_count, c
         settle_kernel<4><<<sm_count * 4, kExpandWarps * 32, 0, s>>>(nv, a);
     else if (nv.EPL == 2)
         settle_kernel<8><<<sm_count * 4, kExpandWarps * 32, 0, s>>>(nv, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_write_rows(const NetView &nv, const LevelArgs &a, int sm_count, cudaStream_t s)
+{
+    if (!(nv.narrow && a.par.sum && a.child.sum && a.wrec)) return cudaSuccess;
+    if (nv.EPL == 1)
+        write_rows_kernel<4><<<sm_count * 8, 256, 0, s>>>(nv, a);
+    else if (nv.EPL == 2)
+        write_rows_kernel<8><<<sm_count * 8, 256, 0, s>>>(nv, a);
     return cudaGetLastError();
 }
 
