@@ -763,6 +763,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
                 CK(cudaEventRecord(w.ev[2], s));
                 CK(cudaMemsetAsync(ctr + C_SLOW, 0, 8, s));
                 CK(launch_generate(nv, a, grid, s));
+                CK(launch_prune_rows(nv, a, net->sm_count, s));
                 CK(launch_write_rows(nv, a, net->sm_count, s));
                 CK(launch_settle(nv, a, net->sm_count, s));
                 CK(launch_dedup(a, nv.Mpad, nv.W, net->sm_count, s));
@@ -779,7 +780,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
                 CK(cudaEventElapsedTime(&ms, w.ev[2], w.ev[3]));
                 out.expand_ms += ms;
                 out.expand_launches += 1;
-                out.kernel_launches += nv.narrow ? 7 : 5;
+                out.kernel_launches += nv.narrow ? (nv.W <= 2 && a.cptr ? 8 : 7) : 5;
                 {
                     const double state_bytes = 8.0 * nv.W + 4.0 * nv.M + 4.0;
                     const uint64_t next_now = h[C_NEXT];

@@ -257,6 +257,8 @@ cudaError_t launch_dedup(const LevelArgs &a, int Mpad, int W, int sm_count, cuda
 // narrow networks: settle the children the generate pass listed (exact gcd,
 // int32 range, superset rule), then write their rows; a no-op otherwise
 cudaError_t launch_settle(const NetView &nv, const LevelArgs &a, int sm_count, cudaStream_t s);
+// narrow networks: the superset rule over the generate pass's reserved rows
+cudaError_t launch_prune_rows(const NetView &nv, const LevelArgs &a, int sm_count, cudaStream_t s);
 // narrow networks: write the extra-flux rows of the generate pass's children
 cudaError_t launch_write_rows(const NetView &nv, const LevelArgs &a, int sm_count, cudaStream_t s);
 // the surviving rows (meta != 0) of [0, n) appended to live; *count must be 0

@@ -2095,13 +2095,13 @@ __device__ void generate_narrow(const NetView &nv, const LevelArgs &a, const uin
             bool ready = okl && nzl && fast;
             const bool vfyl = ready && !cert;
             bool slowl = okl && nzl && !fast;
-            if (ready && !inl) {
+            // the superset rule through the sentinel index runs in the prune
+            // pass over the reserved rows; the column buckets here otherwise
+            if (ready && !inl && !(W <= 2 && a.cptr)) {
                 const int64_t b1 = a.bptr[kl];
                 const int64_t n = a.bptr[kl + 1] - b1;
                 bool pr = false;
-                if (W <= 2 && a.cptr) {
-                    pr = pruned_indexed(a, pu_l, kl, W, nv.N);
-                } else if (n > 0) {
+                if (n > 0) {
                     if (W <= 2) {
                         const uint64_t u0 = child_word(pu_l, 0, kl), u1 = W == 2 ? child_word(pu_l, 1, kl) : 0ull;
                         bool maybe = true;
@@ -2218,6 +2218,47 @@ __global__ void __launch_bounds__(kExpandWarps * 32, 6) generate_narrow_kernel(N
     const uint32_t *bl = stage_blob(nv, smem, mbar, staged != 0, a.ctr);
     if (bl == nullptr) return;
     generate_narrow<G>(nv, a, bl, (int64_t)blockIdx.x * kExpandWarps + wid, (int64_t)gridDim.x * kExpandWarps);
+}
+
+// ---------------------------------------------------------------------------
+// Prune pass (narrow networks, supports of at most 2 words): one thread per
+// reserved row with a row-pass record that adds a new column.  The superset
+// rule on the child's support (the parent's, plus the column); a pruned
+// child gives its row up (no state, no fingerprint, no record).  A child
+// without a written row is tested the same way, from its parent.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) prune_rows_kernel(NetView nv, LevelArgs a)
+{
+    const uint64_t begin = a.ctr[C_DEDUP_BEGIN];
+    uint64_t end = a.ctr[C_WRITTEN];
+    end = end < (uint64_t)a.fp_cap ? end : (uint64_t)a.fp_cap;
+    const uint64_t row_cap = (uint64_t)a.child.cap;
+    const int W = nv.W;
+    unsigned long long n_pr = 0, n_unw = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = begin + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end; i += stride) {
+        const uint4 rc = a.wrec[i];
+        if (rc.x == kNoRecord || ((rc.y >> 13) & 1u)) continue;  // nothing to write, or a secondary step
+        const int k = (int)(rc.y & 0xFFFu);
+        if (pruned_indexed(a, a.par.U + (size_t)rc.x * W, k, W, nv.N)) {
+            a.fp[i] = kDeadFp;
+            a.wrec[i].x = kNoRecord;
+            if (i < row_cap)
+                a.child.meta[i] = 0u;
+            else
+                ++n_unw;
+            ++n_pr;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        n_pr += __shfl_xor_sync(FULL, n_pr, off);
+        n_unw += __shfl_xor_sync(FULL, n_unw, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (n_pr) atomicAdd(&a.ctr[C_PRUNED], n_pr);
+        if (n_unw) atomicAdd(&a.ctr[C_UNWRITTEN], (unsigned long long)(-(long long)n_unw));
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -3529,6 +3570,13 @@ cudaError_t launch_settle(const NetView &nv, const LevelArgs &a, int sm_count, c
         settle_kernel<4><<<sm_count * 4, kExpandWarps * 32, 0, s>>>(nv, a);
     else if (nv.EPL == 2)
         settle_kernel<8><<<sm_count * 4, kExpandWarps * 32, 0, s>>>(nv, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prune_rows(const NetView &nv, const LevelArgs &a, int sm_count, cudaStream_t s)
+{
+    if (!(nv.narrow && a.par.sum && a.child.sum && a.wrec && nv.W <= 2 && a.cptr)) return cudaSuccess;
+    prune_rows_kernel<<<sm_count * 8, 256, 0, s>>>(nv, a);
     return cudaGetLastError();
 }
 
