@@ -2269,10 +2269,9 @@ __global__ void __launch_bounds__(256) prune_rows_kernel(NetView nv, LevelArgs a
 // first, and a row with a gcd above 1 (rare) is withdrawn and handed to the
 // settle pass with its phase-A summaries.
 // ---------------------------------------------------------------------------
-template <int G>
+template <int G, int CPL>
 __global__ void __launch_bounds__(256) write_rows_kernel(NetView nv, LevelArgs a)
 {
-    constexpr int CPL = 2;
     constexpr int NG = 32 / G;
     const int lane = threadIdx.x & 31;
     const int gi = lane / G;
@@ -3583,10 +3582,11 @@ cudaError_t launch_prune_rows(const NetView &nv, const LevelArgs &a, int sm_coun
 cudaError_t launch_write_rows(const NetView &nv, const LevelArgs &a, int sm_count, cudaStream_t s)
 {
     if (!(nv.narrow && a.par.sum && a.child.sum && a.wrec)) return cudaSuccess;
+    // G lanes per row of 32 EPL entries, CPL 16-byte chunks each
     if (nv.EPL == 1)
-        write_rows_kernel<4><<<sm_count * 8, 256, 0, s>>>(nv, a);
+        write_rows_kernel<4, 2><<<sm_count * 8, 256, 0, s>>>(nv, a);
     else if (nv.EPL == 2)
-        write_rows_kernel<8><<<sm_count * 8, 256, 0, s>>>(nv, a);
+        write_rows_kernel<8, 2><<<sm_count * 8, 256, 0, s>>>(nv, a);
     return cudaGetLastError();
 }
 
