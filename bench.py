@@ -378,7 +378,7 @@ def run_ours(args):
         "expansions_per_step": tot_exp / args.steps / max(ws, 1),
         "results_per_step": tot_res / args.steps / max(ws, 1),
         "roofline": {
-            "kernel": "level pass: generate_narrow_kernel<8> + settle_kernel<8> + dedup_kernel",
+            "kernel": "level pass: generate_narrow_kernel<8> + prune_rows_kernel + write_rows_kernel<8,2> + settle_kernel<8> + dedup_kernel",
             "bound": "hbm",
             "achieved": achieved,
             "peak": float(peaks["hbm_gbs"]),
