@@ -305,8 +305,11 @@ int efm_fetch_results(efm_job *job, int32_t job_target_idx, uint64_t *supports, 
 /* Measurements of one target's traversal, for the benchmark's roofline:
  *  total_ms          device time of the whole traversal (CUDA events on the
  *                    network's stream, seeds to sorted results)
- *  expand_ms         summed device time of the expansion kernel launches
- *  expand_launches   number of expansion kernel launches (one per level)
+ *  expand_ms         summed device time of the expansion launches: the
+ *                    generate kernel and the passes that finish its level
+ *                    (prune, row, settle and dedup passes), event to event
+ *  expand_launches   number of expansion launches (one per level, or per
+ *                    chunk of a first-K level)
  *  expand_bytes      algorithmic bytes those launches must move: each parent
  *                    state read once, each new distinct state written once
  *                    (state = 8 W + 4 M + 4 bytes), 16 bytes of hash slot
