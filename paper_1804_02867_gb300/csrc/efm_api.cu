@@ -499,9 +499,26 @@ bool model_reserve_rows(efm_model *m, int64_t rows);
 // every descendant keeps or grows its support.
 // seedset (device, n_seedset columns): start from that one state instead of
 // the target's seeds (Prop. 1), at level n_seedset - 1.
+// A first-K sub-search that starts from rows [r0, r1) of another search's
+// arena `par` (states of level `level`); deg_sum bounds their branch counts.
+struct FrontierStart {
+    Arena par;
+    int64_t r0, r1;
+    int level;
+    uint64_t deg_sum;
+};
+
+// allow_split (first-K only): a level over the frontier budget does not end
+// the search; its parents are split into parts, and the rest of the search
+// runs from each part in turn (with a second work area, parts not split
+// again).  A state reached from two parts is expanded twice, which changes
+// no result: balanced supports are judged per part and merged, and the
+// bound and the superset rule may use any accepted result.  fs / seed_top:
+// such a part's start and the K smallest results known when it starts.
 int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetOut &out,
                const efm_model *model = nullptr, Trace *trace = nullptr, const int32_t *seedset = nullptr,
-               int n_seedset = 0)
+               int n_seedset = 0, const FrontierStart *fs = nullptr, const std::vector<uint64_t> *seed_top = nullptr,
+               bool allow_split = false)
 {
     const NetView &nv = view_of(net, lim);
     cudaStream_t s = net->stream;
@@ -548,14 +565,17 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
     // level 0: seeds (or the seed set's one state, at level |R_in| - 1),
     // written densely: the first level reads its parents in arena order
     int cur = 0;
-    const int level0 = seedset ? n_seedset - 1 : 0;
+    const int level0 = fs ? fs->level : (seedset ? n_seedset - 1 : 0);
     a.level = level0;
     a.child = arena(cur);
-    if (seedset)
+    if (fs) {
+        // the first parents are the caller's rows: nothing to seed
+    } else if (seedset) {
         CK(launch_seedset(nv, a, seedset, n_seedset, s));
-    else
+    } else {
         CK(launch_seed(nv, a, target, s));
-    out.kernel_launches += 1;
+    }
+    out.kernel_launches += fs ? 0 : 1;
     AcceptArgs acc{};
     acc.cand = (const uint64_t *)w.cand.p;
     acc.res = (uint64_t *)w.res.p;
@@ -593,16 +613,21 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
         top.add(fresh.data(), res_n);
         if (top.pc > 0) CK(cudaMemcpyAsync(w.fkb.p, top.kth.data(), (size_t)nv.W * 8, cudaMemcpyHostToDevice, s));
     }
-    int64_t n_front = (int64_t)h[C_NEXT];  // distinct states of the level
+    if (fk && seed_top && !seed_top->empty()) {
+        top.add(seed_top->data(), (int64_t)(seed_top->size() / nv.W));
+        if (top.pc > 0) CK(cudaMemcpyAsync(w.fkb.p, top.kth.data(), (size_t)nv.W * 8, cudaMemcpyHostToDevice, s));
+    }
+    int64_t n_front = fs ? fs->r1 - fs->r0 : (int64_t)h[C_NEXT];  // distinct states of the level
     int64_t n_rows = n_front;              // arena rows the next level reads (seeds are dense)
-    uint64_t deg_sum = h[C_DEGSUM];
+    uint64_t deg_sum = fs ? fs->deg_sum : h[C_DEGSUM];
     int status = 0;
+    bool split = false;  // the K smallest come from the parts of a split level (top)
     c.levels = 1;
     bool stop = false;
     if (lim.max_frontier > 0 && n_front > lim.max_frontier) {
         status |= EFM_TRUNCATED;
         stop = true;
-    } else if (n_front > w.rows[cur]) {
+    } else if (!fs && n_front > w.rows[cur]) {
         return EFM_ECAPACITY;
     } else {
         c.frontier += n_front;
@@ -671,6 +696,9 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
         // first-K: the level's parents in proposal order (positions -> arena
         // rows), expanded in chunks with the bound refreshed between them
         // (rows of later copies have no branches: they cost a meta read)
+        const int64_t par_rows = n_rows;    // this level's parents
+        const uint64_t par_deg = deg_sum;
+        const bool ext = fs && level == level0 + 1;  // parents in the caller's arena
         int64_t chunk = n_rows;
         const uint32_t *order = nullptr;
         if (fk) {
@@ -737,7 +765,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
             CK(cudaMemsetAsync(ctr + C_NEXT, 0, 2 * 8, s));
             CK(cudaMemsetAsync(ctr + C_WRITTEN, 0, 3 * 8, s));
             CK(cudaMemsetAsync(ctr + C_DEDUP_BEGIN, 0, 8, s));
-            a.par = arena(cur);
+            a.par = ext ? fs->par : arena(cur);
             a.child = arena(cur ^ 1);
             a.live = (uint32_t *)w.live[cur ^ 1].p;
             a.slots = (unsigned long long *)w.slots.p;
@@ -755,7 +783,7 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
                 const int64_t cn = std::min<int64_t>(chunk, n_rows - c0);
                 a.n_par = cn;
                 a.perm = order ? order + c0 : nullptr;
-                a.par_base = order ? 0 : c0;
+                a.par_base = order ? 0 : c0 + (ext ? fs->r0 : 0);
                 a.cpw = (int)std::min<int64_t>(32, std::max<int64_t>(1, (cn + total_warps - 1) / total_warps));
                 a.fk_pc = fk ? top.pc : 0;
                 a.fk_sup = (const uint64_t *)w.fkb.p;
@@ -843,7 +871,56 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
         c.levels = level - level0 + 1;
         cur ^= 1;
         if (lim.max_frontier > 0 && n_front > lim.max_frontier) {
-            status |= EFM_TRUNCATED;
+            if (!(fk && allow_split && par_rows > 1)) {
+                status |= EFM_TRUNCATED;
+                break;
+            }
+            // first-K: the level's parents (arena cur ^ 1 now) in parts of
+            // about half the budget's worth of children, each run to the end
+            Work w2;
+            int rc2 = alloc_work(w2, net, lim, total_warps, s);
+            const int64_t parts = std::min<int64_t>(
+                par_rows, std::max<int64_t>(2, (2 * n_front + lim.max_frontier - 1) / lim.max_frontier));
+            for (int64_t p = 0; rc2 == EFM_OK && p < parts; ++p) {
+                FrontierStart sub{arena(cur ^ 1), par_rows * p / parts, par_rows * (p + 1) / parts, level - 1, par_deg};
+                if (sub.r1 <= sub.r0) continue;
+                TargetOut so;
+                const std::vector<uint64_t> known = top.rows;
+                rc2 = run_target(net, w2, lim, target, so, nullptr, nullptr, nullptr, 0, &sub, &known, false);
+                if (rc2 == EFM_OK) {
+                    status |= so.status;
+                    if (so.n > 0) {
+                        std::vector<uint64_t> got((size_t)so.n * nv.W);
+                        if (cudaMemcpyAsync(got.data(), so.sup.p, got.size() * 8, cudaMemcpyDeviceToHost, s) !=
+                                cudaSuccess ||
+                            cudaStreamSynchronize(s) != cudaSuccess)
+                            rc2 = EFM_ECUDA;
+                        else
+                            top.add(got.data(), so.n);
+                    }
+                    c.expansions += so.ctr.expansions;
+                    c.overflow += so.ctr.overflow;
+                    c.balanced += so.ctr.balanced;
+                    c.pruned += so.ctr.pruned;
+                    c.candidates += so.ctr.candidates;
+                    c.results += so.ctr.results;
+                    c.frontier_max = std::max<int64_t>(c.frontier_max, so.ctr.frontier_max);
+                    c.levels = std::max<int64_t>(c.levels, so.ctr.levels + (level - 1 - level0));
+                    out.expand_ms += so.expand_ms;
+                    out.expand_bytes += so.expand_bytes;
+                    out.expand_launches += so.expand_launches;
+                    out.kernel_launches += so.kernel_launches;
+                    if (getenv("EFM_DEBUG"))
+                        fprintf(stderr, "efm: split level %d part %lld/%lld rows %lld status %d kept %lld\n", level,
+                                (long long)p, (long long)parts, (long long)(sub.r1 - sub.r0), so.status,
+                                (long long)(top.rows.size() / nv.W));
+                }
+                dev_free(so.sup, s);
+                if (status & EFM_TRUNCATED) break;  // a part over the budget: the answer is uncertified anyway
+            }
+            free_work(w2, s);
+            if (rc2) return rc2;
+            split = true;
             break;
         }
         if (unwritten) return EFM_ECAPACITY;  // unreachable: the loop above runs such a level again
@@ -864,32 +941,40 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
     // output: sorted by (|U|, column list), capped
     int64_t n_keep = lim.max_results > 0 ? std::min<int64_t>(res_n, lim.max_results) : res_n;
     if (fk) n_keep = std::min<int64_t>(res_n, lim.first_k);
-    const uint64_t n2 = next_pow2((uint64_t)std::max<int64_t>(res_n, 1));
-    if (n2 > w.sort_cap) {
-        dev_free(w.sortidx, s);
-        if (!dev_alloc(w.sortidx, n2 * 4, s)) return EFM_ENOMEM;
-        w.sort_cap = n2;
-    }
-    if (!dev_alloc(out.sup, (size_t)std::max<int64_t>(n_keep, 1) * nv.W * 8, s)) return EFM_ENOMEM;
-    CK(launch_sort_results((const uint64_t *)w.res.p, res_n, nv.W, (uint32_t *)w.sortidx.p, (int64_t)n2,
-                           (uint64_t *)out.sup.p, n_keep, s));
-    if (res_n > 0 && n_keep > 0) {
-        int lg = 0;
-        while ((1ull << lg) < n2) ++lg;
-        out.kernel_launches += 2 + (int64_t)lg * (lg + 1) / 2;
+    if (split) {
+        // the K smallest distinct supports of this search and its parts, sorted by TopK
+        n_keep = (int64_t)(top.rows.size() / nv.W);
+        if (!dev_alloc(out.sup, (size_t)std::max<int64_t>(n_keep, 1) * nv.W * 8, s)) return EFM_ENOMEM;
+        if (n_keep > 0) CK(cudaMemcpyAsync(out.sup.p, top.rows.data(), top.rows.size() * 8, cudaMemcpyHostToDevice, s));
+    } else {
+        const uint64_t n2 = next_pow2((uint64_t)std::max<int64_t>(res_n, 1));
+        if (n2 > w.sort_cap) {
+            dev_free(w.sortidx, s);
+            if (!dev_alloc(w.sortidx, n2 * 4, s)) return EFM_ENOMEM;
+            w.sort_cap = n2;
+        }
+        if (!dev_alloc(out.sup, (size_t)std::max<int64_t>(n_keep, 1) * nv.W * 8, s)) return EFM_ENOMEM;
+        CK(launch_sort_results((const uint64_t *)w.res.p, res_n, nv.W, (uint32_t *)w.sortidx.p, (int64_t)n2,
+                               (uint64_t *)out.sup.p, n_keep, s));
+        if (res_n > 0 && n_keep > 0) {
+            int lg = 0;
+            while ((1ull << lg) < n2) ++lg;
+            out.kernel_launches += 2 + (int64_t)lg * (lg + 1) / 2;
+        }
     }
     CK(cudaEventRecord(w.ev[1], s));
     CK(cudaEventSynchronize(w.ev[1]));
     CK(cudaEventElapsedTime(&ms, w.ev[0], w.ev[1]));
     out.total_ms = ms;
     out.n = n_keep;
+    // (the parts of a split level have added their own work already)
     c.seeds = (int64_t)h[C_SEEDS];
-    c.expansions = (int64_t)h[C_EXP];
-    c.overflow = (int64_t)h[C_OVF];
-    c.balanced = (int64_t)h[C_BAL];
-    c.candidates = (int64_t)h[C_CAND_N];
-    c.results = (int64_t)h[C_RES];
-    c.pruned = (int64_t)h[C_PRUNED];
+    c.expansions += (int64_t)h[C_EXP];
+    c.overflow += (int64_t)h[C_OVF];
+    c.balanced += (int64_t)h[C_BAL];
+    c.candidates += (int64_t)h[C_CAND_N];
+    c.results += (int64_t)h[C_RES];
+    c.pruned += (int64_t)h[C_PRUNED];
     c.zero_flux = (int64_t)h[C_ZERO];
     if (c.overflow) status |= EFM_OVERFLOW_DROPPED;
     c.status = status;
@@ -915,7 +1000,7 @@ int run_first_k(efm_net *net, Work &w, const efm_limits &lim, int target, Target
         efm_limits l2 = lim;
         l2.max_len = std::min(P, lim.max_len);
         TargetOut o;
-        const int rc = run_target(net, w, l2, target, o, model, nullptr, seedset, n_seedset);
+        const int rc = run_target(net, w, l2, target, o, model, nullptr, seedset, n_seedset, nullptr, nullptr, true);
         if (rc) {
             dev_free(o.sup, net->stream);
             return rc;

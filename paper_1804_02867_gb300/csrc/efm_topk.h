@@ -36,23 +36,34 @@ struct TopK {
         }
         return false;
     }
+    // rows: supports (W words each); a support already kept counts once, so
+    // the K kept rows are the K smallest distinct supports seen
     void add(const uint64_t *r, int64_t n)
     {
         rows.insert(rows.end(), r, r + (size_t)n * W);
         const int64_t have = (int64_t)(rows.size() / W);
-        if (have < K) return;
         std::vector<int64_t> idx((size_t)have);
         for (int64_t i = 0; i < have; ++i) idx[i] = i;
         const uint64_t *base = rows.data();
         const int Wl = W;
-        std::nth_element(idx.begin(), idx.begin() + (K - 1), idx.end(), [&](int64_t i, int64_t j) {
-            return less(base + i * Wl, base + j * Wl, Wl);
-        });
-        std::vector<uint64_t> keep((size_t)K * W);
-        for (int i = 0; i < K; ++i) std::copy(base + idx[i] * W, base + idx[i] * W + W, keep.begin() + (size_t)i * W);
-        kth.assign(base + idx[K - 1] * W, base + idx[K - 1] * W + W);
+        std::sort(idx.begin(), idx.end(), [&](int64_t i, int64_t j) { return less(base + i * Wl, base + j * Wl, Wl); });
+        std::vector<uint64_t> keep;
+        keep.reserve((size_t)std::min<int64_t>(have, K) * W);
+        int64_t kept = 0;
+        for (int64_t t = 0; t < have && kept < K; ++t) {
+            const uint64_t *x = base + idx[t] * W;
+            if (kept > 0 && std::equal(x, x + W, keep.end() - W)) continue;  // the same support again
+            keep.insert(keep.end(), x, x + W);
+            ++kept;
+        }
         rows.swap(keep);
-        pc = popc(kth.data(), W);
+        if (kept == K) {
+            kth.assign(rows.end() - W, rows.end());
+            pc = popc(kth.data(), W);
+        } else {
+            kth.clear();
+            pc = 0;
+        }
     }
 };
 

@@ -220,8 +220,12 @@ def order_key(row):
     return (len(cols), cols)
 
 
-@pytest.mark.parametrize("seed,K,W", [(0, 1, 1), (1, 5, 1), (2, 40, 2), (3, 100, 3), (4, 7, 64)])
-def test_topk_keeps_the_k_smallest(driver, seed, K, W):
+@pytest.mark.parametrize("seed,K,W,dup", [(0, 1, 1, False), (1, 5, 1, False), (2, 40, 2, False), (3, 100, 3, False),
+                                         (4, 7, 64, False), (5, 30, 2, True), (6, 3, 1, True)])
+def test_topk_keeps_the_k_smallest(driver, seed, K, W, dup):
+    """The K smallest distinct supports seen, after every batch; with dup,
+    later batches repeat supports of earlier ones (as the merged answers of
+    several searches do), and a repeat counts once."""
     rng = np.random.default_rng(seed)
     n_cols = 64 * W
     seen = set()
@@ -234,6 +238,8 @@ def test_topk_keeps_the_k_smallest(driver, seed, K, W):
         seen.add(tuple(row))
     rows = list(seen)
     rng.shuffle(rows)
+    if dup:  # every third support appears a second time, later
+        rows = rows + [rows[i] for i in range(0, len(rows), 3)]
     cuts = sorted(rng.choice(np.arange(1, len(rows)), size=5, replace=False).tolist()) + [len(rows)]
     text = [f"{K} {W}"]
     batches, lo = [], 0
@@ -247,13 +253,13 @@ def test_topk_keeps_the_k_smallest(driver, seed, K, W):
                          check=True).stdout.splitlines()
     bounds = [ln.split()[1:] for ln in out if ln.startswith("bound")]
     kept = [tuple(int(x) for x in ln.split()[1:]) for ln in out if ln.startswith("row")]
-    so_far = []
+    so_far = set()
     for b, line in zip(batches, bounds):
-        so_far += b
+        so_far |= set(b)
         if len(so_far) < K:
             assert line == ["0"]
             continue
         kth = sorted(so_far, key=order_key)[K - 1]
         assert int(line[0]) == len(columns(kth))
         assert tuple(int(x) for x in line[1:]) == kth
-    assert sorted(kept, key=order_key) == sorted(rows, key=order_key)[:K]
+    assert sorted(kept, key=order_key) == sorted(set(rows), key=order_key)[:K]
