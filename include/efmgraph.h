@@ -70,7 +70,8 @@ typedef struct {
                               traversals with the length cap deepened, P = 1, 2, ... up to
                               max_len, until one holds at least K results (those of size <= P
                               are exactly that run's results), each with an exact branch and
-                              bound; the counters are those of the last run.  The answer is
+                              bound; a level over max_frontier is split into parts run one after
+                              the other; the counters are those of the last run.  The answer is
                               certified unless EFM_TRUNCATED is set.  max_results must be 0
                               (not with the batched call) */
     int32_t proposal;      /* order of a first-K search: EFM_PLAIN (arena order) or
