@@ -1,0 +1,82 @@
+"""First-K with levels over the frontier budget split into parts.
+
+A first-K search does not stop at a level whose distinct children exceed
+max_frontier: it splits the level's parents into parts and runs the rest of
+the search from each part in turn.  The answer is still the definition's
+(the K smallest results of the complete traversal, the oracle's first_k)
+whenever the search reports no truncation.  Small budgets force splits on
+the tiny and core networks; the oracle's own run under the same budget
+(first_k_within) shows where a level did overflow, so the tests can check
+that splitting was exercised.
+"""
+import numpy as np
+import pytest
+
+from paper_1804_02867_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def efm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1804_02867_gb300 import build, efmgraph
+
+    build.build()
+    efmgraph.load_library()
+    return efmgraph
+
+
+def test_split_levels_on_tiny_networks(oracle_lib, efm):
+    split_and_certified = 0
+    for seed in range(10):
+        net = synth.tiny(seed)
+        with efm.Network(net) as nw:
+            for t in list(net.targets) + [-1]:
+                for k, budget in ((3, 4), (6, 6), (20, 12)):
+                    (sup, ctr), = efm.enumerate_targets(nw, [t], 9, 1, 0, budget, first_k=k)
+                    if ctr["status"] & efm.EFM_TRUNCATED:
+                        continue
+                    want, _ = oracle_lib.first_k(net, t, k, 9, 1)
+                    assert np.array_equal(sup, want), (seed, t, k, budget)
+                    _, _, ok = oracle_lib.first_k_within(net, t, k, 9, 1, budget)
+                    split_and_certified += 0 if ok else 1
+    assert split_and_certified > 0  # some certified answers needed a split level
+
+
+# (target, budget): about a third of the largest level of the oracle's run at
+# the length the 40 smallest results need (351K, 46K, 332K and 115K states)
+CORE_CASES = [(63, 1 << 17), (58, 1 << 14), (65, 1 << 17), (1, 1 << 15)]
+
+
+def test_split_levels_on_the_core_network(oracle_lib, efm):
+    net = synth.core()
+    split_and_certified = 0
+    with efm.Network(net) as nw:
+        for t, budget in CORE_CASES:
+            (sup, ctr), = efm.enumerate_targets(nw, [t], 30, 4, 0, budget, first_k=40)
+            if ctr["status"] & efm.EFM_TRUNCATED:
+                continue
+            want, _ = oracle_lib.first_k(net, t, 40, 30, 4)
+            assert np.array_equal(sup, want), (t, budget)
+            _, _, ok = oracle_lib.first_k_within(net, t, 40, 30, 4, budget)
+            split_and_certified += 0 if ok else 1
+    assert split_and_certified > 0
+
+
+def test_seed_set_first_k_with_split_levels(oracle_lib, efm):
+    """A first-K search from a seed set (Prop. 1) splits the same way."""
+    net = synth.tiny(3)
+    with efm.Network(net) as nw:
+        cols = [0]
+        job, _ = efm.efm_find_pathways_from(nw.handle, cols, 9, 1, 0, 6, first_k=5)
+        try:
+            sup, ctr, _ = efm.efm_fetch_results(job, 0)
+        finally:
+            efm.efm_free_job(job)
+        if not ctr["status"] & efm.EFM_TRUNCATED:
+            full, _ = oracle_lib.enumerate_from(net, cols, oracle_lib.Limits(9, 1, 0, 0))
+            assert np.array_equal(sup, full[:5])
