@@ -880,6 +880,13 @@ int run_target(efm_net *net, Work &w, const efm_limits &lim, int target, TargetO
             // budget's worth of children, each run to the end
             Work w2;
             int rc2 = alloc_work(w2, net, lim, total_warps, s);
+            if (rc2 == EFM_ENOMEM) {
+                // no room for a second work area: the answer stays uncertified
+                free_work(w2, s);
+                cudaGetLastError();
+                status |= EFM_TRUNCATED;
+                break;
+            }
             const int64_t parts = std::min<int64_t>(
                 par_rows, std::max<int64_t>(2, (2 * n_front + lim.max_frontier - 1) / lim.max_frontier));
             // the level's parents: this search's arena, or the caller's rows
